@@ -1,0 +1,183 @@
+/*
+ * aa_oracle.c -- plain CPU oracle for brute-force incoherent dedispersion and
+ * the single-pulse search (boxcar SNR + thresholded local-maximum peaks).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product library links, loads or
+ * calls this file.  It is used by tests/, by __graft_entry__.smoke() and by the
+ * cpu_baseline / reference legs of bench.py, and nowhere else.  It shares no
+ * code, header, table or constant generator with the CUDA path.
+ *
+ * Every function is the textbook definition written out as scalar loops:
+ * FP64 for frequencies, delays, mean, standard deviation and SNR; exact int64
+ * for every sum of samples.  The paper (arXiv:1912.07704) names the modules
+ * (dedispersion, boxcar single-pulse search with peak finding, Sec. 1) and the
+ * pipeline shape (Sec. 2.3-3.3); the arithmetic below is the brute-force
+ * method it refers to:
+ *
+ *   f_c     = fch1 + c*foff                              (channel centre, MHz)
+ *   f_top   = highest channel frequency
+ *   Delta_c = f_c^-2 - f_top^-2
+ *   DM_i    = dm_lo + i*dm_step                          (not accumulated)
+ *   s(c,i)  = round_half_away(((K*DM_i)*Delta_c) / (tsamp*dec)),  K = 4.148808e3
+ *   x_r[c][j] = sum_{k<dec} x[c][j*dec+k],  j < floor(T/dec)
+ *   y[i][t]   = sum_c x_r[c][t + s(c,i)],   t < L = floor(T/dec) - max s
+ *   mu, sigma = population mean / std of y[i][0..L)
+ *   SNR_w(t)  = (sum_{k<w} y[t+k] - w*mu) / (sigma*sqrt(w)),  1 <= w <= min(W, L-t)
+ *   B(t)      = max_w SNR_w(t)  (smallest w on ties)
+ *   peak at t iff B(t) >= thr and B(t) > B(t-1) and B(t) >= B(t+1)
+ *                 (missing neighbours count as -infinity; sigma == 0 rows
+ *                  have B = 0 and no peaks)
+ *
+ * Compile with -ffp-contract=off so that every FP64 operation is rounded
+ * separately, in the order written.  OpenMP (when enabled) only splits
+ * independent outputs across threads; integer sums do not depend on order.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORACLE_K_DM 4.148808e3 /* MHz^2 pc^-1 cm^3 s */
+
+int oracle_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
+
+/* Highest channel frequency: fch1 when foff < 0, the last channel otherwise. */
+double oracle_f_top(double fch1, double foff, int32_t nchans)
+{
+    double f_last = fch1 + (double)(nchans - 1) * foff;
+    return f_last > fch1 ? f_last : fch1;
+}
+
+/* Integer delay of every channel for one DM, in samples of the decimated
+ * series.  Returns how many channels fell within 1e-9 of a half-integer
+ * (where the rounding direction is decided by the last bits). */
+int32_t oracle_shifts(int32_t nchans, double fch1, double foff, double tsamp,
+                      double dm, int32_t dec, int32_t* out)
+{
+    double ft = oracle_f_top(fch1, foff, nchans);
+    int32_t near_half = 0;
+    for (int32_t c = 0; c < nchans; ++c) {
+        double fc = fch1 + (double)c * foff;
+        double delta = 1.0 / (fc * fc) - 1.0 / (ft * ft);
+        double v = ORACLE_K_DM * dm * delta / (tsamp * (double)dec);
+        if (fabs(v - floor(v) - 0.5) < 1e-9) near_half++;
+        out[c] = (int32_t)llround(v);
+    }
+    return near_half;
+}
+
+/* Time decimation by summation; the trailing partial bin is dropped. */
+void oracle_decimate(const uint8_t* x, int32_t nchans, int64_t nsamp, int64_t pitch,
+                     int32_t dec, uint16_t* out, int64_t out_pitch)
+{
+    int64_t nd = nsamp / dec;
+    for (int32_t c = 0; c < nchans; ++c) {
+        for (int64_t j = 0; j < nd; ++j) {
+            uint32_t s = 0;
+            for (int32_t k = 0; k < dec; ++k) s += x[(int64_t)c * pitch + j * dec + k];
+            out[(int64_t)c * out_pitch + j] = (uint16_t)s;
+        }
+    }
+}
+
+static inline int64_t sample_at(const void* x, int32_t elem_bytes, int64_t idx)
+{
+    if (elem_bytes == 1) return ((const uint8_t*)x)[idx];
+    return ((const uint16_t*)x)[idx];
+}
+
+/* One dedispersed series y[t] = sum_c x[c][t + shifts[c]] for t in [t0, t1).
+ * x is [nchans][pitch] with 1- or 2-byte unsigned samples. */
+void oracle_dedisperse(const void* x, int32_t elem_bytes, int32_t nchans, int64_t pitch,
+                       const int32_t* shifts, int64_t t0, int64_t t1, int64_t* out)
+{
+    int64_t n = t1 - t0;
+    if (n <= 0) return;
+#pragma omp parallel for schedule(static)
+    for (int64_t t = t0; t < t1; ++t) {
+        int64_t acc = 0;
+        for (int32_t c = 0; c < nchans; ++c)
+            acc += sample_at(x, elem_bytes, (int64_t)c * pitch + t + shifts[c]);
+        out[t - t0] = acc;
+    }
+}
+
+/* Population mean and standard deviation of a series (two passes, FP64). */
+void oracle_moments(const int64_t* y, int64_t n, double* mu, double* sigma)
+{
+    if (n <= 0) { *mu = 0.0; *sigma = 0.0; return; }
+    int64_t s = 0;
+    for (int64_t t = 0; t < n; ++t) s += y[t];
+    double m = (double)s / (double)n;
+    double ss = 0.0;
+    for (int64_t t = 0; t < n; ++t) {
+        double d = (double)y[t] - m;
+        ss += d * d;
+    }
+    *mu = m;
+    *sigma = sqrt(ss / (double)n);
+}
+
+/* Exhaustive boxcar search for t in [t0, t1) of a series of length n.
+ * B[t-t0] = max_{1<=w<=min(W,n-t)} SNR_w(t); wbest = smallest maximising w;
+ * margin = B minus the best SNR over all other widths (+inf if only one). */
+void oracle_boxcar(const int64_t* y, int64_t n, double mu, double sigma, int32_t W,
+                   int64_t t0, int64_t t1, double* B, int32_t* wbest, double* margin)
+{
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t t = t0; t < t1; ++t) {
+        int64_t k = t - t0;
+        if (sigma == 0.0) {
+            B[k] = 0.0;
+            wbest[k] = 1;
+            margin[k] = INFINITY;
+            continue;
+        }
+        int64_t wmax = n - t < (int64_t)W ? n - t : (int64_t)W;
+        int64_t S = 0;
+        double best = -INFINITY, second = -INFINITY;
+        int32_t bw = 0;
+        for (int64_t w = 1; w <= wmax; ++w) {
+            S += y[t + w - 1];
+            double snr = ((double)S - (double)w * mu) / (sigma * sqrt((double)w));
+            if (snr > best) {
+                second = best;
+                best = snr;
+                bw = (int32_t)w;
+            } else if (snr > second) {
+                second = snr;
+            }
+        }
+        B[k] = best;
+        wbest[k] = bw;
+        margin[k] = best - second;
+    }
+}
+
+/* Thresholded local maxima of B over [0, n): returns the number found and
+ * writes up to cap indices. */
+int64_t oracle_peaks(const double* B, int64_t n, double thr, int64_t* out_t, int64_t cap)
+{
+    int64_t found = 0;
+    for (int64_t t = 0; t < n; ++t) {
+        double left = t > 0 ? B[t - 1] : -INFINITY;
+        double right = t + 1 < n ? B[t + 1] : -INFINITY;
+        if (B[t] >= thr && B[t] > left && B[t] >= right) {
+            if (found < cap) out_t[found] = t;
+            found++;
+        }
+    }
+    return found;
+}

@@ -1,0 +1,254 @@
+"""Python face of the CPU oracle (``aa_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY: imported by ``tests/``, ``__graft_entry__.smoke()``
+and the ``cpu_baseline`` / ``--impl reference`` legs of ``bench.py``.  The
+product package never imports it.  It shares no code with the CUDA path.
+
+The C file holds the arithmetic (FP64 delays/statistics/SNR, exact int64
+sums); this module only marshals numpy arrays and assembles the per-range
+plan and candidate lists in the same plain terms:
+
+* plan (brute-force DM grid, per-range decimation): DM_i = dm_lo + i*dm_step,
+  shifts in decimated samples, L_r = floor(T/dec_r) - max shift;
+* dedispersion, boxcar SNR and thresholded local maxima as in the C header;
+* candidate fragility: a candidate whose decision hinges on a margin smaller
+  than the FP32/FP64 disagreement allowed for the GPU path is flagged so that
+  list comparisons can exclude it on both sides.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "aa_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+# Margins that make a candidate "fragile" (FP32 GPU vs FP64 oracle may decide
+# differently): distance of B to the threshold, and the margins of the local
+# maximum comparisons and of the width argmax.
+FRAGILE_THR = 1e-3
+FRAGILE_CMP = 2e-4
+
+
+def build(force: bool = False) -> str:
+    """Compile aa_oracle.c into liboracle.so next to it (gcc, OpenMP)."""
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+        return _LIB
+    cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC",
+           "-shared", "-o", _LIB + ".tmp", _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(_LIB + ".tmp", _LIB)
+    return _LIB
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_LIB)
+        i32, i64, f64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+        vp = ctypes.c_void_p
+        L.oracle_set_threads.argtypes = [ctypes.c_int]
+        L.oracle_set_threads.restype = ctypes.c_int
+        L.oracle_f_top.argtypes = [f64, f64, i32]
+        L.oracle_f_top.restype = f64
+        L.oracle_shifts.argtypes = [i32, f64, f64, f64, f64, i32, vp]
+        L.oracle_shifts.restype = i32
+        L.oracle_decimate.argtypes = [vp, i32, i64, i64, i32, vp, i64]
+        L.oracle_decimate.restype = None
+        L.oracle_dedisperse.argtypes = [vp, i32, i32, i64, vp, i64, i64, vp]
+        L.oracle_dedisperse.restype = None
+        L.oracle_moments.argtypes = [vp, i64, ctypes.POINTER(f64), ctypes.POINTER(f64)]
+        L.oracle_moments.restype = None
+        L.oracle_boxcar.argtypes = [vp, i64, f64, f64, i32, i64, i64, vp, vp, vp]
+        L.oracle_boxcar.restype = None
+        L.oracle_peaks.argtypes = [vp, i64, f64, vp, i64]
+        L.oracle_peaks.restype = i64
+        _lib = L
+    return _lib
+
+
+def set_threads(n: int = 0) -> int:
+    """Set the OpenMP thread count (0 = leave as is); returns the count in use."""
+    return int(lib().oracle_set_threads(int(n)))
+
+
+def _ptr(a: np.ndarray) -> int:
+    return a.ctypes.data
+
+
+# ----------------------------------------------------------------------------
+# Plan
+# ----------------------------------------------------------------------------
+
+def shifts(nchans: int, fch1: float, foff: float, tsamp: float, dm: float, dec: int = 1):
+    """Per-channel integer delays for one DM, in decimated samples."""
+    out = np.empty(nchans, dtype=np.int32)
+    lib().oracle_shifts(nchans, fch1, foff, tsamp, float(dm), int(dec), _ptr(out))
+    return out
+
+
+def shifts_near_half(nchans, fch1, foff, tsamp, dm, dec=1) -> int:
+    out = np.empty(nchans, dtype=np.int32)
+    return int(lib().oracle_shifts(nchans, fch1, foff, tsamp, float(dm), int(dec), _ptr(out)))
+
+
+@dataclass
+class OracleRange:
+    dm_lo: float
+    dm_step: float
+    ndm: int
+    dec: int
+    dms: np.ndarray = field(repr=False)
+    shifts: np.ndarray = field(repr=False)  # [ndm][nchans] int32
+    maxshift: int = 0
+    nsamp_dec: int = 0
+    length: int = 0
+    dm_offset: int = 0
+
+
+def plan(nchans, fch1, foff, tsamp, ranges, nsamp):
+    """Per-range DM list, shift table, max shift and output length."""
+    out = []
+    off = 0
+    for (dm_lo, dm_step, ndm, dec) in ranges:
+        dms = np.array([dm_lo + i * dm_step for i in range(ndm)], dtype=np.float64)
+        tab = np.stack([shifts(nchans, fch1, foff, tsamp, d, dec) for d in dms]) if ndm else \
+            np.zeros((0, nchans), np.int32)
+        ms = int(tab.max()) if ndm else 0
+        nd = nsamp // dec
+        out.append(OracleRange(dm_lo, dm_step, ndm, dec, dms, tab, ms, nd, max(0, nd - ms), off))
+        off += ndm
+    return out
+
+
+# ----------------------------------------------------------------------------
+# Dedispersion
+# ----------------------------------------------------------------------------
+
+def decimate(x: np.ndarray, dec: int) -> np.ndarray:
+    """uint8 [C][T] -> uint16 [C][T//dec], summing dec samples."""
+    x = np.ascontiguousarray(x, dtype=np.uint8)
+    C, T = x.shape
+    nd = T // dec
+    out = np.empty((C, nd), dtype=np.uint16)
+    lib().oracle_decimate(_ptr(x), C, T, T, int(dec), _ptr(out), nd)
+    return out
+
+
+def dedisperse_row(xr: np.ndarray, shift_row: np.ndarray, t0: int, t1: int) -> np.ndarray:
+    """y[t] for t in [t0, t1) of one DM trial; xr is uint8 or uint16 [C][T_r]."""
+    xr = np.ascontiguousarray(xr)
+    assert xr.dtype in (np.uint8, np.uint16)
+    C, Tr = xr.shape
+    sh = np.ascontiguousarray(shift_row, dtype=np.int32)
+    assert t0 >= 0 and t1 >= t0
+    if t1 > t0:
+        assert t1 - 1 + int(sh.max()) < Tr, "window reads past the end of the series"
+    out = np.zeros(max(0, t1 - t0), dtype=np.int64)
+    lib().oracle_dedisperse(_ptr(xr), xr.itemsize, C, Tr, _ptr(sh), int(t0), int(t1), _ptr(out))
+    return out
+
+
+def range_input(x: np.ndarray, dec: int) -> np.ndarray:
+    return np.ascontiguousarray(x, dtype=np.uint8) if dec == 1 else decimate(x, dec)
+
+
+def dedisperse(x, nchans, fch1, foff, tsamp, ranges, rows=None):
+    """Full dedispersion: list (per range) of int64 [ndm_r][L_r] (or the listed rows)."""
+    C, T = x.shape
+    assert C == nchans
+    pl = plan(nchans, fch1, foff, tsamp, ranges, T)
+    res = []
+    for r, rg in enumerate(pl):
+        xr = range_input(x, rg.dec)
+        sel = range(rg.ndm) if rows is None else rows[r]
+        res.append(np.stack([dedisperse_row(xr, rg.shifts[i], 0, rg.length) for i in sel])
+                   if len(sel) else np.zeros((0, rg.length), np.int64))
+    return pl, res
+
+
+# ----------------------------------------------------------------------------
+# Single-pulse search
+# ----------------------------------------------------------------------------
+
+def moments(y: np.ndarray):
+    y = np.ascontiguousarray(y, dtype=np.int64)
+    mu, sg = ctypes.c_double(), ctypes.c_double()
+    lib().oracle_moments(_ptr(y), y.size, ctypes.byref(mu), ctypes.byref(sg))
+    return mu.value, sg.value
+
+
+def boxcar(y: np.ndarray, mu: float, sigma: float, W: int, t0: int = 0, t1: int | None = None):
+    """(B, wbest, margin) for t in [t0, t1)."""
+    y = np.ascontiguousarray(y, dtype=np.int64)
+    n = y.size
+    t1 = n if t1 is None else t1
+    m = max(0, t1 - t0)
+    B = np.empty(m, np.float64)
+    wb = np.empty(m, np.int32)
+    mg = np.empty(m, np.float64)
+    if m:
+        lib().oracle_boxcar(_ptr(y), n, float(mu), float(sigma), int(W), int(t0), int(t1),
+                            _ptr(B), _ptr(wb), _ptr(mg))
+    return B, wb, mg
+
+
+def peaks_thr(B: np.ndarray, thr: float) -> np.ndarray:
+    B = np.ascontiguousarray(B, dtype=np.float64)
+    out = np.empty(B.size, np.int64)
+    n = lib().oracle_peaks(_ptr(B), B.size, float(thr), _ptr(out), B.size)
+    return out[:n].copy()
+
+
+@dataclass
+class Candidate:
+    dm_index: int  # global DM-trial index (ranges concatenated)
+    t: int         # sample index in that range's (decimated) series
+    width: int     # boxcar width in samples of that range
+    range: int
+    snr: float
+    fragile: bool = False
+
+
+def search_row(y: np.ndarray, W: int, thr: float, dm_index: int, rng: int,
+               t_lo: int = 0, t_hi: int | None = None):
+    """Candidates of one DM series with t in [t_lo, t_hi).
+
+    Returns (candidates, B, wbest, mu, sigma) with B/wbest over [t_lo, t_hi).
+    Rows with sigma == 0 have B = 0 and no candidates.  Near-decision entries
+    (|B - thr| < FRAGILE_THR, neighbour or width-argmax margin < FRAGILE_CMP)
+    are flagged fragile; entries just below the threshold that could flip
+    into the list are returned as fragile too.
+    """
+    y = np.ascontiguousarray(y, dtype=np.int64)
+    n = y.size
+    t_hi = n if t_hi is None else min(t_hi, n)
+    mu, sigma = moments(y)
+    a, b = max(0, t_lo - 1), min(n, t_hi + 1)
+    B, wb, mg = boxcar(y, mu, sigma, W, a, b)
+    cands = []
+    if sigma == 0.0 or t_hi <= t_lo:
+        return cands, B[t_lo - a:t_hi - a], wb[t_lo - a:t_hi - a], mu, sigma
+    for t in range(t_lo, t_hi):
+        k = t - a
+        v = B[k]
+        if v < thr - FRAGILE_THR:
+            continue
+        left = B[k - 1] if t > 0 else -np.inf
+        right = B[k + 1] if t + 1 < n else -np.inf
+        is_peak = v >= thr and v > left and v >= right
+        near = (abs(v - thr) < FRAGILE_THR or abs(v - left) < FRAGILE_CMP
+                or abs(v - right) < FRAGILE_CMP)
+        if is_peak or near:
+            fragile = near or mg[k] < FRAGILE_CMP
+            cands.append(Candidate(dm_index, t, int(wb[k]), rng, float(v), bool(fragile)))
+    return cands, B[t_lo - a:t_hi - a], wb[t_lo - a:t_hi - a], mu, sigma

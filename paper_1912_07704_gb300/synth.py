@@ -1,0 +1,148 @@
+"""Seeded synthetic filterbanks standing in for simulated SKA-like data.
+
+The paper evaluates on "simulated SKA-like data" (abstract, Sec. 1) that is not
+published; these generators produce data of that shape instead:
+
+* noise: round(N(128, 16^2)) clipped to [0, 255], uint8, channels x time;
+* dispersed box pulses: amplitude A added to the noise (before rounding and
+  clipping) on samples [t0 + d_c, t0 + d_c + n_w) of every channel c.
+
+The per-channel pulse delays d_c are INPUTS: this module computes no
+dispersion delay and holds none of the search arithmetic.  Callers obtain the
+delays from their own side (the library's plan in bench.py, the oracle in
+tests).  Everything is seeded: torch.Generator for the noise (on the device
+the data is made on), numpy PCG64 for the pulse parameters.
+
+Workload presets mirror the configurations the library is measured on.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+from typing import Callable, Sequence
+
+import numpy as np
+import torch
+
+DATA_SEED = 1912
+PULSE_SEED = 7704
+
+
+@dataclass(frozen=True)
+class Workload:
+    name: str
+    nchans: int
+    fch1: float
+    foff: float
+    tsamp: float
+    nsamp: int
+    ranges: tuple  # ((dm_lo, dm_step, ndm, dec), ...)
+    max_width: int
+    threshold: float
+    index: int  # 0-based position among the presets (seeds are offset by it)
+
+    @property
+    def data_seed(self) -> int:
+        return DATA_SEED + self.index
+
+    @property
+    def pulse_seed(self) -> int:
+        return PULSE_SEED + self.index
+
+
+# 256 channels, 32768 samples, DM 0..255 step 1, widths 1..32, threshold 6.
+PLAIN_256 = Workload("plain-256ch-32768", 256, 1500.0, -1.171875, 64e-6, 32768,
+                     ((0.0, 1.0, 256, 1),), 32, 6.0, 0)
+# 4096 channels, 2^20 samples, four DM ranges with decimation 1/2/4/8,
+# widths 1..8192, threshold 6.
+SKA_4096 = Workload("ska-4096ch-2^20", 4096, 1508.0, -0.0732421875, 64e-6, 1 << 20,
+                    ((0.0, 0.1, 1500, 1), (150.0, 0.2, 750, 2), (300.0, 0.5, 600, 4),
+                     (600.0, 1.0, 1400, 8)), 8192, 6.0, 1)
+
+
+@dataclass
+class Pulse:
+    dm: float
+    t0: int        # arrival sample at the top of the band
+    n_w: int       # width in full-rate samples
+    amplitude: float
+
+
+def pulses_single(dm=150.0, t0=8192, n_w=16, amplitude=40.0) -> list:
+    """The single 1 ms, +40 count pulse of the 256-channel workload."""
+    return [Pulse(dm, t0, n_w, amplitude)]
+
+
+def pulses_ska(w: Workload, max_delay: Callable[[float], int], n: int = 20) -> list:
+    """n pulses: DM ~ U[50, 2000], width log-uniform 64 us .. 16 ms,
+    A ~ U[1, 4] counts, start times evenly spaced with jitter so that no two
+    pulses overlap and every pulse ends before the series does.
+
+    max_delay(dm) must return the largest per-channel delay (full-rate
+    samples) of a pulse at that DM; it is supplied by the caller.
+    """
+    rng = np.random.Generator(np.random.PCG64(w.pulse_seed))
+    dms = rng.uniform(50.0, 2000.0, n)
+    widths_s = np.exp(rng.uniform(np.log(64e-6), np.log(16e-3), n))
+    amps = rng.uniform(1.0, 4.0, n)
+    n_w = np.maximum(1, np.rint(widths_s / w.tsamp)).astype(np.int64)
+    slot = w.nsamp // n
+    out = []
+    for i in range(n):
+        span = int(max_delay(float(dms[i]))) + int(n_w[i])
+        room = slot - span
+        base = i * slot
+        if room <= 0:
+            # the dispersed pulse does not fit its slot: keep it at the slot start
+            t0 = base
+        else:
+            t0 = base + int(rng.integers(0, room))
+        if t0 + span >= w.nsamp:
+            continue
+        out.append(Pulse(float(dms[i]), int(t0), int(n_w[i]), float(amps[i])))
+    return out
+
+
+def make_filterbank(w: Workload, pulses: Sequence[Pulse],
+                    delays: Callable[[float], np.ndarray],
+                    device="cpu", pitch: int | None = None,
+                    chunk_channels: int = 256) -> torch.Tensor:
+    """uint8 tensor [nchans][pitch] (first nsamp columns valid, the rest 0).
+
+    delays(dm) -> int array [nchans] of per-channel delays in full-rate
+    samples (caller-supplied).
+    """
+    C, T = w.nchans, w.nsamp
+    pitch = T if pitch is None else pitch
+    assert pitch >= T
+    dev = torch.device(device)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(w.data_seed)
+    out = torch.zeros((C, pitch), dtype=torch.uint8, device=dev)
+    pul = [(p, np.asarray(delays(p.dm), dtype=np.int64)) for p in pulses]
+    for c0 in range(0, C, chunk_channels):
+        c1 = min(C, c0 + chunk_channels)
+        v = torch.randn((c1 - c0, T), generator=gen, device=dev, dtype=torch.float32)
+        v.mul_(16.0).add_(128.0)
+        for p, d in pul:
+            rows = np.repeat(np.arange(c1 - c0, dtype=np.int64), p.n_w)
+            cols = (np.repeat(p.t0 + d[c0:c1], p.n_w)
+                    + np.tile(np.arange(p.n_w, dtype=np.int64), c1 - c0))
+            keep = cols < T
+            if keep.any():
+                ri = torch.from_numpy(rows[keep]).to(dev)
+                ci = torch.from_numpy(cols[keep]).to(dev)
+                val = torch.full((ri.numel(),), float(p.amplitude), device=dev)
+                v.index_put_((ri, ci), val, accumulate=True)
+        v.round_().clamp_(0.0, 255.0)
+        out[c0:c1, :T] = v.to(torch.uint8)
+    return out
+
+
+def noise_filterbank(nchans: int, nsamp: int, seed: int, device="cpu",
+                     mean=128.0, std=16.0) -> torch.Tensor:
+    """Plain seeded noise, uint8 [nchans][nsamp]."""
+    dev = torch.device(device)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(seed)
+    v = torch.randn((nchans, nsamp), generator=gen, device=dev, dtype=torch.float32)
+    return v.mul_(std).add_(mean).round_().clamp_(0.0, 255.0).to(torch.uint8)
