@@ -1,0 +1,375 @@
+"""Throughput of the dedispersion + single-pulse-search hot path.
+
+One step = decimation + dedispersion of every DM range + the single-pulse
+search (statistics, exhaustive boxcar widths 1..W, peak finding, widths) on
+the 4096-channel, 2^20-sample (67.1 s) SKA-like plan (4250 DM trials over four
+ranges with decimation 1/2/4/8, W = 8192), input resident in HBM.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  With torchrun (N > 1) every rank searches its
+own beam (independent data, same plan; weak scaling, no data-path
+collective); value = all ranks' DM-trial samples / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DM-trial samples/s (4096-ch SKA-like plan, dedispersion + single-pulse search)"
+UNIT = "DM-trial samples/s"
+SM_COUNT = 152
+SM_MAX_MHZ_DEFAULT = 2070.0
+# Minimal lane instructions per boxcar width-sample on sm_103a: running-sum
+# add, normalising FMA, and half of a three-input max.
+BOXCAR_OPS_PER_WS = 2.5
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def load_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f".clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        try:
+            os.remove(self.path)
+        except OSError:
+            pass
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i, v in enumerate(r) if v == "Active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows),
+                "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons,
+                "samples": len(rows)}
+
+
+def build_input(plan, w, device):
+    """Seeded synthetic filterbank on the device (pulse delays from the
+    library's own plan arithmetic, one single-DM plan per pulse)."""
+    from paper_1912_07704_gb300 import synth
+    from paper_1912_07704_gb300.api import Plan
+
+    def delays(dm):
+        with Plan(w.nchans, w.fch1, w.foff, w.tsamp, [(float(dm), 0.0, 1, 1)]) as p1:
+            return p1.shifts(0)[0]
+
+    pulses = synth.pulses_ska(w, lambda dm: int(delays(dm).max()))
+    pitch = plan.query(w.nsamp).in_pitch_min
+    return synth.make_filterbank(w, pulses, delays, device=device, pitch=pitch)
+
+
+def workload_algorithmics(plan, w):
+    lay = plan.layout(w.nsamp)
+    dm_samples = sum(g.ndm * g.length for g in lay)
+    adds = {}
+    for g in lay:
+        key = "dedisperse_u8" if g.dec == 1 else "dedisperse_u16"
+        adds[key] = adds.get(key, 0) + g.ndm * g.length * w.nchans
+    # width-samples: sum over rows and start times of min(W, L - t)
+    ws = 0
+    for g in lay:
+        L, W = g.length, w.max_width
+        full = max(0, L - W + 1) * W
+        tail = sum(range(1, min(W, L)))  # t > L-W: L-t widths
+        ws += g.ndm * (full + tail)
+    in_bytes = w.nchans * w.nsamp
+    dd_bytes = 4 * dm_samples
+    return dict(dm_samples=dm_samples, adds=adds, width_samples=ws, in_bytes=in_bytes,
+                dd_bytes=dd_bytes, lay=lay)
+
+
+def run_oracle_sample(w, x_host, rows_per_range: int, threads: int):
+    """Oracle (CPU) on a bounded sample: `rows_per_range` full-length DM trials
+    of every range (decimated inputs prepared outside the timed part and
+    amortised over all trials).  Returns (DM-trial samples, seconds, cores, desc)."""
+    from oracle import oracle as o
+    cores = o.set_threads(threads)
+    pl = o.plan(w.nchans, w.fch1, w.foff, w.tsamp, w.ranges, w.nsamp)
+    t_dec = 0.0
+    inputs = []
+    for g in pl:
+        t = time.perf_counter()
+        inputs.append(o.range_input(x_host, g.dec))
+        t_dec += time.perf_counter() - t
+    ntrials = sum(g.ndm for g in pl)
+    samples, t_rows, nrows = 0, 0.0, 0
+    for g, xr in zip(pl, inputs):
+        idx = np.linspace(0, g.ndm - 1, rows_per_range).round().astype(int)
+        for i in idx:
+            t = time.perf_counter()
+            y = o.dedisperse_row(xr, g.shifts[i], 0, g.length)
+            o.search_row(y, w.max_width, w.threshold, g.dm_offset + int(i), 0)
+            t_rows += time.perf_counter() - t
+            samples += g.length
+            nrows += 1
+    secs = t_rows + t_dec * nrows / ntrials
+    desc = (f"{rows_per_range} full-length DM trials per range ({nrows} of {ntrials}), "
+            f"decimation time amortised over all trials")
+    return samples, secs, cores, desc
+
+
+def bench_reference(args):
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return
+    from paper_1912_07704_gb300 import synth
+    import torch
+    w = synth.SKA_4096
+    from oracle import oracle as o
+    d1 = lambda dm: o.shifts(w.nchans, w.fch1, w.foff, w.tsamp, dm, 1)
+    pulses = synth.pulses_ska(w, lambda dm: int(d1(dm).max()))
+    x = synth.make_filterbank(w, pulses, d1, device="cpu").numpy()
+    threads = os.cpu_count() or 1
+    for _ in range(args.warmup):
+        run_oracle_sample(w, x, 1, threads)
+    tot_s, tot_t, cores, desc = 0, 0.0, 1, ""
+    for _ in range(args.steps):
+        s, t, cores, desc = run_oracle_sample(w, x, 1, threads)
+        tot_s += s
+        tot_t += t
+    v = tot_s / tot_t
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": w.name, "sample": desc},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def bench_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_1912_07704_gb300 import abi, synth
+    from paper_1912_07704_gb300.api import Plan, candidates_from_device
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("gloo")
+    w = synth.SKA_4096
+    plan = Plan.from_workload(w)
+    plan.bind(local)
+    info = plan.query(w.nsamp, w.max_width)
+    x = build_input(plan, w, "cuda")
+    if ws > 1:  # independent beam per rank: perturb the data deterministically
+        x[:, : w.nsamp].add_(rank).clamp_(max=255)
+    nsamp = w.nsamp
+    out = plan.alloc_output(nsamp)
+    ws_dd = plan.alloc_workspace(info.dedisp_ws_bytes)
+    ws_sps = plan.alloc_workspace(info.sps_ws_bytes)
+    cap = 1 << 20
+    cands = torch.empty(cap * 16, dtype=torch.uint8, device="cuda")
+    count = torch.zeros(1, dtype=torch.int64, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        plan.dedisperse_device(x, nsamp, out=out, ws=ws_dd)
+        plan.sps_search_device(out, nsamp, w.max_width, w.threshold, cap, ws=ws_sps,
+                               cands=cands, count=count)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    alg = workload_algorithmics(plan, w)
+    clocks = ClockSampler(local)
+    if ws > 1:
+        dist.barrier()
+    clocks.start()
+    abi.aa_profile_enable(True)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    abi.aa_profile_enable(False)
+    prof = abi.profile_snapshot()
+    clk = clocks.stop()
+    t = ev0.elapsed_time(ev1) / 1e3
+    if ws > 1:
+        tt = torch.tensor([t], dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt.item())
+    ncand = int(count.item())
+    value = alg["dm_samples"] * args.steps * ws / t
+    step_s = t / args.steps
+    launches = sum(v[0] for v in prof.values())
+
+    # end to end through the host-buffer C-ABI path (pinned host input)
+    e2e = None
+    if not args.no_e2e:
+        host = torch.empty((w.nchans, nsamp), dtype=torch.uint8, pin_memory=True)
+        host.copy_(x[:, :nsamp])
+        hn = host.numpy()
+        for _ in range(1):
+            dd = plan.dedisperse(hn)
+            plan.sps_search(dd, w.max_width, w.threshold, cap)
+            dd.close()
+        torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        d2h = 0
+        for _ in range(args.steps):
+            dd = plan.dedisperse(hn)
+            arr, total = plan.sps_search(dd, w.max_width, w.threshold, cap)
+            dd.close()
+            d2h += 8 + arr.nbytes
+        torch.cuda.synchronize()
+        te = time.perf_counter() - t0
+        if ws > 1:
+            tt = torch.tensor([te], dtype=torch.float64)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            te = float(tt.item())
+        e2e = {"value": alg["dm_samples"] * args.steps * ws / te, "unit": UNIT,
+               "h2d_bytes_per_step": w.nchans * nsamp,
+               "d2h_bytes_per_step": int(d2h / args.steps)}
+
+    # roofline of the dominant kernel, from the live event timings
+    peaks = load_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", SM_MAX_MHZ_DEFAULT))
+    lane_peak = SM_COUNT * 128 * sm_max * 1e6  # lane instructions / s
+    kern = {}
+    for name, (n, ms) in prof.items():
+        if n:
+            kern[name] = {"launches": n, "ms_per_step": ms / args.steps,
+                          "share": ms / max(1e-9, sum(v[1] for v in prof.values()))}
+    box_s = prof["sps_boxcar"][1] / 1e3 / args.steps
+    u8_s = prof["dedisperse_u8"][1] / 1e3 / args.steps
+    u16_s = prof["dedisperse_u16"][1] / 1e3 / args.steps
+    if box_s > 0:
+        kern["sps_boxcar"]["gws_per_s"] = alg["width_samples"] / box_s / 1e9
+    for key, s in (("dedisperse_u8", u8_s), ("dedisperse_u16", u16_s)):
+        if s > 0:
+            kern[key]["gadds_per_s"] = alg["adds"][key] / s / 1e9
+    dominant = max(kern, key=lambda k: kern[k]["ms_per_step"])
+    if dominant == "sps_boxcar":
+        achieved = BOXCAR_OPS_PER_WS * alg["width_samples"] / box_s
+        roof = {"kernel": "sps_boxcar", "bound": "alu", "achieved": achieved / 1e9,
+                "peak": lane_peak / 1e9, "unit": "Gop/s", "frac": achieved / lane_peak,
+                "traffic": None,
+                "ops": f"{BOXCAR_OPS_PER_WS} lane instructions per width-sample; peak = "
+                       f"{SM_COUNT} SMs x 128 lanes x {sm_max:.0f} MHz"}
+    else:
+        key = dominant
+        s = kern[key]["ms_per_step"] / 1e3
+        achieved = alg["adds"].get(key, 0) / s
+        roof = {"kernel": key, "bound": "alu", "achieved": achieved / 1e9,
+                "peak": lane_peak / 1e9, "unit": "Gop/s", "frac": achieved / lane_peak,
+                "traffic": None, "ops": "channel-adds; peak = 1 add per lane per clock"}
+    hbm = float(peaks.get("hbm_gbs", 6678.2))
+    eff_in_gbs = alg["dm_samples"] * w.nchans / step_s / 1e9
+
+    cpu = None
+    if not args.no_cpu_baseline and rank == 0 and ws == 1:
+        xh = x[:, :nsamp].cpu().numpy()
+        s, secs, cores, desc = run_oracle_sample(w, xh, 1, os.cpu_count() or 1)
+        cpu = {"value": s / secs, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * step_s, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u8->int32 (dedispersion), f32 (SNR)",
+            "data": "synthetic",
+            "config": {"workload": w.name, "nchans": w.nchans, "nsamp": w.nsamp,
+                       "dm_trials": sum(g.ndm for g in alg["lay"]), "max_width": w.max_width,
+                       "threshold": w.threshold, "parallelism": f"beams x{ws}",
+                       "l2": "inputs larger than L2 (4.29 GB filterbank, 9.18 GB dedispersed)"},
+            "rtf": (w.nsamp * w.tsamp) / step_s,
+            "hbm": {"effective_input_gbs": eff_in_gbs, "frac_of_measured": eff_in_gbs / hbm,
+                    "algorithmic_gbs": (alg["in_bytes"] + alg["dd_bytes"]) / step_s / 1e9,
+                    "peak_gbs": hbm},
+            "roofline": roof,
+            "kernels": kern,
+            "candidates": ncand,
+            "gpu_launches": launches,
+            "clocks": clk,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        bench_reference(args)
+    else:
+        bench_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,294 @@
+/*
+ * aa_dedisp.h -- C ABI of the GB300 (sm_103a) brute-force dedispersion and
+ * single-pulse search library (libaa_gb300.so).
+ *
+ * Pipeline (arXiv:1912.07704, Sec. 1): dedisperse a uint8 filterbank
+ * (channels x time) over a multi-range DM plan with per-range time
+ * decimation, then run the single-pulse search (boxcar filters + peak
+ * finding) on every dedispersed series, keeping the data on the GPU between
+ * the two stages.
+ *
+ * API shape follows the paper's design:
+ *   - a plan carries the search parameters and metadata; the library derives
+ *     from it an immutable, queryable strategy (Sec. 3.1, 3.2);
+ *   - configuration is separate from device memory: every device buffer the
+ *     library will use can be queried before anything is allocated
+ *     (Sec. 2.3);
+ *   - the caller owns the host input and the library never writes it; the
+ *     library owns the device buffers and the results it returns (Sec. 2.4);
+ *   - every call returns a status code; configuration errors are reported,
+ *     never thrown (Sec. 3.1, 3.3).
+ *
+ * Method (brute force, exact integers):
+ *   f_c      = fch1 + c*foff (MHz),  f_top = highest channel frequency
+ *   DM_i     = dm_lo + i*dm_step           (double; not accumulated)
+ *   s_r(c,i) = round_half_away(((4.148808e3*DM_i)*(f_c^-2 - f_top^-2))
+ *                              / (tsamp*dec_r))   (decimated samples; double)
+ *   x_r[c][j]= sum_{k<dec_r} x[c][j*dec_r+k],  j < floor(T/dec_r)
+ *   y_r[i][t]= sum_c x_r[c][t + s_r(c,i)],      t < L_r = floor(T/dec_r) - max s_r
+ *   SNR_w(t) = (sum_{k<w} y[t+k] - w*mu) / (sigma*sqrt(w)),  1 <= w <= min(W, L_r-t)
+ *              (mu, sigma: population mean/std of that series)
+ *   B(t)     = max_w SNR_w(t);  candidate iff B(t) >= thr, B(t) > B(t-1),
+ *              B(t) >= B(t+1) (missing neighbours are -inf).
+ *   A series with sigma == 0 yields no candidates.
+ *
+ * Threading: a plan may be used from one host thread at a time.  Device
+ * calls are stream-ordered on the given stream (NULL = legacy default).
+ */
+#ifndef AA_DEDISP_H
+#define AA_DEDISP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t. */
+typedef struct CUstream_st* aa_stream_t;
+
+/* Status codes (Sec. 3.3: every iteration/call reports success, pending work
+ * or an error). */
+typedef enum aa_status {
+    AA_OK = 0,
+    AA_PENDING = 1,             /* streaming: chunk accepted, more input needed */
+    AA_WARN_CAND_OVERFLOW = 2,  /* more candidates than capacity; the count holds
+                                   the true total, the first `capacity` stored
+                                   (which ones is unspecified) */
+    AA_ERR_CONFIG = -1,         /* invalid plan description */
+    AA_ERR_NOMEM = -2,          /* device or host allocation failed */
+    AA_ERR_CUDA = -3,           /* a CUDA runtime call failed */
+    AA_ERR_TIMEOUT = -4,        /* a bounded device-side wait gave up */
+    AA_ERR_STATE = -5,          /* call not valid in the object's current state */
+    AA_ERR_ARG = -6             /* invalid argument (NULL, size, alignment) */
+} aa_status;
+
+/* Static string for a status code (never NULL). */
+const char* aa_status_str(aa_status s);
+
+/* Human-readable detail of the last failing call on this host thread
+ * (empty string if none).  Valid until the next library call on the thread. */
+const char* aa_last_error(void);
+
+/* ------------------------------------------------------------------ plan -- */
+
+/* One DM range: ndm trials DM_i = dm_lo + i*dm_step, searched on the input
+ * decimated (summed) by `dec` in time.  Requirements: ndm >= 1, dm_lo >= 0,
+ * dm_step >= 0, 1 <= dec <= 16. */
+typedef struct aa_dm_range {
+    double dm_lo;
+    double dm_step;
+    int32_t ndm;
+    int32_t dec;
+} aa_dm_range;
+
+/* Plan description (Sec. 3.1 "plan": search parameters and metadata).
+ * nchans >= 1; fch1_mhz > 0 and every channel frequency > 0; foff_mhz != 0;
+ * tsamp_s > 0; 1 <= nranges <= 64; nchans*255*max(dec) < 2^24 (so that every
+ * dedispersed sample is an exact integer in FP32).  `ranges` is read during
+ * aa_plan_create only (the caller keeps ownership). */
+typedef struct aa_plan_desc {
+    int32_t nchans;
+    double fch1_mhz;
+    double foff_mhz;
+    double tsamp_s;
+    int32_t nranges;
+    const aa_dm_range* ranges;
+} aa_plan_desc;
+
+typedef struct aa_plan aa_plan;
+
+/* Validate `desc`, build the FP64 delay tables and the strategy (tile shapes,
+ * shared-memory sizes).  Host only: no device memory is touched.
+ * Returns AA_ERR_ARG if desc/out is NULL, AA_ERR_CONFIG (with
+ * aa_last_error() detail) if the description is invalid, AA_ERR_NOMEM on host
+ * allocation failure.  On failure *out is set to NULL. */
+aa_status aa_plan_create(const aa_plan_desc* desc, aa_plan** out);
+
+/* Release the plan and every device buffer it owns (delay tables).  NULL is a
+ * no-op.  Work using the plan must have completed. */
+void aa_plan_destroy(aa_plan* plan);
+
+/* Bind the plan to a CUDA device (Sec. 3.1 usage step 4): uploads the delay
+ * tables (device memory owned by the plan) and marks the plan ready.  Must be
+ * called before any device entry point; the high-level aa_dedisperse binds to
+ * the current device itself if needed.  Rebinding to another device is
+ * AA_ERR_STATE. */
+aa_status aa_plan_bind(aa_plan* plan, int device);
+
+/* Per-range layout for an input of `nsamp` full-rate samples. */
+typedef struct aa_range_info {
+    int32_t ndm;         /* trials in this range */
+    int32_t dec;         /* time decimation */
+    int32_t maxshift;    /* largest delay, decimated samples */
+    int32_t dm_offset;   /* global index of this range's first trial */
+    double dm_lo;
+    double dm_step;
+    int64_t nsamp_dec;   /* floor(nsamp/dec) */
+    int64_t length;      /* L = max(0, nsamp_dec - maxshift): output samples per trial */
+    int64_t pitch;       /* floats between consecutive output rows (multiple of 64) */
+    int64_t row_offset;  /* float offset of this range's row 0 in the output buffer */
+    /* strategy (fixed at aa_plan_create) */
+    int32_t tile_dms;        /* DM trials per dedispersion CTA */
+    int32_t tile_samples;    /* output samples per dedispersion CTA */
+    int32_t stage_channels;  /* channel rows per shared-memory stage */
+    int32_t stages;          /* pipeline depth of the staging copies */
+    int32_t span_max;        /* largest delay spread across one CTA's trials */
+    int32_t smem_bytes;      /* dynamic shared memory per dedispersion CTA */
+} aa_range_info;
+
+/* Strategy and memory requests for `nsamp` samples and boxcar widths up to
+ * `max_width` (0 if the single-pulse search will not be run).  Pure host
+ * computation (Sec. 2.3: memory is requested before it is allocated; Sec. 3.2:
+ * the strategy and the ready state can be queried). */
+typedef struct aa_plan_info {
+    int32_t nchans;
+    int32_t nranges;
+    int32_t ndm_total;
+    int32_t ready;             /* 1 once aa_plan_bind succeeded */
+    int32_t device;            /* bound device, -1 if none */
+    int32_t max_width;
+    int64_t nsamp;
+    int64_t in_pitch_min;      /* minimum device input row pitch, bytes (nsamp rounded up to 16) */
+    int64_t dd_elems;          /* floats in the dedispersed output buffer */
+    int64_t dedisp_ws_bytes;   /* scratch for aa_dedisperse_device */
+    int64_t sps_ws_bytes;      /* scratch for aa_sps_search_device at max_width */
+    int64_t table_bytes;       /* device delay tables owned by the plan */
+    int64_t host_path_bytes;   /* peak device bytes of aa_dedisperse + aa_sps_search */
+    int64_t dm_trial_samples;  /* sum over ranges of ndm * L */
+    double dm_max;             /* largest trial DM */
+} aa_plan_info;
+
+aa_status aa_plan_query(const aa_plan* plan, int64_t nsamp, int32_t max_width,
+                        aa_plan_info* info);
+
+/* Layout of range r (0 <= r < nranges) for `nsamp` samples. */
+aa_status aa_plan_range(const aa_plan* plan, int64_t nsamp, int32_t r, aa_range_info* info);
+
+/* Copy range r's delay table, int32 [ndm][nchans] row-major (decimated
+ * samples), into caller-owned host memory `out` (capacity `cap` elements). */
+aa_status aa_plan_shifts(const aa_plan* plan, int32_t r, int32_t* out, int64_t cap);
+
+/* ----------------------------------------------------- device entry points -- */
+
+/* Candidate record (16 bytes).  dm_index: global trial index (ranges
+ * concatenated in plan order); t: sample index in that range's decimated
+ * series (start of the boxcar window); width: boxcar width in samples of that
+ * series; range: range index; snr: B(t). */
+typedef struct aa_candidate {
+    uint32_t dm_index;
+    uint32_t t;
+    uint16_t width;
+    uint8_t range;
+    uint8_t reserved;
+    float snr;
+} aa_candidate;
+
+/* Dedisperse a device-resident filterbank.
+ *   d_in     : uint8 [nchans][in_pitch] device memory, first nsamp bytes of
+ *              each row valid; in_pitch % 16 == 0, in_pitch >= nsamp; base
+ *              16-byte aligned.  Read only.
+ *   d_out    : float [dd_elems] device memory (aa_plan_info.dd_elems);
+ *              range r, trial i, sample t is at row_offset_r + i*pitch_r + t
+ *              for t < L_r (exact integers); padding is left unwritten.
+ *   d_ws     : device scratch of ws_bytes >= dedisp_ws_bytes (may be NULL if
+ *              that is 0), 256-byte aligned.
+ * The plan must be bound.  Stream-ordered, asynchronous; returns
+ * AA_ERR_ARG/AA_ERR_STATE on bad arguments, AA_ERR_CUDA if a launch fails. */
+aa_status aa_dedisperse_device(const aa_plan* plan, const uint8_t* d_in, int64_t nsamp,
+                               int64_t in_pitch, float* d_out, void* d_ws, size_t ws_bytes,
+                               aa_stream_t stream);
+
+/* Single-pulse search over every dedispersed series in d_dd (layout as
+ * written by aa_dedisperse_device for the same nsamp).
+ *   max_width      : W >= 1, boxcar widths 1..W (in samples of each range);
+ *   threshold      : SNR threshold;
+ *   d_cands        : device array of cand_capacity records (may be NULL iff
+ *                    cand_capacity == 0);
+ *   d_count        : device uint64, set to the total number of candidates
+ *                    (may exceed cand_capacity); records are unordered;
+ *   d_snr_out      : optional float [dd_elems] device buffer receiving B(t)
+ *                    for every t < L_r (NULL to skip);
+ *   d_ws           : scratch of ws_bytes >= sps_ws_bytes for this max_width.
+ * Stream-ordered, asynchronous. */
+aa_status aa_sps_search_device(const aa_plan* plan, int64_t nsamp, const float* d_dd,
+                               int32_t max_width, float threshold, aa_candidate* d_cands,
+                               int64_t cand_capacity, unsigned long long* d_count,
+                               float* d_snr_out, void* d_ws, size_t ws_bytes,
+                               aa_stream_t stream);
+
+/* Read and clear the device error word kept at the start of a workspace used
+ * by the calls above (synchronises `stream`).  AA_OK, or AA_ERR_TIMEOUT if a
+ * bounded device-side wait gave up. */
+aa_status aa_workspace_status(void* d_ws, aa_stream_t stream);
+
+/* ------------------------------------------ host-buffer (API-owned) path -- */
+
+typedef struct aa_dd_result aa_dd_result;
+typedef struct aa_candidates aa_candidates;
+
+/* Copy the caller's host filterbank (uint8 [nchans][host_pitch], first nsamp
+ * bytes of each row valid; never written) to the device and dedisperse it.
+ * The result buffers are allocated and owned by the library (stream-ordered
+ * device allocations).  Returns once the host input has been read; the
+ * dedispersion runs asynchronously on `stream`.  Binds the plan to the current
+ * device if it is not bound. */
+aa_status aa_dedisperse(aa_plan* plan, const uint8_t* host_in, int64_t nsamp,
+                        int64_t host_pitch, aa_stream_t stream, aa_dd_result** out);
+
+/* Const view of a result: device pointer to the output buffer (layout of
+ * aa_dedisperse_device) and the nsamp it was computed for.  Valid until
+ * aa_dd_result_destroy. */
+aa_status aa_dd_result_view(const aa_dd_result* res, const float** d_out, int64_t* nsamp);
+
+/* Free a result (stream-ordered on the stream it was produced on).  NULL is a
+ * no-op. */
+void aa_dd_result_destroy(aa_dd_result* res);
+
+/* Run the single-pulse search on a result and bring the candidates to host
+ * memory owned by the library, sorted by (dm_index, t).  Blocks until done.
+ * Returns AA_WARN_CAND_OVERFLOW if more than cand_capacity were found. */
+aa_status aa_sps_search(aa_plan* plan, const aa_dd_result* dd, int32_t max_width,
+                        float threshold, int64_t cand_capacity, aa_stream_t stream,
+                        aa_candidates** out);
+
+/* Const view of a candidate list: host pointer, records stored, and the
+ * total found.  Valid until aa_candidates_destroy. */
+aa_status aa_candidates_view(const aa_candidates* c, const aa_candidate** host,
+                             int64_t* stored, int64_t* total);
+
+/* Free a candidate list.  NULL is a no-op. */
+void aa_candidates_destroy(aa_candidates* c);
+
+/* ------------------------------------------------------------- profiling -- */
+
+/* Kernel timing (tracing).  While enabled, every kernel the library launches
+ * is bracketed by two CUDA events recorded on the stream it is launched on.
+ * on = 1 clears the counters and starts recording; on = 0 stops. */
+aa_status aa_profile_enable(int32_t on);
+
+/* Launch count and summed device time (ms) of kernel id `kernel` since the
+ * last aa_profile_enable(1); waits for the recorded events.  Ids run from 0
+ * while aa_profile_kernel_name(id) != NULL.  AA_ERR_ARG for a bad id. */
+aa_status aa_profile_read(int32_t kernel, int64_t* launches, double* total_ms);
+
+/* Static name of kernel id `kernel`, NULL past the last id. */
+const char* aa_profile_kernel_name(int32_t kernel);
+
+/* ------------------------------------------------------------ test hooks -- */
+
+/* Fault injection for tests of the bounded device-side waits; affects every
+ * later launch in the process.  what = 0: reset all hooks; what = 1: the
+ * dedispersion producer never issues the staging copy of channel chunk
+ * `value` (that stage's barrier never completes, so every CTA gives up after
+ * the wait limit, sets the workspace error word and exits without writing
+ * output); what = 2: set the wait limit to `value` nanoseconds (default 2 s).
+ * Returns AA_ERR_ARG for an unknown `what` or a non-positive limit. */
+aa_status aa_debug_inject(int32_t what, int64_t value);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AA_DEDISP_H */

@@ -238,11 +238,11 @@ def search_row(y: np.ndarray, W: int, thr: float, dm_index: int, rng: int,
     cands = []
     if sigma == 0.0 or t_hi <= t_lo:
         return cands, B[t_lo - a:t_hi - a], wb[t_lo - a:t_hi - a], mu, sigma
-    for t in range(t_lo, t_hi):
+    # only samples within FRAGILE_THR of the threshold or above can matter
+    near_idx = np.nonzero(B[t_lo - a:t_hi - a] >= thr - FRAGILE_THR)[0] + t_lo
+    for t in near_idx.tolist():
         k = t - a
         v = B[k]
-        if v < thr - FRAGILE_THR:
-            continue
         left = B[k - 1] if t > 0 else -np.inf
         right = B[k + 1] if t + 1 < n else -np.inf
         is_peak = v >= thr and v > left and v >= right

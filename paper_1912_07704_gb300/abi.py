@@ -1,0 +1,261 @@
+"""ctypes binding of include/aa_dedisp.h: one Python function per C entry
+point, same names, argument marshalling only.
+
+The shared library is loaded from this package directory (built by
+``paper_1912_07704_gb300.build``).  There is no fallback: if the library is
+missing or fails to load, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libaa_gb300.so")
+
+AA_OK = 0
+AA_PENDING = 1
+AA_WARN_CAND_OVERFLOW = 2
+AA_ERR_CONFIG = -1
+AA_ERR_NOMEM = -2
+AA_ERR_CUDA = -3
+AA_ERR_TIMEOUT = -4
+AA_ERR_STATE = -5
+AA_ERR_ARG = -6
+
+
+class aa_dm_range(ctypes.Structure):
+    _fields_ = [("dm_lo", ctypes.c_double), ("dm_step", ctypes.c_double),
+                ("ndm", ctypes.c_int32), ("dec", ctypes.c_int32)]
+
+
+class aa_plan_desc(ctypes.Structure):
+    _fields_ = [("nchans", ctypes.c_int32), ("fch1_mhz", ctypes.c_double),
+                ("foff_mhz", ctypes.c_double), ("tsamp_s", ctypes.c_double),
+                ("nranges", ctypes.c_int32), ("ranges", ctypes.POINTER(aa_dm_range))]
+
+
+class aa_range_info(ctypes.Structure):
+    _fields_ = [("ndm", ctypes.c_int32), ("dec", ctypes.c_int32), ("maxshift", ctypes.c_int32),
+                ("dm_offset", ctypes.c_int32), ("dm_lo", ctypes.c_double),
+                ("dm_step", ctypes.c_double), ("nsamp_dec", ctypes.c_int64),
+                ("length", ctypes.c_int64), ("pitch", ctypes.c_int64),
+                ("row_offset", ctypes.c_int64), ("tile_dms", ctypes.c_int32),
+                ("tile_samples", ctypes.c_int32), ("stage_channels", ctypes.c_int32),
+                ("stages", ctypes.c_int32), ("span_max", ctypes.c_int32),
+                ("smem_bytes", ctypes.c_int32)]
+
+
+class aa_plan_info(ctypes.Structure):
+    _fields_ = [("nchans", ctypes.c_int32), ("nranges", ctypes.c_int32),
+                ("ndm_total", ctypes.c_int32), ("ready", ctypes.c_int32),
+                ("device", ctypes.c_int32), ("max_width", ctypes.c_int32),
+                ("nsamp", ctypes.c_int64), ("in_pitch_min", ctypes.c_int64),
+                ("dd_elems", ctypes.c_int64), ("dedisp_ws_bytes", ctypes.c_int64),
+                ("sps_ws_bytes", ctypes.c_int64), ("table_bytes", ctypes.c_int64),
+                ("host_path_bytes", ctypes.c_int64), ("dm_trial_samples", ctypes.c_int64),
+                ("dm_max", ctypes.c_double)]
+
+
+class aa_candidate(ctypes.Structure):
+    _fields_ = [("dm_index", ctypes.c_uint32), ("t", ctypes.c_uint32),
+                ("width", ctypes.c_uint16), ("range", ctypes.c_uint8),
+                ("reserved", ctypes.c_uint8), ("snr", ctypes.c_float)]
+
+
+CANDIDATE_DTYPE = np.dtype([("dm_index", "<u4"), ("t", "<u4"), ("width", "<u2"),
+                            ("range", "u1"), ("reserved", "u1"), ("snr", "<f4")])
+assert CANDIDATE_DTYPE.itemsize == ctypes.sizeof(aa_candidate) == 16
+
+_P = ctypes.c_void_p
+_I32, _I64, _F32 = ctypes.c_int32, ctypes.c_int64, ctypes.c_float
+_SIG = {
+    "aa_status_str": (ctypes.c_char_p, [ctypes.c_int]),
+    "aa_last_error": (ctypes.c_char_p, []),
+    "aa_plan_create": (ctypes.c_int, [ctypes.POINTER(aa_plan_desc), ctypes.POINTER(_P)]),
+    "aa_plan_destroy": (None, [_P]),
+    "aa_plan_bind": (ctypes.c_int, [_P, ctypes.c_int]),
+    "aa_plan_query": (ctypes.c_int, [_P, _I64, _I32, ctypes.POINTER(aa_plan_info)]),
+    "aa_plan_range": (ctypes.c_int, [_P, _I64, _I32, ctypes.POINTER(aa_range_info)]),
+    "aa_plan_shifts": (ctypes.c_int, [_P, _I32, _P, _I64]),
+    "aa_dedisperse_device": (ctypes.c_int, [_P, _P, _I64, _I64, _P, _P, ctypes.c_size_t, _P]),
+    "aa_sps_search_device": (ctypes.c_int, [_P, _I64, _P, _I32, _F32, _P, _I64, _P, _P, _P,
+                                            ctypes.c_size_t, _P]),
+    "aa_workspace_status": (ctypes.c_int, [_P, _P]),
+    "aa_dedisperse": (ctypes.c_int, [_P, _P, _I64, _I64, _P, ctypes.POINTER(_P)]),
+    "aa_dd_result_view": (ctypes.c_int, [_P, ctypes.POINTER(_P), ctypes.POINTER(_I64)]),
+    "aa_dd_result_destroy": (None, [_P]),
+    "aa_sps_search": (ctypes.c_int, [_P, _P, _I32, _F32, _I64, _P, ctypes.POINTER(_P)]),
+    "aa_candidates_view": (ctypes.c_int, [_P, ctypes.POINTER(_P), ctypes.POINTER(_I64),
+                                          ctypes.POINTER(_I64)]),
+    "aa_candidates_destroy": (None, [_P]),
+    "aa_debug_inject": (ctypes.c_int, [_I32, _I64]),
+    "aa_profile_enable": (ctypes.c_int, [_I32]),
+    "aa_profile_read": (ctypes.c_int, [_I32, ctypes.POINTER(_I64), ctypes.POINTER(ctypes.c_double)]),
+    "aa_profile_kernel_name": (ctypes.c_char_p, [_I32]),
+}
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libaa_gb300.so (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -m paper_1912_07704_gb300.build` (needs nvcc)")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIG.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def exported_names() -> list:
+    return list(_SIG)
+
+
+class AAError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        detail = lib().aa_last_error().decode(errors="replace")
+        super().__init__(f"{where}: {status_str(status)}" + (f" ({detail})" if detail else ""))
+
+
+def status_str(s: int) -> str:
+    return lib().aa_status_str(int(s)).decode()
+
+
+def check(status: int, where: str, ok=(AA_OK,)) -> int:
+    if status not in ok:
+        raise AAError(status, where)
+    return status
+
+
+# -- thin wrappers: same names as the C entry points --------------------------
+
+def aa_status_str(s):
+    return status_str(s)
+
+
+def aa_last_error():
+    return lib().aa_last_error().decode(errors="replace")
+
+
+def aa_plan_create(desc: aa_plan_desc) -> int:
+    h = ctypes.c_void_p()
+    check(lib().aa_plan_create(ctypes.byref(desc), ctypes.byref(h)), "aa_plan_create")
+    return h.value
+
+
+def aa_plan_destroy(plan: int) -> None:
+    lib().aa_plan_destroy(plan)
+
+
+def aa_plan_bind(plan: int, device: int) -> None:
+    check(lib().aa_plan_bind(plan, int(device)), "aa_plan_bind")
+
+
+def aa_plan_query(plan: int, nsamp: int, max_width: int = 0) -> aa_plan_info:
+    info = aa_plan_info()
+    check(lib().aa_plan_query(plan, int(nsamp), int(max_width), ctypes.byref(info)), "aa_plan_query")
+    return info
+
+
+def aa_plan_range(plan: int, nsamp: int, r: int) -> aa_range_info:
+    info = aa_range_info()
+    check(lib().aa_plan_range(plan, int(nsamp), int(r), ctypes.byref(info)), "aa_plan_range")
+    return info
+
+
+def aa_plan_shifts(plan: int, r: int, ndm: int, nchans: int) -> np.ndarray:
+    out = np.empty((ndm, nchans), np.int32)
+    check(lib().aa_plan_shifts(plan, int(r), out.ctypes.data, out.size), "aa_plan_shifts")
+    return out
+
+
+def aa_dedisperse_device(plan, d_in, nsamp, in_pitch, d_out, d_ws, ws_bytes, stream) -> None:
+    check(lib().aa_dedisperse_device(plan, d_in, int(nsamp), int(in_pitch), d_out, d_ws,
+                                     int(ws_bytes), stream), "aa_dedisperse_device")
+
+
+def aa_sps_search_device(plan, nsamp, d_dd, max_width, threshold, d_cands, capacity, d_count,
+                         d_snr_out, d_ws, ws_bytes, stream) -> None:
+    check(lib().aa_sps_search_device(plan, int(nsamp), d_dd, int(max_width), float(threshold),
+                                     d_cands, int(capacity), d_count, d_snr_out, d_ws,
+                                     int(ws_bytes), stream), "aa_sps_search_device")
+
+
+def aa_workspace_status(d_ws, stream) -> int:
+    return lib().aa_workspace_status(d_ws, stream)
+
+
+def aa_dedisperse(plan, host_ptr, nsamp, host_pitch, stream) -> int:
+    h = ctypes.c_void_p()
+    check(lib().aa_dedisperse(plan, host_ptr, int(nsamp), int(host_pitch), stream,
+                              ctypes.byref(h)), "aa_dedisperse")
+    return h.value
+
+
+def aa_dd_result_view(res) -> tuple:
+    p, n = ctypes.c_void_p(), ctypes.c_int64()
+    check(lib().aa_dd_result_view(res, ctypes.byref(p), ctypes.byref(n)), "aa_dd_result_view")
+    return p.value, n.value
+
+
+def aa_dd_result_destroy(res) -> None:
+    lib().aa_dd_result_destroy(res)
+
+
+def aa_sps_search(plan, dd, max_width, threshold, capacity, stream) -> tuple:
+    h = ctypes.c_void_p()
+    st = check(lib().aa_sps_search(plan, dd, int(max_width), float(threshold), int(capacity),
+                                   stream, ctypes.byref(h)), "aa_sps_search",
+               ok=(AA_OK, AA_WARN_CAND_OVERFLOW))
+    return h.value, st
+
+
+def aa_candidates_view(c) -> tuple:
+    p, stored, total = ctypes.c_void_p(), ctypes.c_int64(), ctypes.c_int64()
+    check(lib().aa_candidates_view(c, ctypes.byref(p), ctypes.byref(stored), ctypes.byref(total)),
+          "aa_candidates_view")
+    return p.value, stored.value, total.value
+
+
+def aa_candidates_destroy(c) -> None:
+    lib().aa_candidates_destroy(c)
+
+
+def aa_debug_inject(what: int, value: int = 0) -> None:
+    check(lib().aa_debug_inject(int(what), int(value)), "aa_debug_inject")
+
+
+def aa_profile_enable(on: bool) -> None:
+    check(lib().aa_profile_enable(1 if on else 0), "aa_profile_enable")
+
+
+def aa_profile_read(kernel: int) -> tuple:
+    n, ms = ctypes.c_int64(), ctypes.c_double()
+    check(lib().aa_profile_read(int(kernel), ctypes.byref(n), ctypes.byref(ms)), "aa_profile_read")
+    return n.value, ms.value
+
+
+def aa_profile_kernel_name(kernel: int):
+    r = lib().aa_profile_kernel_name(int(kernel))
+    return None if r is None else r.decode()
+
+
+def profile_snapshot() -> dict:
+    """{kernel name: (launches, total ms)} for every library kernel."""
+    out, k = {}, 0
+    while True:
+        name = aa_profile_kernel_name(k)
+        if name is None:
+            return out
+        out[name] = aa_profile_read(k)
+        k += 1

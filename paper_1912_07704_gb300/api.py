@@ -1,0 +1,215 @@
+"""Pythonic face of the C ABI (torch supplies device memory and streams).
+
+Every computation runs in libaa_gb300.so; this module only allocates torch
+buffers of the sizes the plan requests (arXiv:1912.07704 Sec. 2.3: memory is
+requested before it is allocated) and passes raw pointers.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import abi
+
+
+def _stream_handle(stream=None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+@dataclass
+class RangeLayout:
+    ndm: int
+    dec: int
+    maxshift: int
+    dm_offset: int
+    dm_lo: float
+    dm_step: float
+    nsamp_dec: int
+    length: int
+    pitch: int
+    row_offset: int
+
+    @property
+    def dms(self) -> np.ndarray:
+        return np.array([self.dm_lo + i * self.dm_step for i in range(self.ndm)])
+
+
+class Plan:
+    """A bound-on-demand dedispersion + single-pulse search plan."""
+
+    def __init__(self, nchans: int, fch1: float, foff: float, tsamp: float, ranges):
+        ranges = [tuple(r) for r in ranges]
+        arr = (abi.aa_dm_range * len(ranges))(
+            *[abi.aa_dm_range(float(a), float(b), int(n), int(d)) for (a, b, n, d) in ranges])
+        desc = abi.aa_plan_desc(int(nchans), float(fch1), float(foff), float(tsamp), len(ranges),
+                                ctypes.cast(arr, ctypes.POINTER(abi.aa_dm_range)))
+        self.handle = abi.aa_plan_create(desc)
+        self.nchans = int(nchans)
+        self.fch1, self.foff, self.tsamp = float(fch1), float(foff), float(tsamp)
+        self.ranges = ranges
+
+    @classmethod
+    def from_workload(cls, w) -> "Plan":
+        return cls(w.nchans, w.fch1, w.foff, w.tsamp, w.ranges)
+
+    # lifetime ---------------------------------------------------------------
+    def close(self):
+        if getattr(self, "handle", None):
+            abi.aa_plan_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # strategy ---------------------------------------------------------------
+    def query(self, nsamp: int, max_width: int = 0) -> abi.aa_plan_info:
+        return abi.aa_plan_query(self.handle, nsamp, max_width)
+
+    def layout(self, nsamp: int) -> list:
+        out = []
+        for r in range(len(self.ranges)):
+            i = abi.aa_plan_range(self.handle, nsamp, r)
+            out.append(RangeLayout(i.ndm, i.dec, i.maxshift, i.dm_offset, i.dm_lo, i.dm_step,
+                                   i.nsamp_dec, i.length, i.pitch, i.row_offset))
+        return out
+
+    def shifts(self, r: int) -> np.ndarray:
+        return abi.aa_plan_shifts(self.handle, r, self.ranges[r][2], self.nchans)
+
+    def bind(self, device=None):
+        dev = torch.cuda.current_device() if device is None else int(device)
+        abi.aa_plan_bind(self.handle, dev)
+
+    # device path --------------------------------------------------------------
+    def device_input(self, x) -> tuple:
+        """Copy/pad a [nchans][nsamp] uint8 array to a device tensor whose row
+        pitch meets the library's 16-byte rule.  Returns (tensor, nsamp)."""
+        t = torch.as_tensor(x)
+        assert t.dtype == torch.uint8 and t.dim() == 2 and t.shape[0] == self.nchans
+        nsamp = t.shape[1]
+        pitch = self.query(nsamp).in_pitch_min
+        d = torch.zeros((self.nchans, pitch), dtype=torch.uint8, device="cuda")
+        d[:, :nsamp].copy_(t, non_blocking=False)
+        return d, nsamp
+
+    def alloc_output(self, nsamp: int) -> torch.Tensor:
+        return torch.empty(self.query(nsamp).dd_elems, dtype=torch.float32, device="cuda")
+
+    def alloc_workspace(self, nbytes: int) -> torch.Tensor:
+        return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device="cuda")
+
+    def dedisperse_device(self, d_in: torch.Tensor, nsamp: int, out=None, ws=None,
+                          stream=None) -> torch.Tensor:
+        self.bind()
+        info = self.query(nsamp)
+        out = self.alloc_output(nsamp) if out is None else out
+        ws = self.alloc_workspace(info.dedisp_ws_bytes) if ws is None else ws
+        assert out.numel() >= info.dd_elems and ws.numel() >= info.dedisp_ws_bytes
+        abi.aa_dedisperse_device(self.handle, d_in.data_ptr(), nsamp, d_in.stride(0),
+                                 out.data_ptr(), ws.data_ptr(), ws.numel(), _stream_handle(stream))
+        return out
+
+    def sps_search_device(self, dd: torch.Tensor, nsamp: int, max_width: int, threshold: float,
+                          capacity: int = 1 << 20, snr_out=None, ws=None, cands=None, count=None,
+                          stream=None):
+        """Returns (cands uint8 tensor [capacity*16], count uint64 tensor [1], snr_out)."""
+        self.bind()
+        info = self.query(nsamp, max_width)
+        ws = self.alloc_workspace(info.sps_ws_bytes) if ws is None else ws
+        cands = (torch.empty(max(capacity, 1) * 16, dtype=torch.uint8, device="cuda")
+                 if cands is None else cands)
+        count = torch.zeros(1, dtype=torch.int64, device="cuda") if count is None else count
+        abi.aa_sps_search_device(self.handle, nsamp, dd.data_ptr(), max_width, threshold,
+                                 cands.data_ptr(), capacity, count.data_ptr(),
+                                 0 if snr_out is None else snr_out.data_ptr(),
+                                 ws.data_ptr(), ws.numel(), _stream_handle(stream))
+        return cands, count, snr_out
+
+    def range_views(self, flat: torch.Tensor, nsamp: int) -> list:
+        """[ndm_r][L_r] views of a flat output buffer, one per range."""
+        views = []
+        for g in self.layout(nsamp):
+            v = flat[g.row_offset:g.row_offset + g.ndm * g.pitch].view(g.ndm, g.pitch)
+            views.append(v[:, :g.length])
+        return views
+
+    # host-buffer path (library-owned results) ------------------------------
+    def dedisperse(self, host, stream=None) -> "DDResult":
+        h = host if isinstance(host, np.ndarray) else host.numpy()
+        assert h.dtype == np.uint8 and h.ndim == 2 and h.shape[0] == self.nchans
+        assert h.strides[1] == 1
+        res = abi.aa_dedisperse(self.handle, h.ctypes.data, h.shape[1], h.strides[0],
+                                _stream_handle(stream))
+        return DDResult(self, res)
+
+    def sps_search(self, dd: "DDResult", max_width: int, threshold: float,
+                   capacity: int = 1 << 20, stream=None):
+        """Sorted candidate records (numpy structured array) and the total found."""
+        h, st = abi.aa_sps_search(self.handle, dd.handle, max_width, threshold, capacity,
+                                  _stream_handle(stream))
+        try:
+            ptr, stored, total = abi.aa_candidates_view(h)
+            arr = np.zeros(stored, dtype=abi.CANDIDATE_DTYPE)
+            if stored:
+                ctypes.memmove(arr.ctypes.data, ptr, stored * abi.CANDIDATE_DTYPE.itemsize)
+        finally:
+            abi.aa_candidates_destroy(h)
+        return arr, total
+
+
+class _DeviceArray:
+    """Zero-copy description of a library-owned float buffer."""
+
+    def __init__(self, ptr: int, n: int):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": "<f4", "data": (ptr, True),
+                                         "version": 3, "strides": None}
+
+
+class DDResult:
+    """Library-owned dedispersed output (device memory)."""
+
+    def __init__(self, plan: Plan, handle: int):
+        self.plan = plan
+        self.handle = handle
+
+    def view(self) -> tuple:
+        return abi.aa_dd_result_view(self.handle)
+
+    def to_tensor(self) -> torch.Tensor:
+        """Copy of the output buffer as a torch tensor (for inspection/tests)."""
+        ptr, nsamp = self.view()
+        n = self.plan.query(nsamp).dd_elems
+        return torch.as_tensor(_DeviceArray(ptr, n), device="cuda").clone()
+
+    def close(self):
+        if self.handle:
+            abi.aa_dd_result_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def candidates_from_device(cands: torch.Tensor, count: torch.Tensor, capacity: int) -> np.ndarray:
+    """Device candidate buffer -> sorted numpy structured array."""
+    n = min(int(count.item()), capacity)
+    raw = cands[: n * 16].cpu().numpy()
+    arr = raw.view(abi.CANDIDATE_DTYPE).copy()
+    order = np.lexsort((arr["t"], arr["dm_index"]))
+    return arr[order]

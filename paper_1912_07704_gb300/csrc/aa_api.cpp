@@ -1,0 +1,420 @@
+// C-ABI entry points: device-pointer calls (caller-owned device memory) and
+// the host-buffer path with library-owned results (arXiv:1912.07704 Sec. 2.3
+// memory requests, Sec. 2.4 ownership, Sec. 3.1 usage steps 4-8).
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "aa_internal.h"
+
+namespace aa {
+extern int g_fault_skip_chunk;
+extern uint64_t g_wait_limit_ns;
+cudaError_t launch_rsqrt_table(double* t, int wpad, cudaStream_t s);
+}  // namespace aa
+
+using namespace aa;
+
+struct aa_dd_result {
+    const aa_plan* plan = nullptr;
+    float* d_out = nullptr;      // dd_elems floats followed by the error word
+    unsigned* d_err = nullptr;
+    int64_t nsamp = 0;
+    cudaStream_t stream = nullptr;
+    int device = -1;
+};
+
+struct aa_candidates {
+    std::vector<aa_candidate> list;
+    int64_t total = 0;
+};
+
+namespace {
+
+aa_status cuda_fail(cudaError_t e, const char* what) {
+    set_error("%s: %s", what, cudaGetErrorString(e));
+    return (e == cudaErrorMemoryAllocation) ? AA_ERR_NOMEM : AA_ERR_CUDA;
+}
+
+#define AA_CUDA(call, what)                                   \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return cuda_fail(e_, (what));  \
+    } while (0)
+
+bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+aa_status check_device(const aa_plan* p) {
+    if (!p) { set_error("plan is NULL"); return AA_ERR_ARG; }
+    if (!p->ready) { set_error("plan is not bound to a device (aa_plan_bind)"); return AA_ERR_STATE; }
+    int dev = -1;
+    AA_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+    if (dev != p->device) {
+        set_error("current device %d differs from the plan's device %d", dev, p->device);
+        return AA_ERR_STATE;
+    }
+    return AA_OK;
+}
+
+// Stream-ordered allocations released together unless kept.
+struct AsyncAllocs {
+    cudaStream_t s;
+    std::vector<void*> ptrs;
+    explicit AsyncAllocs(cudaStream_t st) : s(st) {}
+    void* get(size_t bytes) {
+        void* p = nullptr;
+        if (cudaMallocAsync(&p, std::max<size_t>(bytes, 256), s) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        ptrs.push_back(p);
+        return p;
+    }
+    void keep(void* p) { ptrs.erase(std::remove(ptrs.begin(), ptrs.end(), p), ptrs.end()); }
+    ~AsyncAllocs() {
+        for (void* p : ptrs) cudaFreeAsync(p, s);
+    }
+};
+
+void keep_pool_memory(int device) {
+    static bool done[64] = {};
+    if (device < 0 || device >= 64 || done[device]) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    cudaGetLastError();
+    done[device] = true;
+}
+
+}  // namespace
+
+extern "C" {
+
+aa_status aa_dedisperse_device(const aa_plan* p, const uint8_t* d_in, int64_t nsamp,
+                               int64_t in_pitch, float* d_out, void* d_ws, size_t ws_bytes,
+                               aa_stream_t stream) {
+    clear_error();
+    aa_status st = check_device(p);
+    if (st != AA_OK) return st;
+    if (nsamp < 0) { set_error("nsamp must be >= 0"); return AA_ERR_ARG; }
+    const Layout L = make_layout(*p, nsamp, 0);
+    if (nsamp == 0 || L.dd_elems == 0) return AA_OK;
+    if (!d_in || !d_out || !d_ws) { set_error("d_in, d_out and d_ws must be non-NULL"); return AA_ERR_ARG; }
+    if (in_pitch < nsamp || in_pitch % 16 != 0) {
+        set_error("in_pitch %lld must be >= nsamp and a multiple of 16", (long long)in_pitch);
+        return AA_ERR_ARG;
+    }
+    if (!aligned(d_in, 16) || !aligned(d_out, 16) || !aligned(d_ws, 256)) {
+        set_error("d_in/d_out must be 16-byte and d_ws 256-byte aligned");
+        return AA_ERR_ARG;
+    }
+    if ((int64_t)ws_bytes < L.dedisp_ws) {
+        set_error("workspace %zu bytes < required %lld", ws_bytes, (long long)L.dedisp_ws);
+        return AA_ERR_ARG;
+    }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    unsigned* err = static_cast<unsigned*>(d_ws);
+    AA_CUDA(cudaMemsetAsync(err, 0, sizeof(unsigned), s), "clear error word");
+    char* ws = static_cast<char*>(d_ws);
+    // decimation cascade
+    for (size_t k = 0; k < p->decs.size(); ++k) {
+        const int dec = p->decs[k];
+        const void* src = d_in;
+        int src_elem = 1, src_dec = 1;
+        int64_t src_pitch = in_pitch;
+        for (size_t j = 0; j < k; ++j)
+            if (dec % p->decs[j] == 0) {
+                src = ws + L.dec_offset[j];
+                src_elem = 2;
+                src_dec = p->decs[j];
+                src_pitch = L.dec_pitch[j];
+            }
+        ProfScope prof(kKDecimate, s);
+        AA_CUDA(launch_decimate(src, src_elem, src_pitch, p->nchans, nsamp / dec, dec / src_dec,
+                                reinterpret_cast<uint16_t*>(ws + L.dec_offset[k]), L.dec_pitch[k], s),
+                "decimate launch");
+    }
+    for (size_t r = 0; r < p->ranges.size(); ++r) {
+        const RangePlan& g = p->ranges[r];
+        DedispArgs a{};
+        if (g.desc.dec == 1) {
+            a.in = d_in;
+            a.in_pitch = in_pitch;
+        } else {
+            const size_t k = std::find(p->decs.begin(), p->decs.end(), g.desc.dec) - p->decs.begin();
+            a.in = ws + L.dec_offset[k];
+            a.in_pitch = L.dec_pitch[k];
+        }
+        a.nchans = p->nchans;
+        a.nsamp = L.nsamp_dec[r];
+        a.length = L.length[r];
+        a.ndm = g.desc.ndm;
+        a.shifts = g.d_shifts;
+        a.out = d_out + L.row_offset[r];
+        a.out_pitch = L.pitch[r];
+        a.rw = g.rw;
+        a.cc = g.cc;
+        a.nstage = g.nstage;
+        a.flush = g.flush;
+        a.elem = g.elem;
+        a.smem = g.smem;
+        a.err = err;
+        if (a.length <= 0) continue;
+        ProfScope prof(g.elem == 1 ? kKDedispU8 : kKDedispU16, s);
+        AA_CUDA(launch_dedisperse(a, s), "dedisperse launch");
+    }
+    return AA_OK;
+}
+
+aa_status aa_sps_search_device(const aa_plan* p, int64_t nsamp, const float* d_dd, int32_t max_width,
+                               float threshold, aa_candidate* d_cands, int64_t cand_capacity,
+                               unsigned long long* d_count, float* d_snr_out, void* d_ws,
+                               size_t ws_bytes, aa_stream_t stream) {
+    clear_error();
+    aa_status st = check_device(p);
+    if (st != AA_OK) return st;
+    if (nsamp < 0) { set_error("nsamp must be >= 0"); return AA_ERR_ARG; }
+    if (max_width < 1 || max_width > 65535) { set_error("max_width must be in [1, 65535]"); return AA_ERR_ARG; }
+    if (cand_capacity < 0 || (cand_capacity > 0 && !d_cands)) { set_error("bad candidate buffer"); return AA_ERR_ARG; }
+    if (!d_count || !d_ws) { set_error("d_count and d_ws must be non-NULL"); return AA_ERR_ARG; }
+    if (!(threshold == threshold)) { set_error("threshold is NaN"); return AA_ERR_ARG; }
+    const Layout L = make_layout(*p, nsamp, max_width);
+    if ((int64_t)ws_bytes < L.sps_ws) {
+        set_error("workspace %zu bytes < required %lld", ws_bytes, (long long)L.sps_ws);
+        return AA_ERR_ARG;
+    }
+    if (!aligned(d_ws, 256) || (d_dd && !aligned(d_dd, 16)) || (d_snr_out && !aligned(d_snr_out, 16))) {
+        set_error("d_ws must be 256-byte and d_dd/d_snr_out 16-byte aligned");
+        return AA_ERR_ARG;
+    }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    AA_CUDA(cudaMemsetAsync(d_count, 0, sizeof(unsigned long long), s), "clear count");
+    if (L.dd_elems == 0 || L.dm_trial_samples == 0) return AA_OK;
+    if (!d_dd) { set_error("d_dd is NULL"); return AA_ERR_ARG; }
+    char* ws = static_cast<char*>(d_ws);
+    unsigned* err = reinterpret_cast<unsigned*>(ws);
+    AA_CUDA(cudaMemsetAsync(err, 0, sizeof(unsigned), s), "clear error word");
+    double* rsw = reinterpret_cast<double*>(ws + kErrBlock);
+    {
+        ProfScope prof(kKRsqrt, s);
+        AA_CUDA(launch_rsqrt_table(rsw, L.wpad, s), "rsqrt table launch");
+    }
+    RowStats* stats = reinterpret_cast<RowStats*>(ws + L.stats_offset);
+    float2* table = reinterpret_cast<float2*>(ws + L.table_offset);
+    std::vector<SpsArgs> args(p->ranges.size());
+    for (size_t r = 0; r < p->ranges.size(); ++r) {
+        const RangePlan& g = p->ranges[r];
+        SpsArgs& a = args[r];
+        a.dd = d_dd + L.row_offset[r];
+        a.pitch = L.pitch[r];
+        a.length = L.length[r];
+        a.nrows = g.desc.ndm;
+        a.dm_offset = g.dm_offset;
+        a.range = (int32_t)r;
+        a.max_width = max_width;
+        a.wpad = L.wpad;
+        a.threshold = threshold;
+        a.rsqrt_w = rsw;
+        a.stats = stats + g.dm_offset;
+        a.table = table + (int64_t)g.dm_offset * L.wpad;
+        a.cands = d_cands;
+        a.capacity = cand_capacity;
+        a.count = d_count;
+        a.snr_out = d_snr_out ? d_snr_out + L.row_offset[r] : nullptr;
+        a.err = err;
+        if (a.length <= 0) continue;
+        {
+            ProfScope prof(kKStats, s);
+            AA_CUDA(launch_sps_stats(a, s), "sps stats launch");
+        }
+        ProfScope prof(kKBoxcar, s);
+        AA_CUDA(launch_sps_boxcar(a, s), "sps boxcar launch");
+    }
+    for (size_t r = 0; r < p->ranges.size(); ++r) {
+        if (args[r].length <= 0) continue;
+        ProfScope prof(kKWidth, s);
+        AA_CUDA(launch_sps_width(args[r], s), "sps width launch");
+    }
+    return AA_OK;
+}
+
+aa_status aa_workspace_status(void* d_ws, aa_stream_t stream) {
+    clear_error();
+    if (!d_ws) { set_error("d_ws is NULL"); return AA_ERR_ARG; }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    unsigned h = 0;
+    AA_CUDA(cudaMemcpyAsync(&h, d_ws, sizeof h, cudaMemcpyDeviceToHost, s), "read error word");
+    AA_CUDA(cudaStreamSynchronize(s), "synchronize");
+    AA_CUDA(cudaMemsetAsync(d_ws, 0, sizeof h, s), "clear error word");
+    if (h) { set_error("a bounded device-side wait gave up (code %u)", h); return AA_ERR_TIMEOUT; }
+    return AA_OK;
+}
+
+aa_status aa_dedisperse(aa_plan* p, const uint8_t* host_in, int64_t nsamp, int64_t host_pitch,
+                        aa_stream_t stream, aa_dd_result** out) {
+    clear_error();
+    if (!out) { set_error("out is NULL"); return AA_ERR_ARG; }
+    *out = nullptr;
+    if (!p) { set_error("plan is NULL"); return AA_ERR_ARG; }
+    if (nsamp < 0 || (nsamp > 0 && (!host_in || host_pitch < nsamp))) {
+        set_error("bad host input (nsamp %lld, pitch %lld)", (long long)nsamp, (long long)host_pitch);
+        return AA_ERR_ARG;
+    }
+    if (!p->ready) {
+        int dev = 0;
+        AA_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+        aa_status b = aa_plan_bind(p, dev);
+        if (b != AA_OK) return b;
+    }
+    aa_status st = check_device(p);
+    if (st != AA_OK) return st;
+    keep_pool_memory(p->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const Layout L = make_layout(*p, nsamp, 0);
+    AsyncAllocs mem(s);
+    aa_dd_result* res = new (std::nothrow) aa_dd_result();
+    if (!res) { set_error("host allocation failed"); return AA_ERR_NOMEM; }
+    res->plan = p;
+    res->nsamp = nsamp;
+    res->stream = s;
+    res->device = p->device;
+    float* d_out = static_cast<float*>(mem.get((size_t)L.dd_elems * 4 + kErrBlock));
+    uint8_t* d_in = static_cast<uint8_t*>(mem.get((size_t)p->nchans * L.in_pitch_min));
+    void* d_ws = mem.get((size_t)L.dedisp_ws);
+    if (!d_out || !d_in || !d_ws) {
+        delete res;
+        set_error("device allocation of %lld bytes failed",
+                  (long long)(L.dd_elems * 4 + p->nchans * L.in_pitch_min + L.dedisp_ws));
+        return AA_ERR_NOMEM;
+    }
+    if (nsamp > 0) {
+        cudaError_t e = cudaMemcpy2DAsync(d_in, L.in_pitch_min, host_in, host_pitch, nsamp,
+                                          p->nchans, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) {
+            cudaEvent_t ev;
+            e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+            if (e == cudaSuccess) {
+                e = cudaEventRecord(ev, s);
+                if (e == cudaSuccess) e = cudaEventSynchronize(ev);  // host input fully read
+                cudaEventDestroy(ev);
+            }
+        }
+        if (e != cudaSuccess) { delete res; return cuda_fail(e, "host-to-device copy"); }
+    }
+    st = aa_dedisperse_device(p, d_in, nsamp, L.in_pitch_min, d_out, d_ws, (size_t)L.dedisp_ws, stream);
+    if (st != AA_OK) { delete res; return st; }
+    unsigned* d_err = reinterpret_cast<unsigned*>(d_out + L.dd_elems);
+    cudaError_t e = nsamp > 0 ? cudaMemcpyAsync(d_err, d_ws, sizeof(unsigned), cudaMemcpyDeviceToDevice, s)
+                              : cudaMemsetAsync(d_err, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) { delete res; return cuda_fail(e, "keep error word"); }
+    mem.keep(d_out);
+    res->d_out = d_out;
+    res->d_err = d_err;
+    *out = res;
+    return AA_OK;
+}
+
+aa_status aa_dd_result_view(const aa_dd_result* r, const float** d_out, int64_t* nsamp) {
+    clear_error();
+    if (!r) { set_error("result is NULL"); return AA_ERR_ARG; }
+    if (d_out) *d_out = r->d_out;
+    if (nsamp) *nsamp = r->nsamp;
+    return AA_OK;
+}
+
+void aa_dd_result_destroy(aa_dd_result* r) {
+    if (!r) return;
+    if (r->d_out) cudaFreeAsync(r->d_out, r->stream);
+    delete r;
+}
+
+aa_status aa_sps_search(aa_plan* p, const aa_dd_result* dd, int32_t max_width, float threshold,
+                        int64_t cand_capacity, aa_stream_t stream, aa_candidates** out) {
+    clear_error();
+    if (!out) { set_error("out is NULL"); return AA_ERR_ARG; }
+    *out = nullptr;
+    if (!p || !dd) { set_error("plan/result is NULL"); return AA_ERR_ARG; }
+    if (dd->plan != p) { set_error("result was produced by another plan"); return AA_ERR_ARG; }
+    if (cand_capacity < 0) { set_error("cand_capacity must be >= 0"); return AA_ERR_ARG; }
+    aa_status st = check_device(p);
+    if (st != AA_OK) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const Layout L = make_layout(*p, dd->nsamp, max_width > 0 ? max_width : 1);
+    AsyncAllocs mem(s);
+    void* d_ws = mem.get((size_t)L.sps_ws);
+    aa_candidate* d_c = static_cast<aa_candidate*>(mem.get((size_t)std::max<int64_t>(cand_capacity, 1) * sizeof(aa_candidate)));
+    unsigned long long* d_n = static_cast<unsigned long long*>(mem.get(sizeof(unsigned long long)));
+    if (!d_ws || !d_c || !d_n) { set_error("device allocation failed"); return AA_ERR_NOMEM; }
+    st = aa_sps_search_device(p, dd->nsamp, dd->d_out, max_width, threshold, d_c, cand_capacity, d_n,
+                              nullptr, d_ws, (size_t)L.sps_ws, stream);
+    if (st != AA_OK) return st;
+    aa_candidates* res = new (std::nothrow) aa_candidates();
+    if (!res) { set_error("host allocation failed"); return AA_ERR_NOMEM; }
+    unsigned long long total = 0;
+    cudaError_t e = cudaMemcpyAsync(&total, d_n, sizeof total, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) { delete res; return cuda_fail(e, "read candidate count"); }
+    const int64_t stored = std::min<int64_t>((int64_t)total, cand_capacity);
+    try {
+        res->list.resize((size_t)stored);
+    } catch (const std::bad_alloc&) {
+        delete res;
+        set_error("host allocation failed");
+        return AA_ERR_NOMEM;
+    }
+    if (stored > 0) {
+        e = cudaMemcpyAsync(res->list.data(), d_c, (size_t)stored * sizeof(aa_candidate),
+                            cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) { delete res; return cuda_fail(e, "read candidates"); }
+    }
+    std::sort(res->list.begin(), res->list.end(), [](const aa_candidate& a, const aa_candidate& b) {
+        return a.dm_index != b.dm_index ? a.dm_index < b.dm_index : a.t < b.t;
+    });
+    res->total = (int64_t)total;
+    unsigned h = 0, h2 = 0;
+    e = cudaMemcpyAsync(&h, d_ws, sizeof h, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h2, dd->d_err, sizeof h2, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) { delete res; return cuda_fail(e, "read error word"); }
+    h |= h2;
+    if (h) { delete res; set_error("a bounded device-side wait gave up"); return AA_ERR_TIMEOUT; }
+    *out = res;
+    return (int64_t)total > cand_capacity ? AA_WARN_CAND_OVERFLOW : AA_OK;
+}
+
+aa_status aa_candidates_view(const aa_candidates* c, const aa_candidate** host, int64_t* stored,
+                             int64_t* total) {
+    clear_error();
+    if (!c) { set_error("candidates is NULL"); return AA_ERR_ARG; }
+    if (host) *host = c->list.empty() ? nullptr : c->list.data();
+    if (stored) *stored = (int64_t)c->list.size();
+    if (total) *total = c->total;
+    return AA_OK;
+}
+
+void aa_candidates_destroy(aa_candidates* c) { delete c; }
+
+aa_status aa_debug_inject(int32_t what, int64_t value) {
+    clear_error();
+    switch (what) {
+        case 0:  // reset
+            g_fault_skip_chunk = -1;
+            g_wait_limit_ns = 2000000000ull;
+            return AA_OK;
+        case 1:  // never issue the staging copy of this channel chunk
+            g_fault_skip_chunk = (int)value;
+            return AA_OK;
+        case 2:  // bounded-wait limit in nanoseconds
+            if (value <= 0) { set_error("limit must be > 0"); return AA_ERR_ARG; }
+            g_wait_limit_ns = (uint64_t)value;
+            return AA_OK;
+    }
+    set_error("unknown injection %d", what);
+    return AA_ERR_ARG;
+}
+
+}  // extern "C"

@@ -1,0 +1,357 @@
+// Time decimation and brute-force dedispersion kernels for sm_103a.
+//
+// Dedispersion (arXiv:1912.07704 Sec. 1, dedispersion module): for every DM
+// trial i of a range, y[i][t] = sum_c x[c][t + s(c,i)], exact integers.
+//
+// Tile: one CTA = 16 DM trials x 512 output samples.  Channels stream through
+// shared memory in stages of `cc` channel rows, each row fetched with one
+// bulk-async (TMA) copy tracked by an mbarrier; the row holds the samples
+// [t0 + s(c,first DM) .. t0 + 512 + s(c,last DM)] rounded out to 16 bytes, so
+// every DM of the block reads from the same staged row.  Because per-channel
+// delays are arbitrary, the row is also stored shifted by 1..spw-1 samples so
+// that every (channel, DM) read is a 32-bit aligned word.  Each lane sums
+// 4 words (uint8: 16 samples) per DM in packed 16-bit lanes (two samples per
+// 32-bit add), flushing into 32-bit totals before a lane can overflow.
+#include <cstdint>
+
+#include "aa_internal.h"
+
+namespace aa {
+namespace {
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_fence_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for a phase with a wall-clock limit; false if it did not complete.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t start = global_ns();
+    while (!mbar_try_wait(bar, parity))
+        if (global_ns() - start > limit_ns) return false;
+    return true;
+}
+
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes,
+                                              uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s per stage: far beyond any real copy
+
+// SPW = samples per 32-bit word: 4 for raw uint8 input, 2 for decimated uint16.
+template <int SPW>
+__global__ void __launch_bounds__(kDedispThreads, 2)
+    dedisperse_kernel(DedispArgs a, int ndm_blocks, uint64_t wait_limit_ns, int fault_skip_chunk) {
+    constexpr int QW = kTau / (32 * SPW);  // words per lane per DM trial
+    constexpr int NCOPY = SPW;             // shifted copies of each staged row
+    constexpr int EB = 4 / SPW;            // bytes per sample
+    constexpr int A16 = 16 / EB;           // samples per 16-byte unit
+    constexpr int SWAR = SPW / 2;          // packed accumulators per word
+
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int cc = a.cc, nstage = a.nstage, rw = a.rw;
+    const size_t stage_w = (size_t)cc * NCOPY * rw;
+    uint32_t* stages = reinterpret_cast<uint32_t*>(smem);
+    int* offs = reinterpret_cast<int*>(stages + nstage * stage_w);  // [nstage][16][cc]
+    int* bases = offs + nstage * kDmPerBlock * cc;                   // [nstage][cc]
+    uint64_t* bars = reinterpret_cast<uint64_t*>(
+        (reinterpret_cast<uintptr_t>(bases + nstage * cc) + 15) & ~uintptr_t(15));
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int dmb = blockIdx.x % ndm_blocks;
+    const int64_t tile = blockIdx.x / ndm_blocks;
+    const int d0 = dmb * kDmPerBlock;
+    const int dlast = min(a.ndm, d0 + kDmPerBlock) - 1;
+    const int64_t t0 = tile * kTau;
+    const int C = a.nchans;
+    const int nchunks = (C + cc - 1) / cc;
+    const unsigned char* in_b = static_cast<const unsigned char*>(a.in);
+    const int64_t pitch_b = a.in_pitch * EB;
+
+    if (tid == 0) {
+        for (int s = 0; s < nstage; ++s) mbar_init(&bars[s], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+
+    // Producer (warp 0): stage chunk k (channels k*cc ..) into stage k % nstage.
+    auto issue = [&](int k) {
+        const int s = k % nstage;
+        const int c0 = k * cc;
+        uint32_t bytes = 0;
+        int64_t src_off = 0;
+        if (lane < cc && c0 + lane < C) {
+            const int c = c0 + lane;
+            const int s_lo = __ldg(&a.shifts[(int64_t)d0 * C + c]);
+            const int s_hi = __ldg(&a.shifts[(int64_t)dlast * C + c]);
+            const int64_t base = ((t0 + s_lo) / A16) * A16;
+            const int64_t end = t0 + kTau + s_hi + SPW;
+            int64_t nb = ((end - base) * EB + 15) / 16 * 16;
+            nb = min(nb, (int64_t)rw * 4);
+            nb = min(nb, pitch_b - base * EB);
+            bytes = nb > 0 ? (uint32_t)nb : 0u;
+            src_off = (int64_t)c * pitch_b + base * EB;
+            bases[s * cc + lane] = (int)(base - t0);
+        }
+        uint32_t total = bytes;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) total += __shfl_xor_sync(0xffffffffu, total, o);
+        if (k == fault_skip_chunk) return;  // fault injection: this stage never completes
+        if (lane == 0) mbar_arrive_expect_tx(&bars[s], total);
+        __syncwarp();
+        if (bytes)
+            bulk_copy_g2s(stages + s * stage_w + (size_t)lane * NCOPY * rw, in_b + src_off, bytes,
+                          &bars[s]);
+    };
+
+    int next_issue = 0;
+    if (warp == 0)
+        for (; next_issue < min(nstage - 1, nchunks); ++next_issue) issue(next_issue);
+    next_issue = min(nstage - 1, nchunks);
+    __syncthreads();  // bases[] of the first stages visible to all threads
+
+    uint32_t acc[kDmPerWarp][QW][SWAR];
+    uint32_t tot[kDmPerWarp][QW][SPW];
+#pragma unroll
+    for (int kk = 0; kk < kDmPerWarp; ++kk)
+#pragma unroll
+        for (int j = 0; j < QW; ++j) {
+#pragma unroll
+            for (int q = 0; q < SWAR; ++q) acc[kk][j][q] = 0;
+#pragma unroll
+            for (int q = 0; q < SPW; ++q) tot[kk][j][q] = 0;
+        }
+
+    auto flush = [&]() {
+#pragma unroll
+        for (int kk = 0; kk < kDmPerWarp; ++kk)
+#pragma unroll
+            for (int j = 0; j < QW; ++j) {
+                if constexpr (SPW == 4) {
+                    const uint32_t e = acc[kk][j][0], o = acc[kk][j][1];
+                    tot[kk][j][0] += e & 0xffffu;
+                    tot[kk][j][2] += e >> 16;
+                    tot[kk][j][1] += o & 0xffffu;
+                    tot[kk][j][3] += o >> 16;
+                } else {
+                    const uint32_t v = acc[kk][j][0];
+                    tot[kk][j][0] += v & 0xffffu;
+                    tot[kk][j][1] += v >> 16;
+                }
+#pragma unroll
+                for (int q = 0; q < SWAR; ++q) acc[kk][j][q] = 0;
+            }
+    };
+
+    int since_flush = 0;
+    for (int k = 0; k < nchunks; ++k) {
+        const int s = k % nstage;
+        const uint32_t parity = (uint32_t)(k / nstage) & 1u;
+        const bool ok = mbar_wait_bounded(&bars[s], parity, wait_limit_ns);
+        uint32_t* st = stages + s * stage_w;
+        const int c0 = k * cc;
+        const int cvalid = min(cc, C - c0);
+        if (ok) {
+            // shifted copies 1..NCOPY-1 of every staged row
+            if constexpr (NCOPY > 1) {
+                const int per = rw - 1;
+                for (int idx = tid; idx < cvalid * per; idx += kDedispThreads) {
+                    const int cl = idx / per, j = idx - cl * per;
+                    uint32_t* row = st + (size_t)cl * NCOPY * rw;
+                    const uint32_t w0 = row[j], w1 = row[j + 1];
+#pragma unroll
+                    for (int q = 1; q < NCOPY; ++q)
+                        row[q * rw + j] = __funnelshift_r(w0, w1, q * 8 * EB);
+                }
+            }
+            // word offset of every (DM, channel) of this chunk
+            int* ot = offs + s * kDmPerBlock * cc;
+            const int* bs = bases + s * cc;
+            for (int idx = tid; idx < kDmPerBlock * cvalid; idx += kDedispThreads) {
+                const int dl = idx / cvalid, cl = idx - dl * cvalid;
+                const int d = min(d0 + dl, dlast);
+                const int o = __ldg(&a.shifts[(int64_t)d * C + c0 + cl]) - bs[cl];
+                ot[dl * cc + cl] = (cl * NCOPY + o % SPW) * rw + o / SPW;
+            }
+        }
+        if (!__syncthreads_and(ok)) {
+            // A stage never arrived: report, drain the copies still in flight
+            // (bounded), and leave without touching the output.
+            if (tid == 0) atomicOr(a.err, 1u);
+            for (int kk = k; kk < next_issue; ++kk)
+                mbar_wait_bounded(&bars[kk % nstage], (uint32_t)(kk / nstage) & 1u, wait_limit_ns);
+            return;
+        }
+        if (next_issue < nchunks) {
+            if (warp == 0) issue(next_issue);
+            ++next_issue;
+        }
+
+        // accumulate: each warp owns kDmPerWarp trials of the block
+#pragma unroll
+        for (int kk = 0; kk < kDmPerWarp; ++kk) {
+            const int* o = offs + (s * kDmPerBlock + warp * kDmPerWarp + kk) * cc;
+            int cl = 0;
+            for (; cl + 1 < cvalid; cl += 2) {
+                const uint32_t* p0 = st + o[cl] + lane;
+                const uint32_t* p1 = st + o[cl + 1] + lane;
+#pragma unroll
+                for (int j = 0; j < QW; ++j) {
+                    const uint32_t v0 = p0[32 * j], v1 = p1[32 * j];
+                    if constexpr (SPW == 4) {
+                        acc[kk][j][0] += (v0 & 0x00ff00ffu) + (v1 & 0x00ff00ffu);
+                        acc[kk][j][1] += __byte_perm(v0, 0u, 0x4341) + __byte_perm(v1, 0u, 0x4341);
+                    } else {
+                        acc[kk][j][0] += v0 + v1;
+                    }
+                }
+            }
+            if (cl < cvalid) {
+                const uint32_t* p0 = st + o[cl] + lane;
+#pragma unroll
+                for (int j = 0; j < QW; ++j) {
+                    const uint32_t v0 = p0[32 * j];
+                    if constexpr (SPW == 4) {
+                        acc[kk][j][0] += v0 & 0x00ff00ffu;
+                        acc[kk][j][1] += __byte_perm(v0, 0u, 0x4341);
+                    } else {
+                        acc[kk][j][0] += v0;
+                    }
+                }
+            }
+        }
+        since_flush += cc;
+        if (since_flush >= a.flush) {
+            flush();
+            since_flush = 0;
+        }
+    }
+    flush();
+
+    // epilogue: exact integer totals -> FP32 rows
+#pragma unroll
+    for (int kk = 0; kk < kDmPerWarp; ++kk) {
+        const int d = d0 + warp * kDmPerWarp + kk;
+        if (d >= a.ndm) continue;
+        float* row = a.out + (int64_t)d * a.out_pitch;
+#pragma unroll
+        for (int j = 0; j < QW; ++j) {
+            const int64_t t = t0 + (int64_t)SPW * (lane + 32 * j);
+            if (t + SPW <= a.length) {
+                if constexpr (SPW == 4) {
+                    *reinterpret_cast<float4*>(row + t) =
+                        make_float4((float)tot[kk][j][0], (float)tot[kk][j][1],
+                                    (float)tot[kk][j][2], (float)tot[kk][j][3]);
+                } else {
+                    *reinterpret_cast<float2*>(row + t) =
+                        make_float2((float)tot[kk][j][0], (float)tot[kk][j][1]);
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < SPW; ++q)
+                    if (t + q < a.length) row[t + q] = (float)tot[kk][j][q];
+            }
+        }
+    }
+}
+
+// x_out[c][j] = sum_{k<factor} x_in[c][j*factor + k], j < nout.  One thread
+// per 4 outputs; grid-stride over (channel, quad).
+template <typename Tin>
+__global__ void __launch_bounds__(256) decimate_kernel(const Tin* __restrict__ in, int64_t in_pitch,
+                                                       int32_t nchans, int64_t nout, int factor,
+                                                       uint16_t* __restrict__ out,
+                                                       int64_t out_pitch) {
+    const int64_t quads = (nout + 3) / 4;
+    const int64_t total = quads * nchans;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = q / quads;
+        const int64_t j0 = (q - c * quads) * 4;
+        const Tin* src = in + c * in_pitch + j0 * factor;
+        uint16_t* dst = out + c * out_pitch + j0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (j0 + u < nout) {
+                uint32_t s = 0;
+                for (int k = 0; k < factor; ++k) s += src[u * factor + k];
+                dst[u] = (uint16_t)s;
+            }
+        }
+    }
+}
+
+}  // namespace
+
+int g_fault_skip_chunk = -1;          // test hook: never issue this chunk
+uint64_t g_wait_limit_ns = kWaitLimitNs;
+
+cudaError_t launch_dedisperse(const DedispArgs& a, cudaStream_t s) {
+    if (a.length <= 0 || a.ndm <= 0) return cudaSuccess;
+    const int ndmb = (a.ndm + kDmPerBlock - 1) / kDmPerBlock;
+    const int64_t ntiles = (a.length + kTau - 1) / kTau;
+    const int64_t nblocks = (int64_t)ndmb * ntiles;
+    if (nblocks >= (1ll << 31)) return cudaErrorInvalidConfiguration;
+    auto kern = a.elem == 1 ? dedisperse_kernel<4> : dedisperse_kernel<2>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)a.smem);
+    if (e != cudaSuccess) return e;
+    kern<<<(unsigned)nblocks, kDedispThreads, a.smem, s>>>(a, ndmb, g_wait_limit_ns,
+                                                            g_fault_skip_chunk);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_decimate(const void* in, int in_elem, int64_t in_pitch, int32_t nchans,
+                            int64_t nout, int factor, uint16_t* out, int64_t out_pitch,
+                            cudaStream_t s) {
+    if (nout <= 0) return cudaSuccess;
+    const int64_t total = (nout + 3) / 4 * nchans;
+    int64_t blocks = (total + 255) / 256;
+    if (blocks > 152 * 64) blocks = 152 * 64;
+    if (in_elem == 1)
+        decimate_kernel<uint8_t><<<(unsigned)blocks, 256, 0, s>>>(
+            static_cast<const uint8_t*>(in), in_pitch, nchans, nout, factor, out, out_pitch);
+    else
+        decimate_kernel<uint16_t><<<(unsigned)blocks, 256, 0, s>>>(
+            static_cast<const uint16_t*>(in), in_pitch, nchans, nout, factor, out, out_pitch);
+    return cudaGetLastError();
+}
+
+}  // namespace aa

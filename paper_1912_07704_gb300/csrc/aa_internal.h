@@ -1,0 +1,168 @@
+// Internal declarations shared by the host plan code and the kernel
+// translation units of libaa_gb300.so.  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/aa_dedisp.h"
+
+namespace aa {
+
+// ---------------------------------------------------------------- strategy --
+// Dedispersion tile: a CTA of kDedispWarps warps covers kDmPerBlock DM trials
+// x kTau output samples; channels stream through shared memory in stages of
+// `cc` channels (bulk-async copies), each stage reused by all the CTA's DMs.
+constexpr int kDedispWarps = 8;
+constexpr int kDmPerWarp = 2;
+constexpr int kDmPerBlock = kDedispWarps * kDmPerWarp;  // 16
+constexpr int kTau = 512;                                // output samples per CTA
+constexpr int kDedispThreads = kDedispWarps * 32;
+
+// Boxcar tile: kSpsThreads threads x kSpsSlots consecutive start times each.
+constexpr int kSpsThreads = 256;
+constexpr int kSpsSlots = 16;
+constexpr int kSpsTile = kSpsThreads * kSpsSlots;  // start times per CTA incl. 2 halo
+constexpr int kSpsOwned = kSpsTile - 2;              // start times owned per CTA
+
+// Per-range strategy, derived once at plan creation (immutable afterwards).
+struct RangePlan {
+    aa_dm_range desc{};
+    std::vector<int32_t> shifts;  // [ndm][nchans], decimated samples
+    int32_t maxshift = 0;
+    int32_t span_max = 0;  // max over DM blocks/channels of s(c,last)-s(c,first)
+    int32_t dm_offset = 0;
+    int elem = 1;          // bytes per input sample (1: raw uint8, 2: decimated uint16)
+    int spw = 4;           // samples per 32-bit word
+    int rw = 0;            // words per shared-memory row copy
+    int cc = 16;           // channels per stage (even)
+    int nstage = 3;        // pipeline depth
+    int flush = 256;       // channels between SWAR flushes (multiple of cc)
+    size_t smem = 0;       // dynamic shared memory per CTA
+    int dec_src = 1;       // decimation source buffer (1 = raw input)
+    int32_t* d_shifts = nullptr;  // device copy (inside the plan's table block)
+};
+
+}  // namespace aa
+
+struct aa_plan {
+    int32_t nchans = 0;
+    double fch1 = 0, foff = 0, tsamp = 0, f_top = 0;
+    std::vector<aa::RangePlan> ranges;
+    std::vector<int> decs;  // distinct decimations > 1, ascending
+    int32_t ndm_total = 0;
+    double dm_max = 0;
+    int device = -1;
+    bool ready = false;
+    void* d_tables = nullptr;
+    size_t table_bytes = 0;
+};
+
+namespace aa {
+
+// Layout of every device buffer for one (nsamp, max_width).
+struct Layout {
+    int64_t nsamp = 0;
+    int64_t in_pitch_min = 0;
+    std::vector<int64_t> nsamp_dec, length, pitch, row_offset;
+    int64_t dd_elems = 0;
+    int64_t dm_trial_samples = 0;
+    // dedispersion workspace: [error word block][one uint16 buffer per decimation]
+    std::vector<int64_t> dec_pitch;   // elements, per entry of plan.decs
+    std::vector<int64_t> dec_offset;  // bytes into the workspace
+    int64_t dedisp_ws = 0;
+    // single-pulse workspace: [error word block][row stats][width tables]
+    int32_t max_width = 0;
+    int32_t wpad = 0;
+    int64_t stats_offset = 0, table_offset = 0, sps_ws = 0;
+};
+
+constexpr int64_t kErrBlock = 256;  // bytes reserved for the device error word
+
+Layout make_layout(const aa_plan& p, int64_t nsamp, int32_t max_width);
+
+void set_error(const char* fmt, ...);
+void clear_error();
+
+inline int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
+
+// Per-row statistics written by the stats kernel, read by the boxcar kernels.
+struct RowStats {
+    double mu;        // mean
+    double sigma;     // population standard deviation
+    double inv_sigma; // 1/sigma (0 if sigma == 0)
+    float m0;         // round(mu): integer offset removed before summing
+    int32_t zero_sigma;
+};
+static_assert(sizeof(RowStats) == 32, "RowStats layout");
+
+// ------------------------------------------------------------- profiling --
+enum KernelId {
+    kKDecimate = 0, kKDedispU8, kKDedispU16, kKRsqrt, kKStats, kKBoxcar, kKWidth, kNumKernels
+};
+
+// RAII: records CUDA events around a launch on `s` while profiling is on.
+class ProfScope {
+  public:
+    ProfScope(int kernel, cudaStream_t s);
+    ~ProfScope();
+    ProfScope(const ProfScope&) = delete;
+    ProfScope& operator=(const ProfScope&) = delete;
+
+  private:
+    int kernel_;
+    cudaStream_t stream_;
+    cudaEvent_t start_ = nullptr, stop_ = nullptr;
+    bool active_ = false;
+};
+
+// ------------------------------------------------------------- launchers --
+struct DedispArgs {
+    const void* in;          // [nchans][in_pitch] samples (uint8 or uint16)
+    int64_t in_pitch;        // elements
+    int32_t nchans;
+    int64_t nsamp;           // valid samples per row of `in`
+    int64_t length;          // output samples per trial
+    int32_t ndm;
+    const int32_t* shifts;   // [ndm][nchans]
+    float* out;              // row 0 of this range
+    int64_t out_pitch;       // floats
+    int rw, cc, nstage, flush, elem;
+    size_t smem;
+    unsigned* err;
+};
+cudaError_t launch_dedisperse(const DedispArgs& a, cudaStream_t s);
+
+cudaError_t launch_decimate(const void* in, int in_elem, int64_t in_pitch, int32_t nchans,
+                            int64_t nout, int factor, uint16_t* out, int64_t out_pitch,
+                            cudaStream_t s);
+
+struct SpsArgs {
+    const float* dd;        // row 0 of this range
+    int64_t pitch;          // floats between rows
+    int64_t length;         // samples per row
+    int32_t nrows;
+    int32_t dm_offset;
+    int32_t range;
+    int32_t max_width;
+    int32_t wpad;
+    float threshold;
+    const double* rsqrt_w;  // [wpad] 1/sqrt(w) for w = 1..wpad (device, FP64)
+    RowStats* stats;        // [nrows] of this range
+    float2* table;          // [nrows][wpad] (r_w, -c_w)
+    aa_candidate* cands;
+    int64_t capacity;
+    unsigned long long* count;
+    float* snr_out;         // optional, row 0 of this range (same pitch)
+    unsigned* err;
+};
+cudaError_t launch_sps_stats(const SpsArgs& a, cudaStream_t s);
+cudaError_t launch_sps_boxcar(const SpsArgs& a, cudaStream_t s);
+// Fill widths of the candidates [first, first+n) recorded for one range.
+cudaError_t launch_sps_width(const SpsArgs& a, cudaStream_t s);
+
+}  // namespace aa

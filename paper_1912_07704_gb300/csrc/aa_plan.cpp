@@ -1,0 +1,347 @@
+// Plan and strategy (arXiv:1912.07704 Sec. 3.1-3.2): validate the user's
+// description, build the FP64 delay tables and derive the immutable,
+// queryable strategy and memory requests (Sec. 2.3).  Host only, except
+// aa_plan_bind which uploads the delay tables.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "aa_internal.h"
+
+namespace aa {
+
+static thread_local std::string g_last_error;
+
+void set_error(const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+}
+
+void clear_error() { g_last_error.clear(); }
+
+// Dispersion constant, MHz^2 pc^-1 cm^3 s.
+static constexpr double kDM = 4.148808e3;
+
+// Delay of channel c at dispersion measure dm, in samples of a series
+// decimated by dec: round half away from zero of ((kDM*dm)*delta_c)/(tsamp*dec)
+// with delta_c = f_c^-2 - f_top^-2, every step an IEEE double rounded in the
+// order written (this file is compiled without FP contraction).
+static int32_t delay_samples(double fch1, double foff, double f_top, int32_t c, double tsamp,
+                             double dm, int32_t dec) {
+    double fc = fch1 + (double)c * foff;
+    double delta = 1.0 / (fc * fc) - 1.0 / (f_top * f_top);
+    double v = kDM * dm * delta / (tsamp * (double)dec);
+    return (int32_t)std::llround(v);
+}
+
+// Shared-memory footprint of one dedispersion CTA for a given channel chunk.
+static size_t dedisp_smem(const RangePlan& r, int cc, int nstage) {
+    size_t stage = (size_t)cc * r.spw * r.rw * 4;  // spw shifted copies per channel row
+    size_t tables = (size_t)kDmPerBlock * cc * 4 + (size_t)cc * 4;  // word offsets + bases
+    return (size_t)nstage * (stage + tables) + 64;  // + mbarriers
+}
+
+static aa_status build_strategy(aa_plan& p) {
+    for (auto& r : p.ranges) {
+        const int dec = r.desc.dec;
+        r.elem = dec == 1 ? 1 : 2;
+        r.spw = 4 / r.elem;
+        const int ndm = r.desc.ndm;
+        const int C = p.nchans;
+        int32_t span = 0;
+        for (int d0 = 0; d0 < ndm; d0 += kDmPerBlock) {
+            int d1 = std::min(ndm, d0 + kDmPerBlock) - 1;
+            const int32_t* a = &r.shifts[(size_t)d0 * C];
+            const int32_t* b = &r.shifts[(size_t)d1 * C];
+            for (int c = 0; c < C; ++c) span = std::max(span, b[c] - a[c]);
+        }
+        r.span_max = span;
+        const int a16 = 16 / r.elem;  // samples per 16-byte alignment unit
+        int64_t window = (int64_t)kTau + span + (a16 - 1) + r.spw;
+        r.rw = (int)round_up((window + r.spw - 1) / r.spw, 4);
+        // SWAR flush period: 16-bit lanes hold at most 65535.
+        const int per_lane_max = 255 * dec;
+        const int max_flush = 65535 / per_lane_max;
+        const size_t budget = 110 * 1024;
+        int cc = 16, nstage = 3;
+        while (cc > 2 && (dedisp_smem(r, cc, nstage) > budget || cc > max_flush)) cc -= 2;
+        if (cc > max_flush || dedisp_smem(r, cc, nstage) > budget) {
+            nstage = 2;
+            if (cc > max_flush || dedisp_smem(r, cc, nstage) > 200 * 1024) {
+                set_error("range dm_lo=%g: DM step too coarse for the dedispersion tile "
+                          "(delay span %d samples over %d trials)", r.desc.dm_lo, span, kDmPerBlock);
+                return AA_ERR_CONFIG;
+            }
+        }
+        r.cc = cc;
+        r.nstage = nstage;
+        r.flush = (std::min(max_flush, 256) / cc) * cc;
+        r.smem = dedisp_smem(r, cc, nstage);
+    }
+    // decimation cascade: each decimated buffer is built from the largest
+    // already-built decimation that divides it (or from the raw input).
+    for (auto& r : p.ranges)
+        if (r.desc.dec > 1 && std::find(p.decs.begin(), p.decs.end(), r.desc.dec) == p.decs.end())
+            p.decs.push_back(r.desc.dec);
+    std::sort(p.decs.begin(), p.decs.end());
+    return AA_OK;
+}
+
+Layout make_layout(const aa_plan& p, int64_t nsamp, int32_t max_width) {
+    Layout L;
+    L.nsamp = nsamp;
+    L.in_pitch_min = round_up(std::max<int64_t>(nsamp, 1), 16);
+    int64_t off = 0;
+    for (auto& r : p.ranges) {
+        int64_t nd = nsamp / r.desc.dec;
+        int64_t len = std::max<int64_t>(0, nd - r.maxshift);
+        int64_t pitch = round_up(std::max<int64_t>(len, 1), 64);
+        L.nsamp_dec.push_back(nd);
+        L.length.push_back(len);
+        L.pitch.push_back(pitch);
+        L.row_offset.push_back(off);
+        off += pitch * r.desc.ndm;
+        L.dm_trial_samples += len * r.desc.ndm;
+    }
+    L.dd_elems = off;
+    int64_t ws = kErrBlock;
+    for (int d : p.decs) {
+        int64_t pitch = round_up(std::max<int64_t>(nsamp / d, 1), 64);
+        L.dec_pitch.push_back(pitch);
+        L.dec_offset.push_back(ws);
+        ws += round_up((int64_t)p.nchans * pitch * 2, 256);
+    }
+    L.dedisp_ws = ws;  // always holds at least the error word
+    L.max_width = max_width;
+    if (max_width > 0) {
+        L.wpad = (int32_t)round_up(max_width, kSpsSlots);
+        int64_t s = kErrBlock;
+        s += round_up((int64_t)L.wpad * 8, 256);  // 1/sqrt(w) table
+        L.stats_offset = s;
+        s += round_up((int64_t)p.ndm_total * (int64_t)sizeof(RowStats), 256);
+        L.table_offset = s;
+        s += (int64_t)p.ndm_total * L.wpad * 8;
+        L.sps_ws = s;
+    }
+    return L;
+}
+
+}  // namespace aa
+
+using namespace aa;
+
+extern "C" {
+
+const char* aa_status_str(aa_status s) {
+    switch (s) {
+        case AA_OK: return "AA_OK";
+        case AA_PENDING: return "AA_PENDING";
+        case AA_WARN_CAND_OVERFLOW: return "AA_WARN_CAND_OVERFLOW";
+        case AA_ERR_CONFIG: return "AA_ERR_CONFIG";
+        case AA_ERR_NOMEM: return "AA_ERR_NOMEM";
+        case AA_ERR_CUDA: return "AA_ERR_CUDA";
+        case AA_ERR_TIMEOUT: return "AA_ERR_TIMEOUT";
+        case AA_ERR_STATE: return "AA_ERR_STATE";
+        case AA_ERR_ARG: return "AA_ERR_ARG";
+    }
+    return "AA_UNKNOWN_STATUS";
+}
+
+const char* aa_last_error(void) { return g_last_error.c_str(); }
+
+aa_status aa_plan_create(const aa_plan_desc* d, aa_plan** out) {
+    clear_error();
+    if (!out) { set_error("out is NULL"); return AA_ERR_ARG; }
+    *out = nullptr;
+    if (!d) { set_error("desc is NULL"); return AA_ERR_ARG; }
+    if (d->nchans < 1) { set_error("nchans must be >= 1 (got %d)", d->nchans); return AA_ERR_CONFIG; }
+    if (!(d->tsamp_s > 0) || !std::isfinite(d->tsamp_s)) { set_error("tsamp must be > 0"); return AA_ERR_CONFIG; }
+    if (!(d->foff_mhz != 0) || !std::isfinite(d->foff_mhz)) { set_error("foff must be non-zero"); return AA_ERR_CONFIG; }
+    if (!(d->fch1_mhz > 0) || !std::isfinite(d->fch1_mhz)) { set_error("fch1 must be > 0"); return AA_ERR_CONFIG; }
+    double f_last = d->fch1_mhz + (double)(d->nchans - 1) * d->foff_mhz;
+    if (!(f_last > 0)) { set_error("lowest channel frequency %g MHz is not positive", f_last); return AA_ERR_CONFIG; }
+    if (d->nranges < 1 || d->nranges > 64) { set_error("nranges must be in [1, 64] (got %d)", d->nranges); return AA_ERR_CONFIG; }
+    if (!d->ranges) { set_error("ranges is NULL"); return AA_ERR_ARG; }
+    int max_dec = 1;
+    int64_t ndm_total = 0;
+    for (int r = 0; r < d->nranges; ++r) {
+        const aa_dm_range& g = d->ranges[r];
+        if (g.ndm < 1) { set_error("range %d: ndm must be >= 1", r); return AA_ERR_CONFIG; }
+        if (g.dec < 1 || g.dec > 16) { set_error("range %d: dec must be in [1, 16] (got %d)", r, g.dec); return AA_ERR_CONFIG; }
+        if (!(g.dm_lo >= 0) || !(g.dm_step >= 0) || !std::isfinite(g.dm_lo) || !std::isfinite(g.dm_step)) {
+            set_error("range %d: dm_lo and dm_step must be finite and >= 0", r);
+            return AA_ERR_CONFIG;
+        }
+        max_dec = std::max(max_dec, g.dec);
+        ndm_total += g.ndm;
+    }
+    if (ndm_total > (1 << 24)) { set_error("too many DM trials (%lld)", (long long)ndm_total); return AA_ERR_CONFIG; }
+    if ((int64_t)d->nchans * 255 * max_dec >= (1 << 24)) {
+        set_error("nchans*255*dec = %lld >= 2^24: sums would not be exact in FP32",
+                  (long long)d->nchans * 255 * max_dec);
+        return AA_ERR_CONFIG;
+    }
+    aa_plan* p = new (std::nothrow) aa_plan();
+    if (!p) return AA_ERR_NOMEM;
+    try {
+        p->nchans = d->nchans;
+        p->fch1 = d->fch1_mhz;
+        p->foff = d->foff_mhz;
+        p->tsamp = d->tsamp_s;
+        p->f_top = f_last > d->fch1_mhz ? f_last : d->fch1_mhz;
+        int32_t off = 0;
+        for (int r = 0; r < d->nranges; ++r) {
+            RangePlan rp;
+            rp.desc = d->ranges[r];
+            rp.dm_offset = off;
+            off += rp.desc.ndm;
+            rp.shifts.resize((size_t)rp.desc.ndm * p->nchans);
+            int32_t ms = 0;
+            for (int i = 0; i < rp.desc.ndm; ++i) {
+                double dm = rp.desc.dm_lo + (double)i * rp.desc.dm_step;
+                p->dm_max = std::max(p->dm_max, dm);
+                for (int c = 0; c < p->nchans; ++c) {
+                    int32_t s = delay_samples(p->fch1, p->foff, p->f_top, c, p->tsamp, dm, rp.desc.dec);
+                    rp.shifts[(size_t)i * p->nchans + c] = s;
+                    ms = std::max(ms, s);
+                }
+            }
+            rp.maxshift = ms;
+            p->ranges.push_back(std::move(rp));
+        }
+        p->ndm_total = off;
+    } catch (const std::bad_alloc&) {
+        delete p;
+        set_error("host allocation failed");
+        return AA_ERR_NOMEM;
+    }
+    aa_status st = build_strategy(*p);
+    if (st != AA_OK) { delete p; return st; }
+    for (auto& r : p->ranges) p->table_bytes += round_up((int64_t)r.shifts.size() * 4, 256);
+    *out = p;
+    return AA_OK;
+}
+
+void aa_plan_destroy(aa_plan* p) {
+    if (!p) return;
+    if (p->d_tables) {
+        int prev = -1;
+        cudaGetDevice(&prev);
+        cudaSetDevice(p->device);
+        cudaFree(p->d_tables);
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+    delete p;
+}
+
+aa_status aa_plan_bind(aa_plan* p, int device) {
+    clear_error();
+    if (!p) { set_error("plan is NULL"); return AA_ERR_ARG; }
+    if (p->ready) {
+        if (p->device == device) return AA_OK;
+        set_error("plan already bound to device %d", p->device);
+        return AA_ERR_STATE;
+    }
+    int prev = -1;
+    cudaGetDevice(&prev);
+    cudaError_t e = cudaSetDevice(device);
+    if (e != cudaSuccess) { set_error("cudaSetDevice(%d): %s", device, cudaGetErrorString(e)); return AA_ERR_CUDA; }
+    void* mem = nullptr;
+    e = cudaMalloc(&mem, p->table_bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        if (prev >= 0) cudaSetDevice(prev);
+        set_error("cudaMalloc(%zu) for delay tables: %s", p->table_bytes, cudaGetErrorString(e));
+        return AA_ERR_NOMEM;
+    }
+    size_t off = 0;
+    for (auto& r : p->ranges) {
+        r.d_shifts = (int32_t*)((char*)mem + off);
+        e = cudaMemcpy(r.d_shifts, r.shifts.data(), r.shifts.size() * 4, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) break;
+        off += round_up((int64_t)r.shifts.size() * 4, 256);
+    }
+    if (e != cudaSuccess) {
+        cudaFree(mem);
+        for (auto& r : p->ranges) r.d_shifts = nullptr;
+        if (prev >= 0) cudaSetDevice(prev);
+        set_error("delay table upload: %s", cudaGetErrorString(e));
+        return AA_ERR_CUDA;
+    }
+    p->d_tables = mem;
+    p->device = device;
+    p->ready = true;
+    if (prev >= 0 && prev != device) cudaSetDevice(prev);
+    return AA_OK;
+}
+
+aa_status aa_plan_query(const aa_plan* p, int64_t nsamp, int32_t max_width, aa_plan_info* info) {
+    clear_error();
+    if (!p || !info) { set_error("plan/info is NULL"); return AA_ERR_ARG; }
+    if (nsamp < 0) { set_error("nsamp must be >= 0"); return AA_ERR_ARG; }
+    if (max_width < 0 || max_width > 65535) { set_error("max_width must be in [0, 65535]"); return AA_ERR_ARG; }
+    Layout L = make_layout(*p, nsamp, max_width);
+    std::memset(info, 0, sizeof *info);
+    info->nchans = p->nchans;
+    info->nranges = (int32_t)p->ranges.size();
+    info->ndm_total = p->ndm_total;
+    info->ready = p->ready ? 1 : 0;
+    info->device = p->device;
+    info->max_width = max_width;
+    info->nsamp = nsamp;
+    info->in_pitch_min = L.in_pitch_min;
+    info->dd_elems = L.dd_elems;
+    info->dedisp_ws_bytes = L.dedisp_ws;
+    info->sps_ws_bytes = L.sps_ws;
+    info->table_bytes = (int64_t)p->table_bytes;
+    info->host_path_bytes = (int64_t)p->nchans * L.in_pitch_min + L.dedisp_ws + L.dd_elems * 4 +
+                            L.sps_ws + 256;
+    info->dm_trial_samples = L.dm_trial_samples;
+    info->dm_max = p->dm_max;
+    return AA_OK;
+}
+
+aa_status aa_plan_range(const aa_plan* p, int64_t nsamp, int32_t r, aa_range_info* info) {
+    clear_error();
+    if (!p || !info) { set_error("plan/info is NULL"); return AA_ERR_ARG; }
+    if (r < 0 || r >= (int32_t)p->ranges.size()) { set_error("range %d out of bounds", r); return AA_ERR_ARG; }
+    if (nsamp < 0) { set_error("nsamp must be >= 0"); return AA_ERR_ARG; }
+    Layout L = make_layout(*p, nsamp, 0);
+    const RangePlan& g = p->ranges[r];
+    info->ndm = g.desc.ndm;
+    info->dec = g.desc.dec;
+    info->maxshift = g.maxshift;
+    info->dm_offset = g.dm_offset;
+    info->dm_lo = g.desc.dm_lo;
+    info->dm_step = g.desc.dm_step;
+    info->nsamp_dec = L.nsamp_dec[r];
+    info->length = L.length[r];
+    info->pitch = L.pitch[r];
+    info->row_offset = L.row_offset[r];
+    info->tile_dms = kDmPerBlock;
+    info->tile_samples = kTau;
+    info->stage_channels = g.cc;
+    info->stages = g.nstage;
+    info->span_max = g.span_max;
+    info->smem_bytes = (int32_t)g.smem;
+    return AA_OK;
+}
+
+aa_status aa_plan_shifts(const aa_plan* p, int32_t r, int32_t* out, int64_t cap) {
+    clear_error();
+    if (!p || !out) { set_error("plan/out is NULL"); return AA_ERR_ARG; }
+    if (r < 0 || r >= (int32_t)p->ranges.size()) { set_error("range %d out of bounds", r); return AA_ERR_ARG; }
+    const auto& s = p->ranges[r].shifts;
+    if (cap < (int64_t)s.size()) { set_error("capacity %lld < %zu", (long long)cap, s.size()); return AA_ERR_ARG; }
+    std::memcpy(out, s.data(), s.size() * 4);
+    return AA_OK;
+}
+
+}  // extern "C"

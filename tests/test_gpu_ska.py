@@ -1,0 +1,112 @@
+"""Full-size 4096-channel, 2^20-sample, four-range plan with W = 8192, run
+exactly as bench.py runs it; the oracle checks sampled DM rows in full
+(dedispersion) and sampled time windows (boxcar SNR and candidates), and
+every strong injected pulse must be detected near its DM and arrival time."""
+import numpy as np
+import pytest
+import torch
+
+from gpu_common import check_snr_rows, compare_candidate_lists, oracle_candidates
+from paper_1912_07704_gb300 import synth
+from paper_1912_07704_gb300.api import Plan, candidates_from_device
+
+pytestmark = pytest.mark.gpu
+
+W = synth.SKA_4096
+
+
+@pytest.fixture(scope="module")
+def ska_run(oracle):
+    oracle.set_threads(0)
+    d1 = lambda dm: oracle.shifts(W.nchans, W.fch1, W.foff, W.tsamp, dm, 1)
+    pulses = synth.pulses_ska(W, lambda dm: int(d1(dm).max()))
+    plan = Plan.from_workload(W)
+    pitch = plan.query(W.nsamp).in_pitch_min
+    x = synth.make_filterbank(W, pulses, d1, device="cuda", pitch=pitch)
+    nsamp = W.nsamp
+    # the bench configuration: no B output
+    out = plan.dedisperse_device(x, nsamp)
+    cap = 1 << 20
+    cands, count, _ = plan.sps_search_device(out, nsamp, W.max_width, W.threshold, cap)
+    torch.cuda.synchronize()
+    bench_cands = candidates_from_device(cands, count, cap)
+    # the same call with the optional B(t) output
+    snr = torch.full_like(out, float("nan"))
+    cands2, count2, _ = plan.sps_search_device(out, nsamp, W.max_width, W.threshold, cap,
+                                               snr_out=snr)
+    torch.cuda.synchronize()
+    snr_cands = candidates_from_device(cands2, count2, cap)
+    xh = x[:, :nsamp].cpu().numpy()
+    del x, cands, cands2
+    torch.cuda.empty_cache()
+    yield plan, xh, out, snr, bench_cands, snr_cands, pulses
+    del out, snr
+    torch.cuda.empty_cache()
+
+
+def test_bench_and_snr_runs_agree(ska_run):
+    plan, xh, out, snr, bc, sc, pulses = ska_run
+    assert np.array_equal(bc, sc)
+
+
+def _sample_rows(lay, pulses, r):
+    g = lay[r]
+    rows = {0, g.ndm // 2, g.ndm - 1}
+    for p in pulses:
+        i = int(round((p.dm - g.dm_lo) / g.dm_step)) if g.dm_step > 0 else 0
+        if 0 <= i < g.ndm:
+            rows.add(i)
+    return sorted(rows)
+
+
+def test_sampled_rows_parity(oracle, ska_run):
+    plan, xh, out, snr, bc, sc, pulses = ska_run
+    lay = plan.layout(W.nsamp)
+    dd = plan.range_views(out, W.nsamp)
+    sv = plan.range_views(snr, W.nsamp)
+    opl = oracle.plan(W.nchans, W.fch1, W.foff, W.tsamp, W.ranges, W.nsamp)
+    compared = 0
+    for r, g in enumerate(lay):
+        xr = oracle.range_input(xh, g.dec)
+        rows = _sample_rows(lay, pulses, r)
+        ys = {}
+        for i in rows:
+            y = oracle.dedisperse_row(xr, opl[r].shifts[i], 0, g.length)
+            assert np.array_equal(dd[r][i].double().cpu().numpy(), y.astype(np.float64)), (r, i)
+            ys[i] = y
+        windows = {}
+        for i in rows:
+            lo, hi = 0, 2048
+            for p in pulses:
+                t = p.t0 // g.dec
+                if abs(p.dm - (g.dm_lo + i * g.dm_step)) < 3 * max(g.dm_step, 1e-9) and t < g.length:
+                    lo, hi = max(0, t - 1024), min(g.length, t + 1024)
+            windows[i] = (lo, hi)
+        solid, fragile, B = oracle_candidates(oracle, ys, W.max_width, W.threshold,
+                                              g.dm_offset, r, windows)
+        check_snr_rows(sv[r], ys, B)
+        glob = {g.dm_offset + i: windows[i] for i in rows}
+        keep = lambda dm, t: dm in glob and glob[dm][0] <= t < glob[dm][1]
+        compared += compare_candidate_lists(bc[bc["range"] == r], solid, fragile, keep)
+    assert compared > 0
+
+
+def test_strong_pulses_detected(ska_run):
+    plan, xh, out, snr, bc, sc, pulses = ska_run
+    lay = plan.layout(W.nsamp)
+    checked = 0
+    for p in pulses:
+        if 4.0 * p.amplitude * np.sqrt(p.n_w) < 12.0:
+            continue  # expected SNR too low to require a detection
+        for r, g in enumerate(lay):
+            hi = g.dm_lo + (g.ndm - 1) * g.dm_step
+            if not (g.dm_lo <= p.dm <= hi + g.dm_step):
+                continue
+            t = p.t0 // g.dec
+            sel = bc[(bc["range"] == r)
+                     & (np.abs(g.dm_lo + (bc["dm_index"] - g.dm_offset) * g.dm_step - p.dm)
+                        <= 2 * g.dm_step)
+                     & (np.abs(bc["t"].astype(np.int64) - t) <= p.n_w // g.dec + 4)]
+            assert len(sel) > 0, (p, r)
+            checked += 1
+    assert checked >= 5
