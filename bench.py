@@ -219,7 +219,7 @@ def bench_ours(args):
     out = plan.alloc_output(nsamp)
     ws_dd = plan.alloc_workspace(info.dedisp_ws_bytes)
     ws_sps = plan.alloc_workspace(info.sps_ws_bytes)
-    cap = 1 << 20
+    cap = 1 << 25
     cands = torch.empty(cap * 16, dtype=torch.uint8, device="cuda")
     count = torch.zeros(1, dtype=torch.int64, device="cuda")
     stream = torch.cuda.current_stream()

@@ -174,7 +174,7 @@ class _DeviceArray:
     """Zero-copy description of a library-owned float buffer."""
 
     def __init__(self, ptr: int, n: int):
-        self.__cuda_array_interface__ = {"shape": (n,), "typestr": "<f4", "data": (ptr, True),
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": "<f4", "data": (ptr, False),
                                          "version": 3, "strides": None}
 
 

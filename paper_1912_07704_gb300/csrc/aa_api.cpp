@@ -196,7 +196,9 @@ aa_status aa_sps_search_device(const aa_plan* p, int64_t nsamp, const float* d_d
     if (!d_dd) { set_error("d_dd is NULL"); return AA_ERR_ARG; }
     char* ws = static_cast<char*>(d_ws);
     unsigned* err = reinterpret_cast<unsigned*>(ws);
-    AA_CUDA(cudaMemsetAsync(err, 0, sizeof(unsigned), s), "clear error word");
+    AA_CUDA(cudaMemsetAsync(err, 0, 16, s), "clear error word and chunk counter");
+    unsigned long long* nchunks = reinterpret_cast<unsigned long long*>(ws + kChunkCounterOffset);
+    CandChunk* chunks = reinterpret_cast<CandChunk*>(ws + L.chunk_offset);
     double* rsw = reinterpret_cast<double*>(ws + kErrBlock);
     {
         ProfScope prof(kKRsqrt, s);
@@ -225,6 +227,9 @@ aa_status aa_sps_search_device(const aa_plan* p, int64_t nsamp, const float* d_d
         a.count = d_count;
         a.snr_out = d_snr_out ? d_snr_out + L.row_offset[r] : nullptr;
         a.err = err;
+        a.chunks = chunks;
+        a.nchunks = nchunks;
+        a.chunk_cap = L.chunk_cap;
         if (a.length <= 0) continue;
         {
             ProfScope prof(kKStats, s);
@@ -358,22 +363,40 @@ aa_status aa_sps_search(aa_plan* p, const aa_dd_result* dd, int32_t max_width, f
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) { delete res; return cuda_fail(e, "read candidate count"); }
     const int64_t stored = std::min<int64_t>((int64_t)total, cand_capacity);
+    // Records arrive as per-CTA runs (each ordered by t); order the runs by
+    // (dm_index, t0) through their headers and concatenate.
+    unsigned long long nchunks = 0;
+    std::vector<aa_candidate> raw;
+    std::vector<CandChunk> heads;
     try {
-        res->list.resize((size_t)stored);
+        raw.resize((size_t)stored);
+        res->list.reserve((size_t)stored);
     } catch (const std::bad_alloc&) {
         delete res;
         set_error("host allocation failed");
         return AA_ERR_NOMEM;
     }
-    if (stored > 0) {
-        e = cudaMemcpyAsync(res->list.data(), d_c, (size_t)stored * sizeof(aa_candidate),
+    e = cudaMemcpyAsync(&nchunks, static_cast<char*>(d_ws) + kChunkCounterOffset, sizeof nchunks,
+                        cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && stored > 0)
+        e = cudaMemcpyAsync(raw.data(), d_c, (size_t)stored * sizeof(aa_candidate),
                             cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) { delete res; return cuda_fail(e, "read candidates"); }
+    const int64_t nh = std::min<int64_t>((int64_t)nchunks, L.chunk_cap);
+    heads.resize((size_t)nh);
+    if (nh > 0) {
+        e = cudaMemcpyAsync(heads.data(), static_cast<char*>(d_ws) + L.chunk_offset,
+                            (size_t)nh * sizeof(CandChunk), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        if (e != cudaSuccess) { delete res; return cuda_fail(e, "read candidates"); }
+        if (e != cudaSuccess) { delete res; return cuda_fail(e, "read candidate chunks"); }
     }
-    std::sort(res->list.begin(), res->list.end(), [](const aa_candidate& a, const aa_candidate& b) {
-        return a.dm_index != b.dm_index ? a.dm_index < b.dm_index : a.t < b.t;
+    std::sort(heads.begin(), heads.end(), [](const CandChunk& a, const CandChunk& b) {
+        return a.dm_index != b.dm_index ? a.dm_index < b.dm_index : a.t0 < b.t0;
     });
+    for (const CandChunk& h : heads)
+        for (unsigned long long k = h.base; k < h.base + h.n && (int64_t)k < stored; ++k)
+            res->list.push_back(raw[(size_t)k]);
     res->total = (int64_t)total;
     unsigned h = 0, h2 = 0;
     e = cudaMemcpyAsync(&h, d_ws, sizeof h, cudaMemcpyDeviceToHost, s);

@@ -75,10 +75,11 @@ struct Layout {
     std::vector<int64_t> dec_pitch;   // elements, per entry of plan.decs
     std::vector<int64_t> dec_offset;  // bytes into the workspace
     int64_t dedisp_ws = 0;
-    // single-pulse workspace: [error word block][row stats][width tables]
+    // single-pulse workspace: [error word + chunk counter][1/sqrt(w)][row stats]
+    //                         [width tables][candidate chunk headers]
     int32_t max_width = 0;
     int32_t wpad = 0;
-    int64_t stats_offset = 0, table_offset = 0, sps_ws = 0;
+    int64_t stats_offset = 0, table_offset = 0, chunk_offset = 0, chunk_cap = 0, sps_ws = 0;
 };
 
 constexpr int64_t kErrBlock = 256;  // bytes reserved for the device error word
@@ -99,6 +100,19 @@ struct RowStats {
     int32_t zero_sigma;
 };
 static_assert(sizeof(RowStats) == 32, "RowStats layout");
+
+// Each boxcar CTA appends its candidates as one contiguous run ordered by t;
+// the run is described by a chunk header so the host can order the list by
+// sorting headers instead of records.
+struct CandChunk {
+    unsigned long long base;  // index of the run's first record
+    uint32_t n;               // records in the run
+    uint32_t dm_index;
+    uint32_t t0;              // first start time owned by the CTA
+    uint32_t reserved;
+};
+static_assert(sizeof(CandChunk) == 24, "CandChunk layout");
+constexpr int64_t kChunkCounterOffset = 8;  // bytes into the error block
 
 // ------------------------------------------------------------- profiling --
 enum KernelId {
@@ -159,6 +173,9 @@ struct SpsArgs {
     unsigned long long* count;
     float* snr_out;         // optional, row 0 of this range (same pitch)
     unsigned* err;
+    CandChunk* chunks;      // chunk headers (all ranges)
+    unsigned long long* nchunks;
+    int64_t chunk_cap;
 };
 cudaError_t launch_sps_stats(const SpsArgs& a, cudaStream_t s);
 cudaError_t launch_sps_boxcar(const SpsArgs& a, cudaStream_t s);

@@ -127,7 +127,13 @@ Layout make_layout(const aa_plan& p, int64_t nsamp, int32_t max_width) {
         L.stats_offset = s;
         s += round_up((int64_t)p.ndm_total * (int64_t)sizeof(RowStats), 256);
         L.table_offset = s;
-        s += (int64_t)p.ndm_total * L.wpad * 8;
+        s += round_up((int64_t)p.ndm_total * L.wpad * 8, 256);
+        int64_t chunks = 0;
+        for (size_t r = 0; r < p.ranges.size(); ++r)
+            chunks += (int64_t)p.ranges[r].desc.ndm * ((L.length[r] + kSpsOwned - 1) / kSpsOwned);
+        L.chunk_offset = s;
+        L.chunk_cap = chunks;
+        s += round_up(std::max<int64_t>(chunks, 1) * (int64_t)sizeof(CandChunk), 256);
         L.sps_ws = s;
     }
     return L;

@@ -8,8 +8,9 @@
 //             SNR_w = (S'_w - w (mu - m0)) / (sigma sqrt w) = S'_w r_w - c_w,
 //             S'_w = sum_{k<w} (y[t+k] - m0) summed exactly (FP32 when every
 //             partial sum of the tile fits in 2^24, int64 otherwise); then
-//             thresholded local maxima are appended to the candidate list
-//             with a warp-aggregated atomic.
+//             thresholded local maxima are appended to the candidate list,
+//             one atomic per CTA (the CTA's run is contiguous and ordered by t,
+//             and is described by a chunk header).
 //   width   : for each candidate, the smallest maximising width (same
 //             arithmetic as the boxcar kernel, bit for bit).
 #include <cfloat>
@@ -140,6 +141,15 @@ __device__ long long block_exclusive_scan(long long v, long long* scratch) {
     __syncthreads();
     const long long before = warp > 0 ? scratch[warp - 1] : 0;
     return before + inc - v;
+}
+
+// Exclusive scan that also returns the block total.
+template <int NT>
+__device__ long long block_exclusive_scan_total(long long v, long long* scratch, long long& total) {
+    const long long ex = block_exclusive_scan<NT>(v, scratch);
+    total = scratch[NT / 32 - 1];
+    __syncthreads();  // scratch may be reused after this
+    return ex;
 }
 
 template <int NT>
@@ -285,39 +295,47 @@ __global__ void __launch_bounds__(NT, 2) sps_boxcar_kernel(SpsArgs a, int ntiles
     for (int i = 0; i < M; ++i) Bs[M * threadIdx.x + i] = B[i];
     __syncthreads();
 
-    const int lane = threadIdx.x & 31;
-    const unsigned lt_mask = (1u << lane) - 1u;
     const bool zero_sigma = st.zero_sigma != 0;
-#pragma unroll 1
+    unsigned cmask = 0;
+#pragma unroll
     for (int i = 0; i < M; ++i) {
         const int p = M * threadIdx.x + i;
         const int64_t t = t0 - 1 + p;
-        const bool owned = p >= 1 && p <= kSpsTile - 2 && t < L;
-        const float v = Bs[p];
-        bool cand = false;
-        if (owned) {
+        if (p >= 1 && p <= kSpsTile - 2 && t < L) {
+            const float v = Bs[p];
             if (a.snr_out) a.snr_out[(int64_t)row * a.pitch + t] = zero_sigma ? 0.0f : v;
-            cand = !zero_sigma && v >= a.threshold && v > Bs[p - 1] && v >= Bs[p + 1];
+            if (!zero_sigma && v >= a.threshold && v > Bs[p - 1] && v >= Bs[p + 1]) cmask |= 1u << i;
         }
-        const unsigned mask = __ballot_sync(0xffffffffu, cand);
-        if (mask) {
-            const int leader = __ffs(mask) - 1;
-            unsigned long long base = 0;
-            if (lane == leader) base = atomicAdd(a.count, (unsigned long long)__popc(mask));
-            base = __shfl_sync(0xffffffffu, base, leader);
-            if (cand) {
-                const unsigned long long idx = base + __popc(mask & lt_mask);
-                if (idx < (unsigned long long)a.capacity) {
-                    aa_candidate c;
-                    c.dm_index = (uint32_t)(a.dm_offset + row);
-                    c.t = (uint32_t)t;
-                    c.width = 0;
-                    c.range = (uint8_t)a.range;
-                    c.reserved = 0;
-                    c.snr = v;
-                    a.cands[idx] = c;
-                }
+    }
+    // One atomic per CTA: the CTA's candidates form one contiguous run in t order.
+    long long total = 0;
+    const long long my_off = block_exclusive_scan_total<NT>(__popc(cmask), scratch, total);
+    if (total > 0) {
+        __shared__ unsigned long long s_base;
+        const uint32_t dm_index = (uint32_t)(a.dm_offset + row);
+        if (threadIdx.x == 0) {
+            s_base = atomicAdd(a.count, (unsigned long long)total);
+            const unsigned long long ci = atomicAdd(a.nchunks, 1ull);
+            if (ci < (unsigned long long)a.chunk_cap)
+                a.chunks[ci] = CandChunk{s_base, (uint32_t)total, dm_index, (uint32_t)t0, 0u};
+        }
+        __syncthreads();
+        unsigned long long idx = s_base + (unsigned long long)my_off;
+        while (cmask) {
+            const int i = __ffs(cmask) - 1;
+            cmask &= cmask - 1;
+            if (idx < (unsigned long long)a.capacity) {
+                const int p = M * threadIdx.x + i;
+                aa_candidate c;
+                c.dm_index = dm_index;
+                c.t = (uint32_t)(t0 - 1 + p);
+                c.width = 0;
+                c.range = (uint8_t)a.range;
+                c.reserved = 0;
+                c.snr = Bs[p];
+                a.cands[idx] = c;
             }
+            ++idx;
         }
     }
 }

@@ -72,10 +72,14 @@ def pulses_single(dm=150.0, t0=8192, n_w=16, amplitude=40.0) -> list:
     return [Pulse(dm, t0, n_w, amplitude)]
 
 
-def pulses_ska(w: Workload, max_delay: Callable[[float], int], n: int = 20) -> list:
-    """n pulses: DM ~ U[50, 2000], width log-uniform 64 us .. 16 ms,
-    A ~ U[1, 4] counts, start times evenly spaced with jitter so that no two
-    pulses overlap and every pulse ends before the series does.
+def pulses_ska(w: Workload, max_delay: Callable[[float], int], n: int = 20,
+               snr_range=(8.0, 150.0)) -> list:
+    """n pulses: DM ~ U[50, 2000], width log-uniform 64 us .. 16 ms, and an
+    amplitude set from a target matched-filter SNR ~ U[snr_range]:
+    A = SNR * 16 / (sqrt(nchans) * sqrt(n_w)) counts (noise std 16 per
+    channel-sample, box of n_w samples summed over all channels).  Start times
+    are evenly spaced with jitter so that no two pulses overlap and every
+    pulse ends before the series does.
 
     max_delay(dm) must return the largest per-channel delay (full-rate
     samples) of a pulse at that DM; it is supplied by the caller.
@@ -83,8 +87,9 @@ def pulses_ska(w: Workload, max_delay: Callable[[float], int], n: int = 20) -> l
     rng = np.random.Generator(np.random.PCG64(w.pulse_seed))
     dms = rng.uniform(50.0, 2000.0, n)
     widths_s = np.exp(rng.uniform(np.log(64e-6), np.log(16e-3), n))
-    amps = rng.uniform(1.0, 4.0, n)
+    snrs = rng.uniform(snr_range[0], snr_range[1], n)
     n_w = np.maximum(1, np.rint(widths_s / w.tsamp)).astype(np.int64)
+    amps = snrs * 16.0 / (np.sqrt(w.nchans) * np.sqrt(n_w))
     slot = w.nsamp // n
     out = []
     for i in range(n):

@@ -26,15 +26,17 @@ def ska_run(oracle):
     nsamp = W.nsamp
     # the bench configuration: no B output
     out = plan.dedisperse_device(x, nsamp)
-    cap = 1 << 20
+    cap = 1 << 25
     cands, count, _ = plan.sps_search_device(out, nsamp, W.max_width, W.threshold, cap)
     torch.cuda.synchronize()
+    assert int(count.item()) <= cap, int(count.item())
     bench_cands = candidates_from_device(cands, count, cap)
     # the same call with the optional B(t) output
     snr = torch.full_like(out, float("nan"))
     cands2, count2, _ = plan.sps_search_device(out, nsamp, W.max_width, W.threshold, cap,
                                                snr_out=snr)
     torch.cuda.synchronize()
+    assert int(count2.item()) == int(count.item())
     snr_cands = candidates_from_device(cands2, count2, cap)
     xh = x[:, :nsamp].cpu().numpy()
     del x, cands, cands2
