@@ -261,6 +261,33 @@ aa_status aa_candidates_view(const aa_candidates* c, const aa_candidate** host,
 /* Free a candidate list.  NULL is a no-op. */
 void aa_candidates_destroy(aa_candidates* c);
 
+/* ---------------------------------------------- no-allocation search -- */
+
+/* Size of the fixed scratch area behind aa_sps_search_device_noalloc. */
+#define AA_NOALLOC_SCRATCH_BYTES (16u << 20)
+
+/* The single-pulse search of aa_sps_search_device for callers that cannot
+ * allocate device memory while running (for example a real-time
+ * beam-processing loop whose memory is fixed at start-up, where an
+ * allocation could synchronise the device, or a plug-in whose host framework
+ * owns all device allocations).  It has no counterpart in the paper.
+ * Arguments and results are those of aa_sps_search_device without d_ws and
+ * ws_bytes: the scratch is a fixed AA_NOALLOC_SCRATCH_BYTES device array that
+ * every GPU loading the library holds until the process exits.  The caller
+ * still passes the dedispersed input, the candidate array, the count and the
+ * optional B(t) output.  The first call on a device looks up the array's
+ * device address (with that device current); make that first call before
+ * any stream capture.  All calls share the one array: calls whose GPU work
+ * overlaps race.  Returns AA_ERR_ARG if the search needs more scratch than
+ * the array holds (aa_plan_query(...).sps_ws_bytes > AA_NOALLOC_SCRATCH_BYTES),
+ * otherwise what aa_sps_search_device returns.  Calls no allocation
+ * routine. */
+aa_status aa_sps_search_device_noalloc(const aa_plan* plan, int64_t nsamp, const float* d_dd,
+                                       int32_t max_width, float threshold,
+                                       aa_candidate* d_cands, int64_t cand_capacity,
+                                       unsigned long long* d_count, float* d_snr_out,
+                                       aa_stream_t stream);
+
 /* ------------------------------------------------------------- profiling -- */
 
 /* Kernel timing (tracing).  While enabled, every kernel the library launches

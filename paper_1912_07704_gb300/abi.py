@@ -92,6 +92,8 @@ _SIG = {
                                           ctypes.POINTER(_I64)]),
     "aa_candidates_destroy": (None, [_P]),
     "aa_debug_inject": (ctypes.c_int, [_I32, _I64]),
+    "aa_sps_search_device_noalloc": (ctypes.c_int, [_P, _I64, _P, _I32, _F32, _P, _I64, _P, _P,
+                                                    _P]),
     "aa_profile_enable": (ctypes.c_int, [_I32]),
     "aa_profile_read": (ctypes.c_int, [_I32, ctypes.POINTER(_I64), ctypes.POINTER(ctypes.c_double)]),
     "aa_profile_kernel_name": (ctypes.c_char_p, [_I32]),
@@ -259,3 +261,12 @@ def profile_snapshot() -> dict:
             return out
         out[name] = aa_profile_read(k)
         k += 1
+
+
+def aa_sps_search_device_noalloc(plan, nsamp, d_dd, max_width, threshold, d_cands, capacity,
+                                 d_count, d_snr_out, stream) -> int:
+    """Returns the status code (callers check it: AA_ERR_ARG means the
+    search needs more scratch than the built-in area holds)."""
+    return lib().aa_sps_search_device_noalloc(plan, int(nsamp), d_dd, int(max_width),
+                                              float(threshold), d_cands, int(capacity), d_count,
+                                              d_snr_out, stream)
