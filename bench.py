@@ -35,6 +35,17 @@ SM_MAX_MHZ_DEFAULT = 2070.0
 BOXCAR_OPS_PER_WS = 2.5
 
 
+def workload(name: str):
+    from paper_1912_07704_gb300 import synth
+    import dataclasses
+    if name == "ska":
+        return synth.SKA_4096
+    if name == "ska-small":
+        # same channels, plan and widths, 2^17 samples: the profiling case
+        return dataclasses.replace(synth.SKA_4096, name="ska-4096ch-2^17", nsamp=1 << 17)
+    raise ValueError(name)
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -174,7 +185,7 @@ def bench_reference(args):
         return
     from paper_1912_07704_gb300 import synth
     import torch
-    w = synth.SKA_4096
+    w = workload(args.workload)
     from oracle import oracle as o
     d1 = lambda dm: o.shifts(w.nchans, w.fch1, w.foff, w.tsamp, dm, 1)
     pulses = synth.pulses_ska(w, lambda dm: int(d1(dm).max()))
@@ -208,7 +219,7 @@ def bench_ours(args):
     torch.cuda.set_device(local)
     if ws > 1:
         dist.init_process_group("gloo")
-    w = synth.SKA_4096
+    w = workload(args.workload)
     plan = Plan.from_workload(w)
     plan.bind(local)
     info = plan.query(w.nsamp, w.max_width)
@@ -362,6 +373,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["ska", "ska-small"], default="ska")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

@@ -226,6 +226,7 @@ aa_status aa_sps_search_device(const aa_plan* p, int64_t nsamp, const float* d_d
         a.capacity = cand_capacity;
         a.count = d_count;
         a.snr_out = d_snr_out ? d_snr_out + L.row_offset[r] : nullptr;
+        a.prune = d_snr_out ? 0 : 1;  // B(t) everywhere requested: exhaustive
         a.err = err;
         a.chunks = chunks;
         a.nchunks = nchunks;
@@ -237,11 +238,6 @@ aa_status aa_sps_search_device(const aa_plan* p, int64_t nsamp, const float* d_d
         }
         ProfScope prof(kKBoxcar, s);
         AA_CUDA(launch_sps_boxcar(a, s), "sps boxcar launch");
-    }
-    for (size_t r = 0; r < p->ranges.size(); ++r) {
-        if (args[r].length <= 0) continue;
-        ProfScope prof(kKWidth, s);
-        AA_CUDA(launch_sps_width(args[r], s), "sps width launch");
     }
     return AA_OK;
 }

@@ -113,15 +113,24 @@ __global__ void __launch_bounds__(kDedispThreads, 2)
     __syncthreads();
 
     // Producer (warp 0): stage chunk k (channels k*cc ..) into stage k % nstage.
-    auto issue = [&](int k) {
+    // Lane l < cc handles channel k*cc + l; its first/last-trial delays (lo,
+    // hi) are loaded one stage ahead so the global-load latency stays hidden.
+    auto load_lohi = [&](int k, int& lo, int& hi) {
+        const int c = k * cc + lane;
+        if (k < nchunks && lane < cc && c < C) {
+            lo = __ldg(&a.shifts[(int64_t)d0 * C + c]);
+            hi = __ldg(&a.shifts[(int64_t)dlast * C + c]);
+        } else {
+            lo = hi = 0;
+        }
+    };
+    auto issue = [&](int k, int s_lo, int s_hi) {
         const int s = k % nstage;
         const int c0 = k * cc;
         uint32_t bytes = 0;
         int64_t src_off = 0;
         if (lane < cc && c0 + lane < C) {
             const int c = c0 + lane;
-            const int s_lo = __ldg(&a.shifts[(int64_t)d0 * C + c]);
-            const int s_hi = __ldg(&a.shifts[(int64_t)dlast * C + c]);
             const int64_t base = ((t0 + s_lo) / A16) * A16;
             const int64_t end = t0 + kTau + s_hi + SPW;
             int64_t nb = ((end - base) * EB + 15) / 16 * 16;
@@ -142,10 +151,22 @@ __global__ void __launch_bounds__(kDedispThreads, 2)
                           &bars[s]);
     };
 
-    int next_issue = 0;
-    if (warp == 0)
-        for (; next_issue < min(nstage - 1, nchunks); ++next_issue) issue(next_issue);
-    next_issue = min(nstage - 1, nchunks);
+    int pre_lo = 0, pre_hi = 0;  // delays of the next chunk to issue (warp 0)
+    if (warp == 0) {
+        for (int k = 0; k < min(nstage - 1, nchunks); ++k) {
+            int lo, hi;
+            load_lohi(k, lo, hi);
+            issue(k, lo, hi);
+        }
+        load_lohi(nstage - 1, pre_lo, pre_hi);
+    }
+    int next_issue = min(nstage - 1, nchunks);
+    // Each thread owns at most one (trial, channel) word offset per chunk;
+    // its delay is prefetched one chunk ahead.
+    const bool own = tid < kDmPerBlock * cc;
+    const int own_dl = own ? tid / cc : 0, own_cl = own ? tid - (tid / cc) * cc : 0;
+    const int64_t own_row = (int64_t)min(d0 + own_dl, dlast) * C;
+    int sh_next = (own && own_cl < C) ? __ldg(&a.shifts[own_row + own_cl]) : 0;
     __syncthreads();  // bases[] of the first stages visible to all threads
 
     uint32_t acc[kDmPerWarp][QW][SWAR];
@@ -185,6 +206,9 @@ __global__ void __launch_bounds__(kDedispThreads, 2)
     for (int k = 0; k < nchunks; ++k) {
         const int s = k % nstage;
         const uint32_t parity = (uint32_t)(k / nstage) & 1u;
+        const int sh_cur = sh_next;
+        if (own && k + 1 < nchunks && (k + 1) * cc + own_cl < C)
+            sh_next = __ldg(&a.shifts[own_row + (k + 1) * cc + own_cl]);
         const bool ok = mbar_wait_bounded(&bars[s], parity, wait_limit_ns);
         uint32_t* st = stages + s * stage_w;
         const int c0 = k * cc;
@@ -192,24 +216,23 @@ __global__ void __launch_bounds__(kDedispThreads, 2)
         if (ok) {
             // shifted copies 1..NCOPY-1 of every staged row
             if constexpr (NCOPY > 1) {
+                // 4 rows at a time, 64 threads per row (no index division)
                 const int per = rw - 1;
-                for (int idx = tid; idx < cvalid * per; idx += kDedispThreads) {
-                    const int cl = idx / per, j = idx - cl * per;
+                for (int cl = tid >> 6; cl < cvalid; cl += kDedispThreads >> 6) {
                     uint32_t* row = st + (size_t)cl * NCOPY * rw;
-                    const uint32_t w0 = row[j], w1 = row[j + 1];
+                    for (int j = tid & 63; j < per; j += 64) {
+                        const uint32_t w0 = row[j], w1 = row[j + 1];
 #pragma unroll
-                    for (int q = 1; q < NCOPY; ++q)
-                        row[q * rw + j] = __funnelshift_r(w0, w1, q * 8 * EB);
+                        for (int q = 1; q < NCOPY; ++q)
+                            row[q * rw + j] = __funnelshift_r(w0, w1, q * 8 * EB);
+                    }
                 }
             }
             // word offset of every (DM, channel) of this chunk
-            int* ot = offs + s * kDmPerBlock * cc;
-            const int* bs = bases + s * cc;
-            for (int idx = tid; idx < kDmPerBlock * cvalid; idx += kDedispThreads) {
-                const int dl = idx / cvalid, cl = idx - dl * cvalid;
-                const int d = min(d0 + dl, dlast);
-                const int o = __ldg(&a.shifts[(int64_t)d * C + c0 + cl]) - bs[cl];
-                ot[dl * cc + cl] = (cl * NCOPY + o % SPW) * rw + o / SPW;
+            if (own && own_cl < cvalid) {
+                const int o = sh_cur - bases[s * cc + own_cl];
+                offs[(s * kDmPerBlock + own_dl) * cc + own_cl] =
+                    (own_cl * NCOPY + o % SPW) * rw + o / SPW;
             }
         }
         if (!__syncthreads_and(ok)) {
@@ -221,7 +244,10 @@ __global__ void __launch_bounds__(kDedispThreads, 2)
             return;
         }
         if (next_issue < nchunks) {
-            if (warp == 0) issue(next_issue);
+            if (warp == 0) {
+                issue(next_issue, pre_lo, pre_hi);
+                load_lohi(next_issue + 1, pre_lo, pre_hi);
+            }
             ++next_issue;
         }
 

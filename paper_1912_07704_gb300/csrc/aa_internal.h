@@ -116,7 +116,7 @@ constexpr int64_t kChunkCounterOffset = 8;  // bytes into the error block
 
 // ------------------------------------------------------------- profiling --
 enum KernelId {
-    kKDecimate = 0, kKDedispU8, kKDedispU16, kKRsqrt, kKStats, kKBoxcar, kKWidth, kNumKernels
+    kKDecimate = 0, kKDedispU8, kKDedispU16, kKRsqrt, kKStats, kKBoxcar, kNumKernels
 };
 
 // RAII: records CUDA events around a launch on `s` while profiling is on.
@@ -173,13 +173,12 @@ struct SpsArgs {
     unsigned long long* count;
     float* snr_out;         // optional, row 0 of this range (same pitch)
     unsigned* err;
+    int32_t prune;          // skip width blocks bounded below the threshold
     CandChunk* chunks;      // chunk headers (all ranges)
     unsigned long long* nchunks;
     int64_t chunk_cap;
 };
 cudaError_t launch_sps_stats(const SpsArgs& a, cudaStream_t s);
 cudaError_t launch_sps_boxcar(const SpsArgs& a, cudaStream_t s);
-// Fill widths of the candidates [first, first+n) recorded for one range.
-cudaError_t launch_sps_width(const SpsArgs& a, cudaStream_t s);
 
 }  // namespace aa

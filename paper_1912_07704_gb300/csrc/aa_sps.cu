@@ -11,8 +11,9 @@
 //             thresholded local maxima are appended to the candidate list,
 //             one atomic per CTA (the CTA's run is contiguous and ordered by t,
 //             and is described by a chunk header).
-//   width   : for each candidate, the smallest maximising width (same
-//             arithmetic as the boxcar kernel, bit for bit).
+//             The CTA then resolves each of its candidates' width (the
+//             smallest maximising w) from the series it staged, with the same
+//             arithmetic bit for bit.
 #include <cfloat>
 #include <cstdint>
 
@@ -177,31 +178,35 @@ __device__ void block_minmax(long long& mn, long long& mx, long long* scratch) {
 constexpr int M = kSpsSlots;
 constexpr int NT = kSpsThreads;
 
-// ys: staged series minus m0 (sentinel outside [0, L)), index i <-> t0-1+i.
-// Thread owns slots p = M*tid + i.  Running sums in FP32, exact because the
-// caller checked that every partial sum of the tile is an integer of
-// magnitude <= 2^24.  Slot i at width w = w0+s+1 adds ys[M*tid + i + w0 + s].
-__device__ __forceinline__ void boxcar_fast(const float* __restrict__ ys,
-                                            const float2* __restrict__ tab, int wpad,
-                                            float (&B)[M]) {
-    const float* yb = ys + M * threadIdx.x;
-    float win[2 * M];
+// Exact-FP32 tiles.  P is the prefix-sum array of the staged series (index
+// i <-> start time t0-1+i): P[i] = sum of y - m0 over the valid samples before
+// i, -kBig once a window would run past the series end.  Every window sum
+// S_w(t) = P[p+w] - P[p] is an exact FP32 integer (the caller checked that
+// the prefix range of the tile is <= 2^24), so this is bit for bit the
+// running sum.  Thread owns slots p = M*tid + i; base[i] = P[p] (or +kBig for
+// a start outside the series).  Width blocks w-1 in [2^k, 2^(k+1)), k >= 4,
+// whose bit is set in `skip` are not evaluated (their SNRs are bounded below
+// the threshold by the caller).
+constexpr float kBig = 1.2676506002282294e30f;  // 2^100
+
+__device__ __forceinline__ void boxcar_prefix(const float* __restrict__ P,
+                                              const float2* __restrict__ tab, int wpad,
+                                              const float (&base)[M], unsigned skip,
+                                              float (&B)[M]) {
+    const float* pb = P + M * threadIdx.x;
 #pragma unroll
-    for (int k = 0; k < M; k += 4) {
-        const float4 v = *reinterpret_cast<const float4*>(yb + k);
-        win[k] = v.x; win[k + 1] = v.y; win[k + 2] = v.z; win[k + 3] = v.w;
-    }
-    float S[M];
-#pragma unroll
-    for (int i = 0; i < M; ++i) {
-        S[i] = 0.0f;
-        B[i] = -FLT_MAX;
-    }
+    for (int i = 0; i < M; ++i) B[i] = -FLT_MAX;
     for (int w0 = 0; w0 < wpad; w0 += M) {
+        if (w0 >= 16 && ((skip >> (31 - __clz(w0))) & 1u)) {
+            // jump to the next width block
+            w0 = (2 << (31 - __clz(w0))) - M;
+            continue;
+        }
+        float win[2 * M];  // win[k] = P[p_thread + w0 + k]
 #pragma unroll
-        for (int k = 0; k < M; k += 4) {
-            const float4 v = *reinterpret_cast<const float4*>(yb + w0 + M + k);
-            win[M + k] = v.x; win[M + k + 1] = v.y; win[M + k + 2] = v.z; win[M + k + 3] = v.w;
+        for (int k = 0; k < 2 * M; k += 4) {
+            const float4 v = *reinterpret_cast<const float4*>(pb + w0 + k);
+            win[k] = v.x; win[k + 1] = v.y; win[k + 2] = v.z; win[k + 3] = v.w;
         }
 #pragma unroll
         for (int s = 0; s < M; s += 2) {
@@ -209,15 +214,11 @@ __device__ __forceinline__ void boxcar_fast(const float* __restrict__ ys,
             const float2 rc1 = tab[w0 + s + 1];
 #pragma unroll
             for (int i = 0; i < M; ++i) {
-                S[i] += win[i + s];
-                const float v0 = fmaf(S[i], rc0.x, rc0.y);
-                S[i] += win[i + s + 1];
-                const float v1 = fmaf(S[i], rc1.x, rc1.y);
+                const float v0 = fmaf(win[i + s + 1] - base[i], rc0.x, rc0.y);
+                const float v1 = fmaf(win[i + s + 2] - base[i], rc1.x, rc1.y);
                 B[i] = max3f(B[i], v0, v1);
             }
         }
-#pragma unroll
-        for (int k = 0; k < M; ++k) win[k] = win[M + k];
     }
 }
 
@@ -239,9 +240,16 @@ __device__ __noinline__ float boxcar_exact_slot(const float* __restrict__ ys,
     return best;
 }
 
+// Shared memory after the main loop: the table region is reused for B(t)
+// (kSpsTile floats) followed by the candidate positions (kSpsTile u16).
+__host__ __device__ constexpr int sps_region_bytes(int wpad) {
+    return (wpad * 8 > kSpsTile * 6) ? wpad * 8 : kSpsTile * 6;
+}
+
 __global__ void __launch_bounds__(NT, 2) sps_boxcar_kernel(SpsArgs a, int ntiles) {
     extern __shared__ __align__(16) float sm[];
     __shared__ long long scratch[2 * NT / 32];
+    __shared__ unsigned long long s_base;
     const int wpad = a.wpad;
     const int ylen = kSpsTile + wpad + M;
     float* ys = sm;
@@ -253,6 +261,7 @@ __global__ void __launch_bounds__(NT, 2) sps_boxcar_kernel(SpsArgs a, int ntiles
     const float* y = a.dd + (int64_t)row * a.pitch;
     const RowStats st = a.stats[row];
     const float m0 = st.m0;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
     for (int i = threadIdx.x; i < ylen; i += NT) {
         const int64_t t = t0 - 1 + i;
@@ -263,34 +272,79 @@ __global__ void __launch_bounds__(NT, 2) sps_boxcar_kernel(SpsArgs a, int ntiles
     __syncthreads();
 
     // Largest |partial sum| of the tile = range of the prefix sums of ys over
-    // its valid samples: FP32 running sums are exact when it is <= 2^24.
+    // its valid samples: FP32 sums are exact when it is <= 2^24.
     const int seg = (ylen + NT - 1) / NT;
     const int i0 = min(ylen, threadIdx.x * seg), i1 = min(ylen, i0 + seg);
     long long run = 0, mn = 0, mx = 0;
     for (int i = i0; i < i1; ++i) {
         const float v = ys[i];
         if (v > kSentinelTest) {
-            run += (long long)v;
+            run += (long long)(int)v;
             mn = min(mn, run);
             mx = max(mx, run);
         }
     }
     const long long before = block_exclusive_scan<NT>(run, scratch);
-    mn += before;
-    mx += before;
-    block_minmax<NT>(mn, mx, scratch);
-    const bool fast = (mx - mn) <= (1ll << 24);
+    long long gmn = mn + before, gmx = mx + before;
+    block_minmax<NT>(gmn, gmx, scratch);
+    const bool fast = (gmx - gmn) <= (1ll << 24);
+    // valid start/sample positions: i in [va, vb]  (t = t0-1+i in [0, L))
+    const int va = t0 == 0 ? 1 : 0;
+    const int vb = (int)min((int64_t)ylen - 1, L - t0);
 
     float B[M];
     if (fast) {
-        boxcar_fast(ys, tab, wpad, B);
+        // ys -> prefix sums P, in place (exact FP32 integers)
+        __syncthreads();
+        float runf = (float)before;
+        for (int i = i0; i < i1; ++i) {
+            const float v = ys[i];
+            ys[i] = i > vb + 1 ? -kBig : runf;
+            if (v > kSentinelTest) runf += v;
+        }
+        __syncthreads();
+        const float* P = ys;
+        float base[M];
+        float pmin = FLT_MAX;
+#pragma unroll
+        for (int i = 0; i < M; ++i) {
+            const int p = M * threadIdx.x + i;
+            const bool valid = p >= va && p <= vb;
+            base[i] = valid ? P[p] : kBig;
+            if (valid) pmin = fminf(pmin, base[i]);
+        }
+        // Per-warp bound on SNR over a width block: window sums are at most
+        // max P(ends) - min P(starts); SNR = (S - w f)/(sigma sqrt w).
+        unsigned skip = 0;
+        if (a.prune && a.threshold > 0.0f) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) pmin = fminf(pmin, __shfl_xor_sync(0xffffffffu, pmin, o));
+            const double f = st.mu - (double)m0;
+            const float inv_sigma = (float)st.inv_sigma;
+            const int p_first = M * 32 * warp;
+            for (int k = 4; (1 << k) < a.max_width; ++k) {
+                const int w1 = (1 << k) + 1, w2 = min(2 << k, a.max_width);
+                const int lo = p_first + w1, hi = min(ylen - 1, p_first + M * 32 - 1 + w2);
+                float pmax = -FLT_MAX;
+                for (int j = lo + lane; j <= hi; j += 32) pmax = fmaxf(pmax, P[j]);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) pmax = fmaxf(pmax, __shfl_xor_sync(0xffffffffu, pmax, o));
+                const double drift = f >= 0 ? (double)w1 * f : (double)w2 * f;
+                const double num = (double)pmax - (double)pmin - drift;
+                const double ub = num > 0 ? num * (double)inv_sigma / sqrt((double)w1) : num;
+                if (pmin == FLT_MAX || ub * (1.0 + 1e-4) + 1e-4 < (double)a.threshold - 1e-3)
+                    skip |= 1u << k;
+            }
+        }
+        boxcar_prefix(P, tab, wpad, base, skip, B);
     } else {
 #pragma unroll
         for (int i = 0; i < M; ++i) B[i] = boxcar_exact_slot(ys, tab, wpad, i);
     }
 
-    __syncthreads();  // everyone done with ys / tab
-    float* Bs = sm;   // reuse
+    __syncthreads();  // everyone done with the table
+    float* Bs = reinterpret_cast<float*>(tab);  // B(t) of every slot
+    unsigned short* plist = reinterpret_cast<unsigned short*>(Bs + kSpsTile);
 #pragma unroll
     for (int i = 0; i < M; ++i) Bs[M * threadIdx.x + i] = B[i];
     __syncthreads();
@@ -310,70 +364,70 @@ __global__ void __launch_bounds__(NT, 2) sps_boxcar_kernel(SpsArgs a, int ntiles
     // One atomic per CTA: the CTA's candidates form one contiguous run in t order.
     long long total = 0;
     const long long my_off = block_exclusive_scan_total<NT>(__popc(cmask), scratch, total);
-    if (total > 0) {
-        __shared__ unsigned long long s_base;
-        const uint32_t dm_index = (uint32_t)(a.dm_offset + row);
-        if (threadIdx.x == 0) {
-            s_base = atomicAdd(a.count, (unsigned long long)total);
-            const unsigned long long ci = atomicAdd(a.nchunks, 1ull);
-            if (ci < (unsigned long long)a.chunk_cap)
-                a.chunks[ci] = CandChunk{s_base, (uint32_t)total, dm_index, (uint32_t)t0, 0u};
-        }
-        __syncthreads();
-        unsigned long long idx = s_base + (unsigned long long)my_off;
+    if (total == 0) return;
+    const uint32_t dm_index = (uint32_t)(a.dm_offset + row);
+    if (threadIdx.x == 0) {
+        s_base = atomicAdd(a.count, (unsigned long long)total);
+        const unsigned long long ci = atomicAdd(a.nchunks, 1ull);
+        if (ci < (unsigned long long)a.chunk_cap)
+            a.chunks[ci] = CandChunk{s_base, (uint32_t)total, dm_index, (uint32_t)t0, 0u};
+    }
+    {
+        int j = (int)my_off;
         while (cmask) {
             const int i = __ffs(cmask) - 1;
             cmask &= cmask - 1;
-            if (idx < (unsigned long long)a.capacity) {
-                const int p = M * threadIdx.x + i;
-                aa_candidate c;
-                c.dm_index = dm_index;
-                c.t = (uint32_t)(t0 - 1 + p);
-                c.width = 0;
-                c.range = (uint8_t)a.range;
-                c.reserved = 0;
-                c.snr = Bs[p];
-                a.cands[idx] = c;
-            }
-            ++idx;
+            plist[j++] = (unsigned short)(M * threadIdx.x + i);
         }
     }
-}
+    __syncthreads();
 
-// One warp per candidate of this range: recompute SNR_w for w = 1..min(W, L-t)
-// with the boxcar kernel's arithmetic and keep the smallest maximising w.
-__global__ void __launch_bounds__(256) sps_width_kernel(SpsArgs a) {
-    const int lane = threadIdx.x & 31;
-    const int64_t nstored = min((long long)*a.count, (long long)a.capacity);
-    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t ci = wid; ci < nstored; ci += nw) {
-        aa_candidate c = a.cands[ci];
-        if (c.range != (uint8_t)a.range) continue;
-        const int row = (int)c.dm_index - a.dm_offset;
-        const int64_t t = c.t;
-        const float* y = a.dd + (int64_t)row * a.pitch;
-        const float2* tab = a.table + (int64_t)row * a.wpad;
-        const long long m0 = (long long)a.stats[row].m0;
-        const int wmax = (int)min((int64_t)a.max_width, a.length - t);
-        const int seg = (wmax + 31) / 32;
-        const int w_lo = lane * seg + 1, w_hi = min(wmax, (lane + 1) * seg);
-        long long part = 0;
-        for (int w = w_lo; w <= w_hi; ++w) part += (long long)y[t + w - 1] - m0;
-        long long inc = part;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const long long u = __shfl_up_sync(0xffffffffu, inc, o);
-            if (lane >= o) inc += u;
-        }
-        long long S = inc - part;
+    // Width of each candidate: the smallest w reaching B(t), recomputed from
+    // the staged series with the main loop's arithmetic (exact running sums,
+    // fmaf of the correctly rounded sum), one warp per candidate, widths
+    // interleaved over lanes with a warp prefix sum.
+    for (int q = warp; q < (int)total; q += NT / 32) {
+        const int p = plist[q];
+        const int64_t t = t0 - 1 + p;
+        const int wmax = (int)min((int64_t)a.max_width, L - t);
+        const float* yq = ys + p;  // exact path: yq[w-1] = y[t+w-1] - m0
+        const float target = Bs[p];
         float best = -FLT_MAX;
         int bw = 0x7fffffff;
-        for (int w = w_lo; w <= w_hi; ++w) {
-            S += (long long)y[t + w - 1] - m0;
-            const float2 rc = tab[w - 1];
-            const float v = fmaf(__ll2float_rn(S), rc.x, rc.y);
-            if (v > best) { best = v; bw = w; }
+        if (fast) {
+            // prefix form: S_w = P[p+w] - P[p], exact
+            const float* P = ys;
+            const float b0 = P[p];
+            for (int w0 = 0; w0 < wmax; w0 += 32) {
+                const int w = w0 + lane + 1;
+                if (w <= wmax) {
+                    const float2 rc = __ldg(gtab + w - 1);
+                    const float snr = fmaf(P[p + w] - b0, rc.x, rc.y);
+                    if (snr > best) { best = snr; bw = w; }
+                }
+                // widths are visited in increasing order: stop at the chunk
+                // where B(t) is first reached
+                if (__any_sync(0xffffffffu, best == target)) break;
+            }
+        } else {
+            long long base = 0;
+            for (int w0 = 0; w0 < wmax; w0 += 32) {
+                const int w = w0 + lane + 1;
+                long long v = (w <= wmax) ? (long long)yq[w - 1] : 0;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const long long u = __shfl_up_sync(0xffffffffu, v, o);
+                    if (lane >= o) v += u;
+                }
+                const long long S = base + v;
+                base += __shfl_sync(0xffffffffu, v, 31);
+                if (w <= wmax) {
+                    const float2 rc = __ldg(gtab + w - 1);
+                    const float snr = fmaf(__ll2float_rn(S), rc.x, rc.y);
+                    if (snr > best) { best = snr; bw = w; }
+                }
+                if (__any_sync(0xffffffffu, best == target)) break;
+            }
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -381,10 +435,16 @@ __global__ void __launch_bounds__(256) sps_width_kernel(SpsArgs a) {
             const int ow = __shfl_xor_sync(0xffffffffu, bw, o);
             if (ob > best || (ob == best && ow < bw)) { best = ob; bw = ow; }
         }
-        if (lane == 0) {
+        const unsigned long long idx = s_base + (unsigned long long)q;
+        if (lane == 0 && idx < (unsigned long long)a.capacity) {
+            aa_candidate c;
+            c.dm_index = dm_index;
+            c.t = (uint32_t)t;
             c.width = (uint16_t)bw;
+            c.range = (uint8_t)a.range;
+            c.reserved = 0;
             c.snr = best;
-            a.cands[ci] = c;
+            a.cands[idx] = c;
         }
     }
 }
@@ -404,7 +464,7 @@ cudaError_t launch_rsqrt_table(double* t, int wpad, cudaStream_t s) {
 
 size_t sps_boxcar_smem(int wpad) {
     const int ylen = kSpsTile + wpad + M;
-    return (size_t)((ylen + 3) & ~3) * 4 + (size_t)wpad * 8;
+    return (size_t)((ylen + 3) & ~3) * 4 + (size_t)sps_region_bytes(wpad);
 }
 
 cudaError_t launch_sps_boxcar(const SpsArgs& a, cudaStream_t s) {
@@ -419,10 +479,5 @@ cudaError_t launch_sps_boxcar(const SpsArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_sps_width(const SpsArgs& a, cudaStream_t s) {
-    if (a.nrows <= 0 || a.length <= 0 || a.capacity <= 0) return cudaSuccess;
-    sps_width_kernel<<<152 * 4, 256, 0, s>>>(a);
-    return cudaGetLastError();
-}
 
 }  // namespace aa

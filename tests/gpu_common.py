@@ -12,14 +12,23 @@ SNR_TOL = 1e-4  # absolute SNR tolerance against the FP64 oracle
 
 def run_gpu(plan: Plan, x, W: int, thr: float, capacity: int = 1 << 16, want_snr=True):
     """Dedisperse + search on the GPU.  Returns (flat dd, flat snr, sorted
-    candidates, total count, nsamp)."""
+    candidates, total count, nsamp).  With want_snr the search runs twice:
+    with the B(t) output (exhaustive widths) and without it (width blocks
+    bounded below the threshold skipped); both candidate lists must agree."""
     d, nsamp = plan.device_input(x)
     out = plan.dedisperse_device(d, nsamp)
     snr = torch.full_like(out, float("nan")) if want_snr else None
     cands, count, snr = plan.sps_search_device(out, nsamp, W, thr, capacity, snr_out=snr)
     torch.cuda.synchronize()
     total = int(count.item())
-    return out, snr, candidates_from_device(cands, count, capacity), total, nsamp
+    got = candidates_from_device(cands, count, capacity)
+    if want_snr:
+        c2, n2, _ = plan.sps_search_device(out, nsamp, W, thr, capacity)
+        torch.cuda.synchronize()
+        assert int(n2.item()) == total
+        if total <= capacity:  # on overflow, which records are stored is unspecified
+            assert np.array_equal(candidates_from_device(c2, n2, capacity), got)
+    return out, snr, got, total, nsamp
 
 
 def oracle_candidates(oracle, rows_y, W, thr, dm_offset, rng, windows=None):
