@@ -77,9 +77,18 @@ __device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s per stage: far beyond any real copy
 
 // SPW = samples per 32-bit word: 4 for raw uint8 input, 2 for decimated uint16.
+// acc + x through the FMA pipe (integer multiply-add by a runtime 1): the byte
+// split already occupies the ALU pipe.
+__device__ __forceinline__ uint32_t mad_add(uint32_t x, uint32_t one, uint32_t acc) {
+    uint32_t d;
+    asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(x), "r"(one), "r"(acc));
+    return d;
+}
+
 template <int SPW>
 __global__ void __launch_bounds__(kDedispThreads, 2)
-    dedisperse_kernel(DedispArgs a, int ndm_blocks, uint64_t wait_limit_ns, int fault_skip_chunk) {
+    dedisperse_kernel(DedispArgs a, int ndm_blocks, uint64_t wait_limit_ns, int fault_skip_chunk,
+                      uint32_t one) {
     constexpr int QW = kTau / (32 * SPW);  // words per lane per DM trial
     constexpr int NCOPY = SPW;             // shifted copies of each staged row
     constexpr int EB = 4 / SPW;            // bytes per sample
@@ -216,15 +225,19 @@ __global__ void __launch_bounds__(kDedispThreads, 2)
         if (ok) {
             // shifted copies 1..NCOPY-1 of every staged row
             if constexpr (NCOPY > 1) {
-                // 4 rows at a time, 64 threads per row (no index division)
-                const int per = rw - 1;
-                for (int cl = tid >> 6; cl < cvalid; cl += kDedispThreads >> 6) {
+                // one warp per row, 4 words per lane (128-bit loads/stores)
+                for (int cl = warp; cl < cvalid; cl += kDedispWarps) {
                     uint32_t* row = st + (size_t)cl * NCOPY * rw;
-                    for (int j = tid & 63; j < per; j += 64) {
-                        const uint32_t w0 = row[j], w1 = row[j + 1];
+                    for (int j = 4 * lane; j < rw - 1; j += 128) {
+                        const uint4 w = *reinterpret_cast<const uint4*>(row + j);
+                        const uint32_t w4 = (j + 4 < rw) ? row[j + 4] : 0u;
 #pragma unroll
-                        for (int q = 1; q < NCOPY; ++q)
-                            row[q * rw + j] = __funnelshift_r(w0, w1, q * 8 * EB);
+                        for (int q = 1; q < NCOPY; ++q) {
+                            const int sh = q * 8 * EB;
+                            *reinterpret_cast<uint4*>(row + q * rw + j) =
+                                make_uint4(__funnelshift_r(w.x, w.y, sh), __funnelshift_r(w.y, w.z, sh),
+                                           __funnelshift_r(w.z, w.w, sh), __funnelshift_r(w.w, w4, sh));
+                        }
                     }
                 }
             }
@@ -263,10 +276,13 @@ __global__ void __launch_bounds__(kDedispThreads, 2)
                 for (int j = 0; j < QW; ++j) {
                     const uint32_t v0 = p0[32 * j], v1 = p1[32 * j];
                     if constexpr (SPW == 4) {
-                        acc[kk][j][0] += (v0 & 0x00ff00ffu) + (v1 & 0x00ff00ffu);
-                        acc[kk][j][1] += __byte_perm(v0, 0u, 0x4341) + __byte_perm(v1, 0u, 0x4341);
+                        acc[kk][j][0] = mad_add(v0 & 0x00ff00ffu, one, acc[kk][j][0]);
+                        acc[kk][j][0] = mad_add(v1 & 0x00ff00ffu, one, acc[kk][j][0]);
+                        acc[kk][j][1] = mad_add(__byte_perm(v0, 0u, 0x4341), one, acc[kk][j][1]);
+                        acc[kk][j][1] = mad_add(__byte_perm(v1, 0u, 0x4341), one, acc[kk][j][1]);
                     } else {
-                        acc[kk][j][0] += v0 + v1;
+                        acc[kk][j][0] = mad_add(v0, one, acc[kk][j][0]);
+                        acc[kk][j][0] = mad_add(v1, one, acc[kk][j][0]);
                     }
                 }
             }
@@ -276,10 +292,10 @@ __global__ void __launch_bounds__(kDedispThreads, 2)
                 for (int j = 0; j < QW; ++j) {
                     const uint32_t v0 = p0[32 * j];
                     if constexpr (SPW == 4) {
-                        acc[kk][j][0] += v0 & 0x00ff00ffu;
-                        acc[kk][j][1] += __byte_perm(v0, 0u, 0x4341);
+                        acc[kk][j][0] = mad_add(v0 & 0x00ff00ffu, one, acc[kk][j][0]);
+                        acc[kk][j][1] = mad_add(__byte_perm(v0, 0u, 0x4341), one, acc[kk][j][1]);
                     } else {
-                        acc[kk][j][0] += v0;
+                        acc[kk][j][0] = mad_add(v0, one, acc[kk][j][0]);
                     }
                 }
             }
@@ -360,7 +376,7 @@ cudaError_t launch_dedisperse(const DedispArgs& a, cudaStream_t s) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)a.smem);
     if (e != cudaSuccess) return e;
     kern<<<(unsigned)nblocks, kDedispThreads, a.smem, s>>>(a, ndmb, g_wait_limit_ns,
-                                                            g_fault_skip_chunk);
+                                                            g_fault_skip_chunk, 1u);
     return cudaGetLastError();
 }
 

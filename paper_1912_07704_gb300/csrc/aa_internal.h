@@ -17,8 +17,8 @@ namespace aa {
 // Dedispersion tile: a CTA of kDedispWarps warps covers kDmPerBlock DM trials
 // x kTau output samples; channels stream through shared memory in stages of
 // `cc` channels (bulk-async copies), each stage reused by all the CTA's DMs.
-constexpr int kDedispWarps = 8;
-constexpr int kDmPerWarp = 2;
+constexpr int kDedispWarps = 16;
+constexpr int kDmPerWarp = 1;
 constexpr int kDmPerBlock = kDedispWarps * kDmPerWarp;  // 16
 constexpr int kTau = 512;                                // output samples per CTA
 constexpr int kDedispThreads = kDedispWarps * 32;

@@ -263,12 +263,38 @@ __global__ void __launch_bounds__(NT, 2) sps_boxcar_kernel(SpsArgs a, int ntiles
     const float m0 = st.m0;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
-    for (int i = threadIdx.x; i < ylen; i += NT) {
-        const int64_t t = t0 - 1 + i;
-        ys[i] = (t >= 0 && t < L) ? __ldg(y + t) - m0 : kSentinel;
+    // Stage the series (minus m0, sentinel outside [0, L)) and the width
+    // table; loads are issued in batches so that their latencies overlap.
+    constexpr int kBatch = 8;
+    for (int i0b = threadIdx.x; i0b < ylen; i0b += NT * kBatch) {
+        float v[kBatch];
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+            const int i = i0b + u * NT;
+            const int64_t t = t0 - 1 + i;
+            v[u] = (i < ylen && t >= 0 && t < L) ? __ldg(y + t) - m0 : kSentinel;
+        }
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u)
+            if (i0b + u * NT < ylen) ys[i0b + u * NT] = v[u];
     }
     const float2* gtab = a.table + (int64_t)row * wpad;
-    for (int i = threadIdx.x; i < wpad; i += NT) tab[i] = __ldg(gtab + i);
+    {
+        const float4* g4 = reinterpret_cast<const float4*>(gtab);  // wpad is even
+        float4* t4 = reinterpret_cast<float4*>(tab);
+        const int n4 = wpad / 2;
+        for (int i0b = threadIdx.x; i0b < n4; i0b += NT * kBatch) {
+            float4 v[kBatch];
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u) {
+                const int i = i0b + u * NT;
+                if (i < n4) v[u] = __ldg(g4 + i);
+            }
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u)
+                if (i0b + u * NT < n4) t4[i0b + u * NT] = v[u];
+        }
+    }
     __syncthreads();
 
     // Largest |partial sum| of the tile = range of the prefix sums of ys over
