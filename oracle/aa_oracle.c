@@ -181,3 +181,42 @@ int64_t oracle_peaks(const double* B, int64_t n, double thr, int64_t* out_t, int
     }
     return found;
 }
+
+/* ---- differentiable (float-weighted) form -------------------------------
+ * Forward:  y[d][t] = sum_c w[c] * x[c][t + s(c,d)],  t < L
+ * Adjoint (transpose of the forward in x, definition written as a scatter):
+ *   gx[c][t + s(c,d)] += w[c] * gy[d][t]
+ *   gw[c]             += gy[d][t] * x[c][t + s(c,d)]
+ * Loss:     mean over d, t of (y[d][t] - T[d][t])^2
+ * All in FP64.
+ */
+void oracle_forward_f64(const double* x, int32_t nchans, int64_t pitch, const double* w,
+                        const int32_t* shifts, int64_t L, double* out)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t t = 0; t < L; ++t) {
+        double acc = 0.0;
+        for (int32_t c = 0; c < nchans; ++c)
+            acc += w[c] * x[(int64_t)c * pitch + t + shifts[c]];
+        out[t] = acc;
+    }
+}
+
+/* shifts: [ndm][nchans]; gy: [ndm][L]; gx: [nchans][pitch] (accumulated);
+ * gw: [nchans] (accumulated). */
+void oracle_adjoint_f64(const double* x, int32_t nchans, int64_t pitch, const double* w,
+                        const int32_t* shifts, int32_t ndm, const double* gy, int64_t L,
+                        double* gx, double* gw)
+{
+#pragma omp parallel for schedule(static)
+    for (int32_t c = 0; c < nchans; ++c) {
+        for (int32_t d = 0; d < ndm; ++d) {
+            const int32_t s = shifts[(int64_t)d * nchans + c];
+            for (int64_t t = 0; t < L; ++t) {
+                const double g = gy[(int64_t)d * L + t];
+                gx[(int64_t)c * pitch + t + s] += w[c] * g;
+                gw[c] += g * x[(int64_t)c * pitch + t + s];
+            }
+        }
+    }
+}

@@ -72,6 +72,10 @@ def lib():
         L.oracle_boxcar.restype = None
         L.oracle_peaks.argtypes = [vp, i64, f64, vp, i64]
         L.oracle_peaks.restype = i64
+        L.oracle_forward_f64.argtypes = [vp, i32, i64, vp, vp, i64, vp]
+        L.oracle_forward_f64.restype = None
+        L.oracle_adjoint_f64.argtypes = [vp, i32, i64, vp, vp, i32, vp, i64, vp, vp]
+        L.oracle_adjoint_f64.restype = None
         _lib = L
     return _lib
 
@@ -252,3 +256,44 @@ def search_row(y: np.ndarray, W: int, thr: float, dm_index: int, rng: int,
             fragile = near or mg[k] < FRAGILE_CMP
             cands.append(Candidate(dm_index, t, int(wb[k]), rng, float(v), bool(fragile)))
     return cands, B[t_lo - a:t_hi - a], wb[t_lo - a:t_hi - a], mu, sigma
+
+
+# ----------------------------------------------------------------------------
+# Differentiable form (per-channel float weights), FP64
+# ----------------------------------------------------------------------------
+
+def forward_f64(x: np.ndarray, w: np.ndarray, shift_table: np.ndarray, L: int) -> np.ndarray:
+    """y[d][t] = sum_c w_c x[c][t + s(c,d)] for every row of shift_table [D][C]."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    C, T = x.shape
+    out = np.zeros((shift_table.shape[0], max(L, 0)), np.float64)
+    for d in range(shift_table.shape[0]):
+        sh = np.ascontiguousarray(shift_table[d], dtype=np.int32)
+        if L > 0:
+            assert L - 1 + int(sh.max()) < T
+            row = np.empty(L, np.float64)
+            lib().oracle_forward_f64(_ptr(x), C, T, _ptr(w), _ptr(sh), L, _ptr(row))
+            out[d] = row
+    return out
+
+
+def adjoint_f64(x: np.ndarray, w: np.ndarray, shift_table: np.ndarray, gy: np.ndarray):
+    """(gx [C][T], gw [C]) of <gy, y(x, w)> (transpose of the forward)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    gy = np.ascontiguousarray(gy, dtype=np.float64)
+    C, T = x.shape
+    D, L = gy.shape
+    sh = np.ascontiguousarray(shift_table, dtype=np.int32)
+    gx = np.zeros((C, T), np.float64)
+    gw = np.zeros(C, np.float64)
+    if L > 0:
+        lib().oracle_adjoint_f64(_ptr(x), C, T, _ptr(w), _ptr(sh), D, _ptr(gy), L, _ptr(gx),
+                                 _ptr(gw))
+    return gx, gw
+
+
+def mse_f64(x, w, shift_table, L, template) -> float:
+    y = forward_f64(x, w, shift_table, L)
+    return float(np.mean((y - template) ** 2)) if y.size else 0.0
