@@ -367,18 +367,75 @@ def bench_ours(args):
         dist.destroy_process_group()
 
 
+def _time_cuda(fn, steps, warmup):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(steps):
+        fn()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / steps
+
+
+def bench_adjoint(args):
+    """Differentiable form (1024 ch, 65536 float samples, 1024 trials): float
+    forward, fused MSE loss, loss + gradients (chunked recomputation), next
+    to the plain uint8 path on the same plan shape."""
+    import torch
+    from paper_1912_07704_gb300 import synth
+    from paper_1912_07704_gb300.api import Plan
+    w = synth.ADJ_1024
+    plan = Plan.from_workload(w)
+    plan.bind()
+    lay = plan.layout(w.nsamp)[0]
+
+    def delays(dm):
+        with Plan(w.nchans, w.fch1, w.foff, w.tsamp, [(float(dm), 0.0, 1, 1)]) as p1:
+            return p1.shifts(0)[0]
+
+    pulse = [synth.Pulse(400.0, w.nsamp // 4, 16, 1.0)]
+    x = synth.float_filterbank(w, pulse, delays, device="cuda")
+    wt = synth.channel_weights(w.nchans, w.data_seed + 100, device="cuda")
+    tmpl = plan.f32_forward(synth.float_filterbank(w, pulse, delays, device="cuda", noise=False),
+                            torch.ones_like(wt))
+    y = plan.alloc_output(w.nsamp)
+    t_fwd = _time_cuda(lambda: plan.f32_forward(x, wt, out=y), args.steps, args.warmup)
+    t_loss = _time_cuda(lambda: plan.f32_mse(x, wt, tmpl), args.steps, args.warmup)
+    t_grad = _time_cuda(lambda: plan.f32_mse(x, wt, tmpl, grad=True), args.steps, args.warmup)
+    xq = (x * 16 + 128).round().clamp(0, 255).to(torch.uint8)
+    dq, nsamp = plan.device_input(xq)
+    out = plan.alloc_output(nsamp)
+    wsd = plan.alloc_workspace(plan.query(nsamp).dedisp_ws_bytes)
+    t_u8 = _time_cuda(lambda: plan.dedisperse_device(dq, nsamp, out=out, ws=wsd), args.steps,
+                      args.warmup)
+    fma = lay.ndm * lay.length * w.nchans
+    line = {"metric": "differentiable dedispersion: loss + gradients per second", "workload": w.name,
+            "unit": "ms", "steps": args.steps, "warmup": args.warmup,
+            "f32_forward_ms": t_fwd, "mse_loss_ms": t_loss, "mse_loss_and_grad_ms": t_grad,
+            "u8_dedisperse_same_plan_ms": t_u8,
+            "forward_tflops": 2 * fma / t_fwd / 1e9, "grad_over_forward": t_grad / t_fwd,
+            "dm_trial_samples": lay.ndm * lay.length}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["ska", "ska-small"], default="ska")
+    ap.add_argument("--workload", choices=["ska", "ska-small", "adjoint"], default="ska")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         bench_reference(args)
+    elif args.workload == "adjoint":
+        bench_adjoint(args)
     else:
         bench_ours(args)
 

@@ -158,6 +158,7 @@ typedef struct aa_plan_info {
     int64_t host_path_bytes;   /* peak device bytes of aa_dedisperse + aa_sps_search */
     int64_t dm_trial_samples;  /* sum over ranges of ndm * L */
     double dm_max;             /* largest trial DM */
+    int64_t f32_ws_bytes;      /* scratch for the differentiable-form calls */
 } aa_plan_info;
 
 aa_status aa_plan_query(const aa_plan* plan, int64_t nsamp, int32_t max_width,
@@ -222,6 +223,37 @@ aa_status aa_sps_search_device(const aa_plan* plan, int64_t nsamp, const float* 
  * by the calls above (synchronises `stream`).  AA_OK, or AA_ERR_TIMEOUT if a
  * bounded device-side wait gave up. */
 aa_status aa_workspace_status(void* d_ws, aa_stream_t stream);
+
+/* ------------------------------------------------- differentiable form -- */
+
+/* Float input with per-channel weights (every range must have dec == 1,
+ * else AA_ERR_CONFIG):  y[d][t] = sum_c w[c] * x[c][t + s(c,d)]  (FP32 FMA,
+ * channels summed in index order).  d_x: float [nchans][x_pitch] (x_pitch >=
+ * nsamp), d_w: float [nchans], d_y: float [dd_elems] in the layout of
+ * aa_dedisperse_device.  Stream-ordered. */
+aa_status aa_dedisperse_f32_device(const aa_plan* plan, const float* d_x, int64_t nsamp,
+                                   int64_t x_pitch, const float* d_w, float* d_y,
+                                   aa_stream_t stream);
+
+/* Transpose of the float forward: given d_gy (layout of d_y), writes
+ * gx[c][u] = w[c] * sum_d gy[d][u - s(c,d)] (float [nchans][x_pitch],
+ * overwritten for u < nsamp) and gw[c] = sum_{d,t} gy[d][t] * x[c][t + s(c,d)]
+ * (float [nchans], overwritten).  d_ws: aa_plan_info.f32_ws_bytes of scratch. */
+aa_status aa_dedisperse_f32_adjoint_device(const aa_plan* plan, const float* d_x, int64_t nsamp,
+                                           int64_t x_pitch, const float* d_w, const float* d_gy,
+                                           float* d_gx, float* d_gw, void* d_ws, size_t ws_bytes,
+                                           aa_stream_t stream);
+
+/* Mean squared error of the float forward against a template (layout of
+ * d_y): *d_loss (device double) = mean over every (trial, t < L) of
+ * (y - T)^2, reduced in the forward without storing y.  If d_gx and d_gw are
+ * both non-NULL the gradients of the loss with respect to x and w are written
+ * too; y is then recomputed chunk by chunk of trials (never stored whole).
+ * Stream-ordered. */
+aa_status aa_dedisperse_f32_mse_device(const aa_plan* plan, const float* d_x, int64_t nsamp,
+                                       int64_t x_pitch, const float* d_w, const float* d_template,
+                                       double* d_loss, float* d_gx, float* d_gw, void* d_ws,
+                                       size_t ws_bytes, aa_stream_t stream);
 
 /* ------------------------------------------ host-buffer (API-owned) path -- */
 

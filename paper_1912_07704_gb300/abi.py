@@ -56,7 +56,7 @@ class aa_plan_info(ctypes.Structure):
                 ("dd_elems", ctypes.c_int64), ("dedisp_ws_bytes", ctypes.c_int64),
                 ("sps_ws_bytes", ctypes.c_int64), ("table_bytes", ctypes.c_int64),
                 ("host_path_bytes", ctypes.c_int64), ("dm_trial_samples", ctypes.c_int64),
-                ("dm_max", ctypes.c_double)]
+                ("dm_max", ctypes.c_double), ("f32_ws_bytes", ctypes.c_int64)]
 
 
 class aa_candidate(ctypes.Structure):
@@ -94,6 +94,11 @@ _SIG = {
     "aa_debug_inject": (ctypes.c_int, [_I32, _I64]),
     "aa_sps_search_device_noalloc": (ctypes.c_int, [_P, _I64, _P, _I32, _F32, _P, _I64, _P, _P,
                                                     _P]),
+    "aa_dedisperse_f32_device": (ctypes.c_int, [_P, _P, _I64, _I64, _P, _P, _P]),
+    "aa_dedisperse_f32_adjoint_device": (ctypes.c_int, [_P, _P, _I64, _I64, _P, _P, _P, _P, _P,
+                                                        ctypes.c_size_t, _P]),
+    "aa_dedisperse_f32_mse_device": (ctypes.c_int, [_P, _P, _I64, _I64, _P, _P, _P, _P, _P, _P,
+                                                    ctypes.c_size_t, _P]),
     "aa_profile_enable": (ctypes.c_int, [_I32]),
     "aa_profile_read": (ctypes.c_int, [_I32, ctypes.POINTER(_I64), ctypes.POINTER(ctypes.c_double)]),
     "aa_profile_kernel_name": (ctypes.c_char_p, [_I32]),
@@ -270,3 +275,22 @@ def aa_sps_search_device_noalloc(plan, nsamp, d_dd, max_width, threshold, d_cand
     return lib().aa_sps_search_device_noalloc(plan, int(nsamp), d_dd, int(max_width),
                                               float(threshold), d_cands, int(capacity), d_count,
                                               d_snr_out, stream)
+
+
+def aa_dedisperse_f32_device(plan, d_x, nsamp, x_pitch, d_w, d_y, stream) -> None:
+    check(lib().aa_dedisperse_f32_device(plan, d_x, int(nsamp), int(x_pitch), d_w, d_y, stream),
+          "aa_dedisperse_f32_device")
+
+
+def aa_dedisperse_f32_adjoint_device(plan, d_x, nsamp, x_pitch, d_w, d_gy, d_gx, d_gw, d_ws,
+                                     ws_bytes, stream) -> None:
+    check(lib().aa_dedisperse_f32_adjoint_device(plan, d_x, int(nsamp), int(x_pitch), d_w, d_gy,
+                                                 d_gx, d_gw, d_ws, int(ws_bytes), stream),
+          "aa_dedisperse_f32_adjoint_device")
+
+
+def aa_dedisperse_f32_mse_device(plan, d_x, nsamp, x_pitch, d_w, d_tmpl, d_loss, d_gx, d_gw,
+                                 d_ws, ws_bytes, stream) -> None:
+    check(lib().aa_dedisperse_f32_mse_device(plan, d_x, int(nsamp), int(x_pitch), d_w, d_tmpl,
+                                             d_loss, d_gx, d_gw, d_ws, int(ws_bytes), stream),
+          "aa_dedisperse_f32_mse_device")

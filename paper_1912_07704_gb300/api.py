@@ -138,6 +138,45 @@ class Plan:
                                  ws.data_ptr(), ws.numel(), _stream_handle(stream))
         return cands, count, snr_out
 
+    # differentiable form ------------------------------------------------------
+    def f32_forward(self, x: torch.Tensor, w: torch.Tensor, out=None, stream=None) -> torch.Tensor:
+        """y = sum_c w_c x[c][t + s(c,d)] for float x [nchans][>= nsamp] (row
+        stride = pitch); returns the flat output buffer (layout of the u8 path)."""
+        self.bind()
+        nsamp = x.shape[1]
+        out = self.alloc_output(nsamp) if out is None else out
+        abi.aa_dedisperse_f32_device(self.handle, x.data_ptr(), nsamp, x.stride(0), w.data_ptr(),
+                                     out.data_ptr(), _stream_handle(stream))
+        return out
+
+    def f32_adjoint(self, x: torch.Tensor, w: torch.Tensor, gy: torch.Tensor, stream=None):
+        self.bind()
+        nsamp = x.shape[1]
+        gx = torch.empty_like(x)
+        gw = torch.empty_like(w)
+        ws = self.alloc_workspace(self.query(nsamp).f32_ws_bytes)
+        abi.aa_dedisperse_f32_adjoint_device(self.handle, x.data_ptr(), nsamp, x.stride(0),
+                                             w.data_ptr(), gy.data_ptr(), gx.data_ptr(),
+                                             gw.data_ptr(), ws.data_ptr(), ws.numel(),
+                                             _stream_handle(stream))
+        return gx, gw
+
+    def f32_mse(self, x: torch.Tensor, w: torch.Tensor, template: torch.Tensor, grad=False,
+                stream=None):
+        """(loss [float64 scalar tensor], gx or None, gw or None)."""
+        self.bind()
+        nsamp = x.shape[1]
+        loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+        ws = self.alloc_workspace(self.query(nsamp).f32_ws_bytes)
+        gx = torch.empty_like(x) if grad else None
+        gw = torch.empty_like(w) if grad else None
+        abi.aa_dedisperse_f32_mse_device(self.handle, x.data_ptr(), nsamp, x.stride(0),
+                                         w.data_ptr(), template.data_ptr(), loss.data_ptr(),
+                                         gx.data_ptr() if grad else 0,
+                                         gw.data_ptr() if grad else 0,
+                                         ws.data_ptr(), ws.numel(), _stream_handle(stream))
+        return loss[0], gx, gw
+
     def range_views(self, flat: torch.Tensor, nsamp: int) -> list:
         """[ndm_r][L_r] views of a flat output buffer, one per range."""
         views = []

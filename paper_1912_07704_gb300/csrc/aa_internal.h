@@ -44,6 +44,8 @@ struct RangePlan {
     int flush = 256;       // channels between SWAR flushes (multiple of cc)
     size_t smem = 0;       // dynamic shared memory per CTA
     int dec_src = 1;       // decimation source buffer (1 = raw input)
+    int f32_span = 0;      // differentiable form: delay spread over any 16 consecutive trials
+    int f32_cspan = 0;     // ... and over any 16 consecutive channels
     int32_t* d_shifts = nullptr;  // device copy (inside the plan's table block)
 };
 
@@ -80,6 +82,8 @@ struct Layout {
     int32_t max_width = 0;
     int32_t wpad = 0;
     int64_t stats_offset = 0, table_offset = 0, chunk_offset = 0, chunk_cap = 0, sps_ws = 0;
+    // differentiable-form workspace: [loss sum][w-gradient partials][residual chunk]
+    int64_t f32_part_offset = 0, f32_resid_offset = 0, f32_ws = 0;
 };
 
 constexpr int64_t kErrBlock = 256;  // bytes reserved for the device error word
@@ -116,7 +120,8 @@ constexpr int64_t kChunkCounterOffset = 8;  // bytes into the error block
 
 // ------------------------------------------------------------- profiling --
 enum KernelId {
-    kKDecimate = 0, kKDedispU8, kKDedispU16, kKRsqrt, kKStats, kKBoxcar, kNumKernels
+    kKDecimate = 0, kKDedispU8, kKDedispU16, kKRsqrt, kKStats, kKBoxcar, kKF32Fwd, kKF32Adj,
+    kNumKernels
 };
 
 // RAII: records CUDA events around a launch on `s` while profiling is on.
@@ -180,5 +185,48 @@ struct SpsArgs {
 };
 cudaError_t launch_sps_stats(const SpsArgs& a, cudaStream_t s);
 cudaError_t launch_sps_boxcar(const SpsArgs& a, cudaStream_t s);
+
+// ---------------------------------------------------- differentiable form --
+struct F32FwdArgs {
+    const float* x;
+    int64_t x_pitch;
+    int32_t nchans;
+    int64_t nsamp;
+    const float* w;
+    const int32_t* shifts;
+    int32_t d_begin, d_end;
+    int64_t length;
+    int32_t rowlen;
+    float* y;
+    int64_t pitch;
+    const float* tmpl;
+    double* loss_sum;
+    float* resid;
+    int64_t rpitch;
+    float scale;
+};
+struct F32AdjArgs {
+    const float* x;
+    int64_t x_pitch;
+    int32_t nchans;
+    int64_t nsamp;
+    const float* w;
+    const int32_t* shifts;
+    int32_t d_begin, d_end;
+    const float* gy;
+    int64_t gpitch;
+    int64_t length;
+    int32_t rowlen;
+    float* gx;
+    float* gw_part;
+    float* gw;
+};
+constexpr int kF32Chunk = 256;  // DM trials per recomputation chunk of the loss gradient
+int f32_fwd_rowlen(int span);
+int f32_adj_rowlen(int cspan);
+int f32_adj_tiles(int64_t nsamp);
+cudaError_t launch_f32_forward(int mode, const F32FwdArgs& p, cudaStream_t s);
+cudaError_t launch_f32_adjoint(const F32AdjArgs& p, cudaStream_t s);
+cudaError_t launch_finish_loss(const double* sum, double n, double* loss, cudaStream_t s);
 
 }  // namespace aa

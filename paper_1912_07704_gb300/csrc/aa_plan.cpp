@@ -84,6 +84,17 @@ static aa_status build_strategy(aa_plan& p) {
         r.nstage = nstage;
         r.flush = (std::min(max_flush, 256) / cc) * cc;
         r.smem = dedisp_smem(r, cc, nstage);
+        if (dec == 1) {  // spans used by the differentiable (float) form
+            int sp = 0, csp = 0;
+            for (int d = 0; d < ndm; ++d) {
+                const int32_t* a = &r.shifts[(size_t)d * C];
+                const int32_t* b = &r.shifts[(size_t)std::min(ndm - 1, d + 15) * C];
+                for (int c = 0; c < C; ++c) sp = std::max(sp, std::abs(b[c] - a[c]));
+                for (int c = 0; c < C; ++c) csp = std::max(csp, std::abs(a[std::min(C - 1, c + 15)] - a[c]));
+            }
+            r.f32_span = sp;
+            r.f32_cspan = csp;
+        }
     }
     // decimation cascade: each decimated buffer is built from the largest
     // already-built decimation that divides it (or from the raw input).
@@ -135,6 +146,16 @@ Layout make_layout(const aa_plan& p, int64_t nsamp, int32_t max_width) {
         L.chunk_cap = chunks;
         s += round_up(std::max<int64_t>(chunks, 1) * (int64_t)sizeof(CandChunk), 256);
         L.sps_ws = s;
+    }
+    {
+        int64_t s = kErrBlock;  // loss accumulator (double) lives at offset 0
+        L.f32_part_offset = s;
+        s += round_up((int64_t)p.nchans * f32_adj_tiles(std::max<int64_t>(nsamp, 1)) * 4, 256);
+        L.f32_resid_offset = s;
+        int64_t maxpitch = 0;
+        for (size_t r = 0; r < p.ranges.size(); ++r) maxpitch = std::max(maxpitch, L.pitch[r]);
+        s += (int64_t)kF32Chunk * maxpitch * 4;
+        L.f32_ws = s;
     }
     return L;
 }
@@ -311,6 +332,7 @@ aa_status aa_plan_query(const aa_plan* p, int64_t nsamp, int32_t max_width, aa_p
                             L.sps_ws + 256;
     info->dm_trial_samples = L.dm_trial_samples;
     info->dm_max = p->dm_max;
+    info->f32_ws_bytes = L.f32_ws;
     return AA_OK;
 }
 

@@ -151,3 +151,44 @@ def noise_filterbank(nchans: int, nsamp: int, seed: int, device="cpu",
     gen.manual_seed(seed)
     v = torch.randn((nchans, nsamp), generator=gen, device=dev, dtype=torch.float32)
     return v.mul_(std).add_(mean).round_().clamp_(0.0, 255.0).to(torch.uint8)
+
+
+# Differentiable form: 1024 channels over 300 MHz, 65536 float samples
+# ~N(0, 1), 1024 trials DM 0..511.5 step 0.5, one pulse at DM 400.
+ADJ_1024 = Workload("adjoint-1024ch-65536", 1024, 1508.0, -0.29296875, 64e-6, 65536,
+                    ((0.0, 0.5, 1024, 1),), 0, 0.0, 3)
+# its finite-difference check size: 256 channels, 4096 samples, DM 0..127.5
+ADJ_256 = Workload("adjoint-256ch-4096", 256, 1508.0, -1.171875, 64e-6, 4096,
+                   ((0.0, 0.5, 256, 1),), 0, 0.0, 4)
+
+
+def float_filterbank(w: Workload, pulses: Sequence[Pulse],
+                     delays: Callable[[float], np.ndarray], device="cpu",
+                     noise: bool = True) -> torch.Tensor:
+    """float32 [nchans][nsamp]: N(0, 1) noise (seeded) plus box pulses of
+    amplitude A (delays supplied by the caller)."""
+    dev = torch.device(device)
+    C, T = w.nchans, w.nsamp
+    if noise:
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(w.data_seed)
+        x = torch.randn((C, T), generator=gen, device=dev, dtype=torch.float32)
+    else:
+        x = torch.zeros((C, T), device=dev, dtype=torch.float32)
+    for p in pulses:
+        d = np.asarray(delays(p.dm), dtype=np.int64)
+        rows = np.repeat(np.arange(C, dtype=np.int64), p.n_w)
+        cols = np.repeat(p.t0 + d, p.n_w) + np.tile(np.arange(p.n_w, dtype=np.int64), C)
+        keep = cols < T
+        ri = torch.from_numpy(rows[keep]).to(dev)
+        ci = torch.from_numpy(cols[keep]).to(dev)
+        x.index_put_((ri, ci), torch.full((ri.numel(),), float(p.amplitude), device=dev),
+                     accumulate=True)
+    return x
+
+
+def channel_weights(nchans: int, seed: int, device="cpu") -> torch.Tensor:
+    """Per-channel weights ~U[0.5, 1.5] (seeded)."""
+    gen = torch.Generator(device=torch.device(device))
+    gen.manual_seed(seed)
+    return torch.rand(nchans, generator=gen, device=device, dtype=torch.float32) + 0.5
