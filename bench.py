@@ -422,13 +422,65 @@ def bench_adjoint(args):
     print(json.dumps(line), flush=True)
 
 
+def bench_batched(args):
+    """32 uneven beams (1024/4096 ch, 2^17..2^20 samples, DM_max 500..3000):
+    one CUDA graph of persistent work-queue kernels vs the beams run one
+    after another through the single-beam path, same GPU, same results."""
+    import torch
+    from paper_1912_07704_gb300 import synth
+    from paper_1912_07704_gb300.api import Batch, Plan
+    beams = synth.batched_beams(32)
+    plans = [Plan.from_workload(w) for w in beams]
+    for p in plans:
+        p.bind()
+    batch = Batch(plans, [w.nsamp for w in beams], 8192, 6.0, capacity=1 << 25)
+    dm_samples = 0
+    for i, (w, p) in enumerate(zip(beams, plans)):
+        def delays(dm, w=w):
+            with Plan(w.nchans, w.fch1, w.foff, w.tsamp, [(float(dm), 0.0, 1, 1)]) as p1:
+                return p1.shifts(0)[0]
+        pulses = synth.pulses_ska(w, lambda dm: int(delays(dm).max()), n=4)
+        x = synth.make_filterbank(w, pulses, delays, device="cuda")
+        batch.input_view(i)[:, : w.nsamp].copy_(x)
+        del x
+        dm_samples += p.query(w.nsamp).dm_trial_samples
+    torch.cuda.synchronize()
+    t_batch = _time_cuda(batch.run, args.steps, args.warmup)
+    nwaves, nbytes = batch.info()
+    arr, total = batch.candidates()
+    # the same beams through the single-beam path, one after another
+    info = [p.query(w.nsamp, 8192) for p, w in zip(plans, beams)]
+    out = torch.empty(max(i.dd_elems for i in info), dtype=torch.float32, device="cuda")
+    wsd = torch.empty(max(i.dedisp_ws_bytes for i in info), dtype=torch.uint8, device="cuda")
+    wss = torch.empty(max(i.sps_ws_bytes for i in info), dtype=torch.uint8, device="cuda")
+    cands = torch.empty((1 << 25) * 16, dtype=torch.uint8, device="cuda")
+    count = torch.zeros(1, dtype=torch.int64, device="cuda")
+    views = [batch.input_view(i) for i in range(len(beams))]
+
+    def one_by_one():
+        for i, (p, w) in enumerate(zip(plans, beams)):
+            p.dedisperse_device(views[i], w.nsamp, out=out, ws=wsd)
+            p.sps_search_device(out, w.nsamp, 8192, 6.0, 1 << 25, ws=wss, cands=cands, count=count)
+
+    t_single = _time_cuda(one_by_one, args.steps, args.warmup)
+    line = {"metric": "batched beams: DM-trial samples/s", "workload": "32 uneven beams",
+            "unit": "DM-trial samples/s", "steps": args.steps, "warmup": args.warmup,
+            "batched_value": dm_samples / (t_batch / 1e3),
+            "single_beam_sum_value": dm_samples / (t_single / 1e3),
+            "batched_ms": t_batch, "single_beams_ms": t_single, "speedup": t_single / t_batch,
+            "waves": nwaves, "batch_device_bytes": nbytes, "dm_trial_samples": dm_samples,
+            "candidates": total}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["ska", "ska-small", "adjoint"], default="ska")
+    ap.add_argument("--workload", choices=["ska", "ska-small", "adjoint", "batched"],
+                    default="ska")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -436,6 +488,8 @@ def main():
         bench_reference(args)
     elif args.workload == "adjoint":
         bench_adjoint(args)
+    elif args.workload == "batched":
+        bench_batched(args)
     else:
         bench_ours(args)
 

@@ -98,6 +98,8 @@ typedef struct aa_plan_desc {
 } aa_plan_desc;
 
 typedef struct aa_plan aa_plan;
+typedef struct aa_dd_result aa_dd_result;    /* library-owned dedispersed output */
+typedef struct aa_candidates aa_candidates;  /* library-owned host candidate list */
 
 /* Validate `desc`, build the FP64 delay tables and the strategy (tile shapes,
  * shared-memory sizes).  Host only: no device memory is touched.
@@ -176,7 +178,8 @@ aa_status aa_plan_shifts(const aa_plan* plan, int32_t r, int32_t* out, int64_t c
 /* Candidate record (16 bytes).  dm_index: global trial index (ranges
  * concatenated in plan order); t: sample index in that range's decimated
  * series (start of the boxcar window); width: boxcar width in samples of that
- * series; range: range index; snr: B(t). */
+ * series; range: range index; reserved: 0 (beam index in batched runs);
+ * snr: B(t). */
 typedef struct aa_candidate {
     uint32_t dm_index;
     uint32_t t;
@@ -224,6 +227,49 @@ aa_status aa_sps_search_device(const aa_plan* plan, int64_t nsamp, const float* 
  * bounded device-side wait gave up. */
 aa_status aa_workspace_status(void* d_ws, aa_stream_t stream);
 
+/* ------------------------------------------------------------ autotuner -- */
+
+/* Time the dedispersion kernel of every range of a bound plan over a
+ * synthetic probe input of nsamp_probe samples for each feasible tile shape
+ * (channels per shared-memory stage x staging depth) and keep the fastest
+ * in the plan's strategy.  Call before the plan's first dedispersion (the
+ * strategy is fixed from then on).  cache_path: optional text file; shapes
+ * found there (keyed by GPU model, SM count, channels, decimation and the
+ * staged row size) are applied without timing, new results are appended.
+ * The probe buffers are allocated and freed inside the call. */
+aa_status aa_plan_autotune(aa_plan* plan, int64_t nsamp_probe, const char* cache_path);
+
+/* ------------------------------------------------------ batched beams -- */
+
+/* Many independent beams (each with its own plan and length) searched by one
+ * CUDA graph: per stage (decimation, dedispersion, statistics, boxcar +
+ * peaks) one persistent kernel whose work queue spans every beam of a wave;
+ * beams are grouped into waves whose working set fits wave_budget_bytes
+ * (<= 0: half of the free device memory) and waves reuse one buffer region.
+ * Plans are bound to the current device if needed; they must stay alive
+ * while the batch exists.  The library allocates all device memory at
+ * creation (inputs included: see aa_batch_input).  nbeams <= 256. */
+typedef struct aa_batch aa_batch;
+aa_status aa_batch_create(aa_plan* const* plans, const int64_t* nsamps, int32_t nbeams,
+                          int32_t max_width, float threshold, int64_t cand_capacity,
+                          int64_t wave_budget_bytes, aa_batch** out);
+void aa_batch_destroy(aa_batch* batch);
+
+/* Library-owned device input of a beam: uint8 [nchans][pitch] (first nsamp
+ * bytes of each row are read).  The caller fills it before aa_batch_run. */
+aa_status aa_batch_input(aa_batch* batch, int32_t beam, uint8_t** d_in, int64_t* pitch);
+
+/* Number of waves and total device bytes held by the batch. */
+aa_status aa_batch_info(const aa_batch* batch, int32_t* nwaves, int64_t* device_bytes);
+
+/* Launch the captured graph on `stream` (asynchronous). */
+aa_status aa_batch_run(aa_batch* batch, aa_stream_t stream);
+
+/* Candidates of the last run, sorted by (beam, dm_index, t); the record's
+ * `reserved` byte holds the beam index.  Synchronises `stream`.  Returns
+ * AA_WARN_CAND_OVERFLOW if more than cand_capacity were found. */
+aa_status aa_batch_candidates(aa_batch* batch, aa_stream_t stream, aa_candidates** out);
+
 /* ------------------------------------------------- differentiable form -- */
 
 /* Float input with per-channel weights (every range must have dec == 1,
@@ -256,9 +302,6 @@ aa_status aa_dedisperse_f32_mse_device(const aa_plan* plan, const float* d_x, in
                                        size_t ws_bytes, aa_stream_t stream);
 
 /* ------------------------------------------ host-buffer (API-owned) path -- */
-
-typedef struct aa_dd_result aa_dd_result;
-typedef struct aa_candidates aa_candidates;
 
 /* Copy the caller's host filterbank (uint8 [nchans][host_pitch], first nsamp
  * bytes of each row valid; never written) to the device and dedisperse it.

@@ -99,6 +99,13 @@ _SIG = {
                                                         ctypes.c_size_t, _P]),
     "aa_dedisperse_f32_mse_device": (ctypes.c_int, [_P, _P, _I64, _I64, _P, _P, _P, _P, _P, _P,
                                                     ctypes.c_size_t, _P]),
+    "aa_plan_autotune": (ctypes.c_int, [_P, _I64, ctypes.c_char_p]),
+    "aa_batch_create": (ctypes.c_int, [_P, _P, _I32, _I32, _F32, _I64, _I64, ctypes.POINTER(_P)]),
+    "aa_batch_destroy": (None, [_P]),
+    "aa_batch_input": (ctypes.c_int, [_P, _I32, ctypes.POINTER(_P), ctypes.POINTER(_I64)]),
+    "aa_batch_info": (ctypes.c_int, [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I64)]),
+    "aa_batch_run": (ctypes.c_int, [_P, _P]),
+    "aa_batch_candidates": (ctypes.c_int, [_P, _P, ctypes.POINTER(_P)]),
     "aa_profile_enable": (ctypes.c_int, [_I32]),
     "aa_profile_read": (ctypes.c_int, [_I32, ctypes.POINTER(_I64), ctypes.POINTER(ctypes.c_double)]),
     "aa_profile_kernel_name": (ctypes.c_char_p, [_I32]),
@@ -294,3 +301,47 @@ def aa_dedisperse_f32_mse_device(plan, d_x, nsamp, x_pitch, d_w, d_tmpl, d_loss,
     check(lib().aa_dedisperse_f32_mse_device(plan, d_x, int(nsamp), int(x_pitch), d_w, d_tmpl,
                                              d_loss, d_gx, d_gw, d_ws, int(ws_bytes), stream),
           "aa_dedisperse_f32_mse_device")
+
+
+def aa_plan_autotune(plan, nsamp_probe: int, cache_path=None) -> None:
+    check(lib().aa_plan_autotune(plan, int(nsamp_probe),
+                                 None if cache_path is None else str(cache_path).encode()),
+          "aa_plan_autotune")
+
+
+def aa_batch_create(plans, nsamps, max_width, threshold, capacity, wave_budget=0) -> int:
+    n = len(plans)
+    parr = (ctypes.c_void_p * n)(*plans)
+    narr = (ctypes.c_int64 * n)(*[int(v) for v in nsamps])
+    h = ctypes.c_void_p()
+    check(lib().aa_batch_create(parr, narr, n, int(max_width), float(threshold), int(capacity),
+                                int(wave_budget), ctypes.byref(h)), "aa_batch_create")
+    return h.value
+
+
+def aa_batch_destroy(batch) -> None:
+    lib().aa_batch_destroy(batch)
+
+
+def aa_batch_input(batch, beam: int) -> tuple:
+    p, pitch = ctypes.c_void_p(), ctypes.c_int64()
+    check(lib().aa_batch_input(batch, int(beam), ctypes.byref(p), ctypes.byref(pitch)),
+          "aa_batch_input")
+    return p.value, pitch.value
+
+
+def aa_batch_info(batch) -> tuple:
+    nw, nb = ctypes.c_int32(), ctypes.c_int64()
+    check(lib().aa_batch_info(batch, ctypes.byref(nw), ctypes.byref(nb)), "aa_batch_info")
+    return nw.value, nb.value
+
+
+def aa_batch_run(batch, stream) -> None:
+    check(lib().aa_batch_run(batch, stream), "aa_batch_run")
+
+
+def aa_batch_candidates(batch, stream) -> tuple:
+    h = ctypes.c_void_p()
+    st = check(lib().aa_batch_candidates(batch, stream, ctypes.byref(h)), "aa_batch_candidates",
+               ok=(AA_OK, AA_WARN_CAND_OVERFLOW))
+    return h.value, st

@@ -89,6 +89,12 @@ class Plan:
     def shifts(self, r: int) -> np.ndarray:
         return abi.aa_plan_shifts(self.handle, r, self.ranges[r][2], self.nchans)
 
+    def autotune(self, nsamp_probe: int, cache_path=None):
+        """Pick the dedispersion tile shapes of every range by timing them on
+        the bound device (see aa_plan_autotune)."""
+        self.bind()
+        abi.aa_plan_autotune(self.handle, nsamp_probe, cache_path)
+
     def bind(self, device=None):
         dev = torch.cuda.current_device() if device is None else int(device)
         abi.aa_plan_bind(self.handle, dev)
@@ -252,3 +258,60 @@ def candidates_from_device(cands: torch.Tensor, count: torch.Tensor, capacity: i
     arr = raw.view(abi.CANDIDATE_DTYPE).copy()
     order = np.lexsort((arr["t"], arr["dm_index"]))
     return arr[order]
+
+
+def _candidates_array(h) -> tuple:
+    try:
+        ptr, stored, total = abi.aa_candidates_view(h)
+        arr = np.zeros(stored, dtype=abi.CANDIDATE_DTYPE)
+        if stored:
+            ctypes.memmove(arr.ctypes.data, ptr, stored * abi.CANDIDATE_DTYPE.itemsize)
+    finally:
+        abi.aa_candidates_destroy(h)
+    return arr, total
+
+
+class Batch:
+    """Several beams searched by one CUDA graph of persistent work-queue
+    kernels (see aa_batch_create).  The plans must outlive the batch."""
+
+    def __init__(self, plans, nsamps, max_width, threshold, capacity=1 << 24, wave_budget=0):
+        for p in plans:
+            p.bind()
+        self.plans = list(plans)
+        self.nsamps = [int(n) for n in nsamps]
+        self.handle = abi.aa_batch_create([p.handle for p in plans], self.nsamps, max_width,
+                                          threshold, capacity, wave_budget)
+
+    def input_view(self, beam: int) -> torch.Tensor:
+        """The library-owned device input of a beam as a uint8 tensor
+        [nchans][pitch] (zero-copy)."""
+        ptr, pitch = abi.aa_batch_input(self.handle, beam)
+        C = self.plans[beam].nchans
+
+        class _U8:
+            __cuda_array_interface__ = {"shape": (C, pitch), "typestr": "|u1",
+                                        "data": (ptr, False), "version": 3, "strides": None}
+        return torch.as_tensor(_U8(), device="cuda")
+
+    def info(self) -> tuple:
+        return abi.aa_batch_info(self.handle)
+
+    def run(self, stream=None):
+        abi.aa_batch_run(self.handle, _stream_handle(stream))
+
+    def candidates(self, stream=None):
+        """Sorted records (beam in the `reserved` field) and the total found."""
+        h, st = abi.aa_batch_candidates(self.handle, _stream_handle(stream))
+        return _candidates_array(h)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            abi.aa_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

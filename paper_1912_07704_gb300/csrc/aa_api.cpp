@@ -11,7 +11,6 @@
 namespace aa {
 extern int g_fault_skip_chunk;
 extern uint64_t g_wait_limit_ns;
-cudaError_t launch_rsqrt_table(double* t, int wpad, cudaStream_t s);
 }  // namespace aa
 
 using namespace aa;
@@ -29,6 +28,12 @@ struct aa_candidates {
     std::vector<aa_candidate> list;
     int64_t total = 0;
 };
+
+namespace aa {
+aa_candidates* candidates_new() { return new (std::nothrow) aa_candidates(); }
+std::vector<aa_candidate>& candidates_list(aa_candidates* c) { return c->list; }
+void candidates_set_total(aa_candidates* c, int64_t total) { c->total = total; }
+}  // namespace aa
 
 namespace {
 

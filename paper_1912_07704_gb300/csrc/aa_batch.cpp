@@ -1,0 +1,463 @@
+// Batched multi-beam search: many independent beams (each its own bound
+// plan and length) processed by persistent work-queue kernels, one per stage
+// (decimation, dedispersion, statistics, boxcar + peaks), whose queues span
+// every beam of a wave, all captured in one CUDA graph.  Beams are grouped
+// into waves whose working set (decimated inputs, dedispersed series, search
+// workspace) fits a memory budget; waves reuse one buffer region.
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "aa_internal.h"
+
+using namespace aa;
+
+namespace {
+
+aa_status fail(cudaError_t e, const char* what) {
+    set_error("%s: %s", what, cudaGetErrorString(e));
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? AA_ERR_NOMEM : AA_ERR_CUDA;
+}
+
+#define AA_CUDA(call, what)                              \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) return fail(e_, (what));  \
+    } while (0)
+
+struct WaveTables {
+    // host copies (uploaded into the arena)
+    std::vector<DecimateJob> dec_jobs[4];  // one launch per cascade level
+    std::vector<int64_t> dec_first[4];
+    std::vector<DedispArgs> dd;
+    std::vector<int64_t> dd_first;
+    std::vector<int> dd_ndmb;
+    std::vector<SpsArgs> sps;
+    std::vector<int64_t> st_first, bx_first;
+    std::vector<int> bx_ntiles;
+    // device copies
+    DecimateJob* d_dec_jobs[4] = {};
+    int64_t* d_dec_first[4] = {};
+    DedispArgs* d_dd = nullptr;
+    int64_t* d_dd_first = nullptr;
+    int* d_dd_ndmb = nullptr;
+    SpsArgs* d_sps = nullptr;
+    int64_t* d_st_first = nullptr;
+    int64_t* d_bx_first = nullptr;
+    int* d_bx_ntiles = nullptr;
+    unsigned long long* d_queues = nullptr;  // 3 counters
+    size_t dd_smem = 0;
+};
+
+}  // namespace
+
+struct aa_batch {
+    int device = -1;
+    int32_t nbeams = 0;
+    std::vector<aa_plan*> plans;
+    std::vector<int64_t> nsamps, in_pitch, in_offset;
+    int32_t max_width = 0;
+    float threshold = 0;
+    int64_t capacity = 0;
+    int64_t chunk_cap = 0;
+    int32_t wpad = 0;
+    char* arena = nullptr;
+    size_t arena_bytes = 0;
+    std::vector<std::vector<int>> waves;
+    std::vector<WaveTables> tables;
+    aa_candidate* d_cands = nullptr;
+    unsigned long long* d_counts = nullptr;  // [0] candidates, [1] chunks
+    CandChunk* d_chunks = nullptr;
+    unsigned* d_err = nullptr;
+    double* d_rsw = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int grid_dd = 0, grid_st = 0, grid_bx = 0, grid_dec = 0;
+};
+
+namespace {
+
+struct BeamNeeds {
+    int64_t dec_bytes = 0, dd_bytes = 0, sps_bytes = 0;
+    int64_t total() const { return dec_bytes + dd_bytes + sps_bytes; }
+};
+
+BeamNeeds beam_needs(const aa_plan& p, int64_t nsamp, int32_t W) {
+    const Layout L = make_layout(p, nsamp, W);
+    BeamNeeds n;
+    n.dec_bytes = round_up(L.dedisp_ws, 256);
+    n.dd_bytes = round_up(L.dd_elems * 4, 256);
+    n.sps_bytes = round_up((int64_t)p.ndm_total * (int64_t)sizeof(RowStats), 256) +
+                  round_up((int64_t)p.ndm_total * L.wpad * 8, 256);
+    return n;
+}
+
+void free_batch(aa_batch* b) {
+    if (!b) return;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->arena) cudaFree(b->arena);
+    delete b;
+}
+
+}  // namespace
+
+extern "C" {
+
+aa_status aa_batch_create(aa_plan* const* plans, const int64_t* nsamps, int32_t nbeams,
+                          int32_t max_width, float threshold, int64_t cand_capacity,
+                          int64_t wave_budget_bytes, aa_batch** out) {
+    clear_error();
+    if (!out) { set_error("out is NULL"); return AA_ERR_ARG; }
+    *out = nullptr;
+    if (!plans || !nsamps || nbeams < 1 || nbeams > 256) { set_error("need 1..256 beams"); return AA_ERR_ARG; }
+    if (max_width < 1 || max_width > 65535) { set_error("max_width must be in [1, 65535]"); return AA_ERR_ARG; }
+    if (cand_capacity < 1) { set_error("cand_capacity must be >= 1"); return AA_ERR_ARG; }
+    int dev = -1;
+    AA_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+    for (int i = 0; i < nbeams; ++i) {
+        if (!plans[i]) { set_error("plan %d is NULL", i); return AA_ERR_ARG; }
+        if (nsamps[i] < 0) { set_error("nsamp of beam %d is negative", i); return AA_ERR_ARG; }
+        if (!plans[i]->ready) {
+            aa_status st = aa_plan_bind(plans[i], dev);
+            if (st != AA_OK) return st;
+        }
+        if (plans[i]->device != dev) { set_error("plan %d is bound to another device", i); return AA_ERR_STATE; }
+    }
+    aa_batch* b = new (std::nothrow) aa_batch();
+    if (!b) return AA_ERR_NOMEM;
+    b->device = dev;
+    b->nbeams = nbeams;
+    b->plans.assign(plans, plans + nbeams);
+    b->nsamps.assign(nsamps, nsamps + nbeams);
+    b->max_width = max_width;
+    b->threshold = threshold;
+    b->capacity = cand_capacity;
+    b->wpad = (int32_t)round_up(max_width, kSpsSlots);
+
+    // waves by memory
+    if (wave_budget_bytes <= 0) {
+        size_t fr = 0, tot = 0;
+        cudaMemGetInfo(&fr, &tot);
+        wave_budget_bytes = (int64_t)(fr / 2);
+    }
+    std::vector<BeamNeeds> needs(nbeams);
+    int64_t in_bytes = 0, chunk_cap = 0;
+    for (int i = 0; i < nbeams; ++i) {
+        needs[i] = beam_needs(*plans[i], nsamps[i], max_width);
+        const Layout L = make_layout(*plans[i], nsamps[i], max_width);
+        b->in_pitch.push_back(L.in_pitch_min);
+        b->in_offset.push_back(in_bytes);
+        in_bytes += round_up((int64_t)plans[i]->nchans * L.in_pitch_min, 256);
+        chunk_cap += L.chunk_cap;
+    }
+    b->chunk_cap = std::max<int64_t>(chunk_cap, 1);
+    int64_t wave_bytes = 0, cur = 0;
+    std::vector<int> w;
+    for (int i = 0; i < nbeams; ++i) {
+        if (!w.empty() && cur + needs[i].total() > wave_budget_bytes) {
+            b->waves.push_back(w);
+            wave_bytes = std::max(wave_bytes, cur);
+            w.clear();
+            cur = 0;
+        }
+        w.push_back(i);
+        cur += needs[i].total();
+    }
+    b->waves.push_back(w);
+    wave_bytes = std::max(wave_bytes, cur);
+
+    // descriptor tables: 16 arrays per wave, each padded to 256 bytes
+    constexpr int64_t kArraysPerWave = 16;
+    size_t table_bytes = 0;
+    for (auto& wv : b->waves) {
+        int64_t nr = 0;
+        for (int i : wv) nr += (int64_t)plans[i]->ranges.size();
+        table_bytes += (size_t)(kArraysPerWave * 256 +
+                                round_up(nr * (int64_t)sizeof(DedispArgs), 256) +
+                                round_up(nr * (int64_t)sizeof(SpsArgs), 256) +
+                                3 * round_up((nr + 1) * 8, 256) + 2 * round_up(nr * 4, 256) +
+                                4 * round_up(nr * (int64_t)sizeof(DecimateJob), 256) +
+                                4 * round_up((nr + 1) * 8, 256));
+    }
+    const int64_t cand_bytes = round_up(cand_capacity * (int64_t)sizeof(aa_candidate), 256);
+    const int64_t chunk_bytes = round_up(b->chunk_cap * (int64_t)sizeof(CandChunk), 256);
+    const int64_t small_bytes = 256 + 256 + round_up((int64_t)b->wpad * 8, 256);
+    b->arena_bytes = (size_t)(in_bytes + wave_bytes + table_bytes + cand_bytes + chunk_bytes + small_bytes);
+    cudaError_t e = cudaMalloc(&b->arena, b->arena_bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error("batch needs %zu device bytes: %s", b->arena_bytes, cudaGetErrorString(e));
+        free_batch(b);
+        return AA_ERR_NOMEM;
+    }
+    char* p = b->arena;
+    p += in_bytes;  // beam inputs first (aa_batch_input)
+    char* wave_area = p;
+    p += wave_bytes;
+    b->d_cands = reinterpret_cast<aa_candidate*>(p);
+    p += cand_bytes;
+    b->d_chunks = reinterpret_cast<CandChunk*>(p);
+    p += chunk_bytes;
+    b->d_counts = reinterpret_cast<unsigned long long*>(p);
+    p += 256;
+    b->d_err = reinterpret_cast<unsigned*>(p);
+    p += 256;
+    b->d_rsw = reinterpret_cast<double*>(p);
+    p += round_up((int64_t)b->wpad * 8, 256);
+    char* tables = p;
+
+    // per-wave descriptors
+    b->tables.resize(b->waves.size());
+    size_t dd_smem_max = 0;
+    for (size_t wi = 0; wi < b->waves.size(); ++wi) {
+        WaveTables& T = b->tables[wi];
+        char* q = wave_area;
+        T.dd_first.push_back(0);
+        T.st_first.push_back(0);
+        T.bx_first.push_back(0);
+        for (int lv = 0; lv < 4; ++lv) T.dec_first[lv].push_back(0);
+        for (int bi : b->waves[wi]) {
+            const aa_plan& pl = *plans[bi];
+            const int64_t n = nsamps[bi];
+            const Layout L = make_layout(pl, n, max_width);
+            const uint8_t* d_in = reinterpret_cast<const uint8_t*>(b->arena + b->in_offset[bi]);
+            char* dec_ws = q;
+            q += needs[bi].dec_bytes;
+            float* dd = reinterpret_cast<float*>(q);
+            q += needs[bi].dd_bytes;
+            RowStats* stats = reinterpret_cast<RowStats*>(q);
+            q += round_up((int64_t)pl.ndm_total * (int64_t)sizeof(RowStats), 256);
+            float2* tab = reinterpret_cast<float2*>(q);
+            q += round_up((int64_t)pl.ndm_total * L.wpad * 8, 256);
+            // decimation cascade (level = position of the source in the chain)
+            std::vector<int> level(pl.decs.size(), 0);
+            for (size_t k = 0; k < pl.decs.size(); ++k) {
+                const int dec = pl.decs[k];
+                const void* src = d_in;
+                int src_elem = 1, src_dec = 1;
+                int64_t src_pitch = b->in_pitch[bi];
+                for (size_t j = 0; j < k; ++j)
+                    if (dec % pl.decs[j] == 0) {
+                        src = dec_ws + L.dec_offset[j];
+                        src_elem = 2;
+                        src_dec = pl.decs[j];
+                        src_pitch = L.dec_pitch[j];
+                        level[k] = level[j] + 1;
+                    }
+                if (level[k] > 3) {
+                    set_error("decimation cascade deeper than 4 levels");
+                    free_batch(b);
+                    return AA_ERR_CONFIG;
+                }
+                DecimateJob job{src, src_elem, dec / src_dec, src_pitch, n / dec,
+                                reinterpret_cast<uint16_t*>(dec_ws + L.dec_offset[k]), L.dec_pitch[k]};
+                if (job.nout > 0) {
+                    T.dec_jobs[level[k]].push_back(job);
+                    T.dec_first[level[k]].push_back(T.dec_first[level[k]].back() +
+                                                    (job.nout + 3) / 4 * pl.nchans);
+                }
+            }
+            for (size_t r = 0; r < pl.ranges.size(); ++r) {
+                const RangePlan& g = pl.ranges[r];
+                if (L.length[r] <= 0) continue;
+                DedispArgs a{};
+                if (g.desc.dec == 1) {
+                    a.in = d_in;
+                    a.in_pitch = b->in_pitch[bi];
+                } else {
+                    const size_t k = std::find(pl.decs.begin(), pl.decs.end(), g.desc.dec) - pl.decs.begin();
+                    a.in = dec_ws + L.dec_offset[k];
+                    a.in_pitch = L.dec_pitch[k];
+                }
+                a.nchans = pl.nchans;
+                a.nsamp = L.nsamp_dec[r];
+                a.length = L.length[r];
+                a.ndm = g.desc.ndm;
+                a.shifts = g.d_shifts;
+                a.out = dd + L.row_offset[r];
+                a.out_pitch = L.pitch[r];
+                a.rw = g.rw;
+                a.cc = g.cc;
+                a.nstage = g.nstage;
+                a.flush = g.flush;
+                a.elem = g.elem;
+                a.smem = g.smem;
+                a.err = b->d_err;
+                dd_smem_max = std::max(dd_smem_max, g.smem);
+                const int ndmb = (a.ndm + kDmPerBlock - 1) / kDmPerBlock;
+                const int64_t ntiles = (a.length + kTau - 1) / kTau;
+                T.dd.push_back(a);
+                T.dd_ndmb.push_back(ndmb);
+                T.dd_first.push_back(T.dd_first.back() + (int64_t)ndmb * ntiles);
+                SpsArgs s{};
+                s.dd = dd + L.row_offset[r];
+                s.pitch = L.pitch[r];
+                s.length = L.length[r];
+                s.nrows = g.desc.ndm;
+                s.dm_offset = g.dm_offset;
+                s.range = (int32_t)r;
+                s.max_width = max_width;
+                s.wpad = L.wpad;
+                s.threshold = threshold;
+                s.rsqrt_w = b->d_rsw;
+                s.stats = stats + g.dm_offset;
+                s.table = tab + (int64_t)g.dm_offset * L.wpad;
+                s.cands = b->d_cands;
+                s.capacity = cand_capacity;
+                s.count = &b->d_counts[0];
+                s.snr_out = nullptr;
+                s.err = b->d_err;
+                s.prune = 1;
+                s.beam = bi;
+                s.chunks = b->d_chunks;
+                s.nchunks = &b->d_counts[1];
+                s.chunk_cap = b->chunk_cap;
+                T.sps.push_back(s);
+                T.st_first.push_back(T.st_first.back() + s.nrows);
+                const int nt = sps_boxcar_tiles(s.length);
+                T.bx_ntiles.push_back(nt);
+                T.bx_first.push_back(T.bx_first.back() + (int64_t)nt * s.nrows);
+            }
+        }
+        T.dd_smem = dd_smem_max;
+        // upload tables
+        bool overflow = false;
+        auto put = [&](const void* src, size_t bytes) {
+            char* dst = tables;
+            tables += round_up((int64_t)std::max<size_t>(bytes, 8), 256);
+            if (tables > b->arena + b->arena_bytes) {
+                overflow = true;  // never copy outside the arena
+                return b->arena;
+            }
+            if (bytes) cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice);
+            return dst;
+        };
+        for (int lv = 0; lv < 4; ++lv) {
+            T.d_dec_jobs[lv] = reinterpret_cast<DecimateJob*>(put(T.dec_jobs[lv].data(), T.dec_jobs[lv].size() * sizeof(DecimateJob)));
+            T.d_dec_first[lv] = reinterpret_cast<int64_t*>(put(T.dec_first[lv].data(), T.dec_first[lv].size() * 8));
+        }
+        T.d_dd = reinterpret_cast<DedispArgs*>(put(T.dd.data(), T.dd.size() * sizeof(DedispArgs)));
+        T.d_dd_first = reinterpret_cast<int64_t*>(put(T.dd_first.data(), T.dd_first.size() * 8));
+        T.d_dd_ndmb = reinterpret_cast<int*>(put(T.dd_ndmb.data(), T.dd_ndmb.size() * 4));
+        T.d_sps = reinterpret_cast<SpsArgs*>(put(T.sps.data(), T.sps.size() * sizeof(SpsArgs)));
+        T.d_st_first = reinterpret_cast<int64_t*>(put(T.st_first.data(), T.st_first.size() * 8));
+        T.d_bx_first = reinterpret_cast<int64_t*>(put(T.bx_first.data(), T.bx_first.size() * 8));
+        T.d_bx_ntiles = reinterpret_cast<int*>(put(T.bx_ntiles.data(), T.bx_ntiles.size() * 4));
+        T.d_queues = reinterpret_cast<unsigned long long*>(put(nullptr, 0));
+        if (overflow) {
+            set_error("internal: descriptor tables overflow the arena");
+            free_batch(b);
+            return AA_ERR_STATE;
+        }
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) { free_batch(b); return fail(e, "upload batch tables"); }
+    cudaDeviceProp prop{};
+    cudaGetDeviceProperties(&prop, dev);
+    const int sms = prop.multiProcessorCount;
+    b->grid_dd = sms;  // one 512-thread CTA per SM (the staging ring uses ~120 KB)
+    b->grid_st = sms * 4;
+    b->grid_bx = sms * 2;
+    b->grid_dec = sms * 16;
+
+    // capture the whole batch into one graph
+    cudaStream_t cs;
+    e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e != cudaSuccess) { free_batch(b); return fail(e, "create capture stream"); }
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaMemsetAsync(b->d_counts, 0, 16, cs);
+        cudaMemsetAsync(b->d_err, 0, 4, cs);
+        launch_rsqrt_table(b->d_rsw, b->wpad, cs);
+        for (auto& T : b->tables) {
+            cudaMemsetAsync(T.d_queues, 0, 3 * sizeof(unsigned long long), cs);
+            for (int lv = 0; lv < 4; ++lv)
+                launch_decimate_batch(T.d_dec_jobs[lv], T.d_dec_first[lv], (int)T.dec_jobs[lv].size(),
+                                      b->grid_dec, cs);
+            launch_dedisperse_batch(T.d_dd, T.d_dd_first, T.d_dd_ndmb, (int)T.dd.size(), T.dd_smem,
+                                    &T.d_queues[0], b->grid_dd, cs);
+            launch_sps_stats_batch(T.d_sps, T.d_st_first, (int)T.sps.size(), &T.d_queues[1],
+                                   b->grid_st, cs);
+            launch_sps_boxcar_batch(T.d_sps, T.d_bx_first, T.d_bx_ntiles, (int)T.sps.size(), b->wpad,
+                                    &T.d_queues[2], b->grid_bx, cs);
+        }
+        e = cudaStreamEndCapture(cs, &b->graph);
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) { free_batch(b); return fail(e, "capture batch graph"); }
+    *out = b;
+    return AA_OK;
+}
+
+void aa_batch_destroy(aa_batch* b) {
+    if (!b) return;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    cudaSetDevice(b->device);
+    free_batch(b);
+    if (prev >= 0) cudaSetDevice(prev);
+}
+
+aa_status aa_batch_input(aa_batch* b, int32_t beam, uint8_t** d_in, int64_t* pitch) {
+    clear_error();
+    if (!b || beam < 0 || beam >= b->nbeams) { set_error("bad batch/beam"); return AA_ERR_ARG; }
+    if (d_in) *d_in = reinterpret_cast<uint8_t*>(b->arena + b->in_offset[beam]);
+    if (pitch) *pitch = b->in_pitch[beam];
+    return AA_OK;
+}
+
+aa_status aa_batch_info(const aa_batch* b, int32_t* nwaves, int64_t* device_bytes) {
+    clear_error();
+    if (!b) { set_error("batch is NULL"); return AA_ERR_ARG; }
+    if (nwaves) *nwaves = (int32_t)b->waves.size();
+    if (device_bytes) *device_bytes = (int64_t)b->arena_bytes;
+    return AA_OK;
+}
+
+aa_status aa_batch_run(aa_batch* b, aa_stream_t stream) {
+    clear_error();
+    if (!b) { set_error("batch is NULL"); return AA_ERR_ARG; }
+    AA_CUDA(cudaGraphLaunch(b->exec, reinterpret_cast<cudaStream_t>(stream)), "batch graph launch");
+    return AA_OK;
+}
+
+aa_status aa_batch_candidates(aa_batch* b, aa_stream_t stream, aa_candidates** out) {
+    clear_error();
+    if (!out) { set_error("out is NULL"); return AA_ERR_ARG; }
+    *out = nullptr;
+    if (!b) { set_error("batch is NULL"); return AA_ERR_ARG; }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    unsigned long long counts[2] = {0, 0};
+    unsigned err = 0;
+    AA_CUDA(cudaMemcpyAsync(counts, b->d_counts, 16, cudaMemcpyDeviceToHost, s), "read counts");
+    AA_CUDA(cudaMemcpyAsync(&err, b->d_err, 4, cudaMemcpyDeviceToHost, s), "read error word");
+    AA_CUDA(cudaStreamSynchronize(s), "synchronize");
+    if (err) { set_error("a bounded device-side wait gave up"); return AA_ERR_TIMEOUT; }
+    const int64_t stored = std::min<int64_t>((int64_t)counts[0], b->capacity);
+    const int64_t nh = std::min<int64_t>((int64_t)counts[1], b->chunk_cap);
+    std::vector<aa_candidate> raw((size_t)stored);
+    std::vector<CandChunk> heads((size_t)nh);
+    if (stored) AA_CUDA(cudaMemcpyAsync(raw.data(), b->d_cands, stored * sizeof(aa_candidate), cudaMemcpyDeviceToHost, s), "read candidates");
+    if (nh) AA_CUDA(cudaMemcpyAsync(heads.data(), b->d_chunks, nh * sizeof(CandChunk), cudaMemcpyDeviceToHost, s), "read chunks");
+    AA_CUDA(cudaStreamSynchronize(s), "synchronize");
+    std::sort(heads.begin(), heads.end(), [](const CandChunk& x, const CandChunk& y) {
+        if (x.reserved != y.reserved) return x.reserved < y.reserved;  // beam
+        return x.dm_index != y.dm_index ? x.dm_index < y.dm_index : x.t0 < y.t0;
+    });
+    aa_candidates* res = candidates_new();
+    if (!res) { set_error("host allocation failed"); return AA_ERR_NOMEM; }
+    std::vector<aa_candidate>& list = candidates_list(res);
+    list.reserve((size_t)stored);
+    for (const CandChunk& h : heads)
+        for (unsigned long long k = h.base; k < h.base + h.n && (int64_t)k < stored; ++k)
+            list.push_back(raw[(size_t)k]);
+    candidates_set_total(res, (int64_t)counts[0]);
+    *out = res;
+    return (int64_t)counts[0] > b->capacity ? AA_WARN_CAND_OVERFLOW : AA_OK;
+}
+
+}  // extern "C"

@@ -85,17 +85,23 @@ __device__ __forceinline__ uint32_t mad_add(uint32_t x, uint32_t one, uint32_t a
     return d;
 }
 
+__device__ __forceinline__ void mbar_inval(uint64_t* bar) {
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+// One CTA's work item: DM block (bid % ndm_blocks) x time tile (bid / ndm_blocks).
+// `smem` is the dynamic shared memory (layout below); the caller guarantees
+// that every thread of the CTA has finished any previous item.
 template <int SPW>
-__global__ void __launch_bounds__(kDedispThreads, 2)
-    dedisperse_kernel(DedispArgs a, int ndm_blocks, uint64_t wait_limit_ns, int fault_skip_chunk,
-                      uint32_t one) {
+__device__ __forceinline__ void dedisperse_block(const DedispArgs& a, int ndm_blocks, int64_t bid,
+                                                 uint64_t wait_limit_ns, int fault_skip_chunk,
+                                                 uint32_t one, unsigned char* smem, bool reinit) {
     constexpr int QW = kTau / (32 * SPW);  // words per lane per DM trial
     constexpr int NCOPY = SPW;             // shifted copies of each staged row
     constexpr int EB = 4 / SPW;            // bytes per sample
     constexpr int A16 = 16 / EB;           // samples per 16-byte unit
     constexpr int SWAR = SPW / 2;          // packed accumulators per word
 
-    extern __shared__ __align__(128) unsigned char smem[];
     const int cc = a.cc, nstage = a.nstage, rw = a.rw;
     const size_t stage_w = (size_t)cc * NCOPY * rw;
     uint32_t* stages = reinterpret_cast<uint32_t*>(smem);
@@ -105,8 +111,8 @@ __global__ void __launch_bounds__(kDedispThreads, 2)
         (reinterpret_cast<uintptr_t>(bases + nstage * cc) + 15) & ~uintptr_t(15));
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int dmb = blockIdx.x % ndm_blocks;
-    const int64_t tile = blockIdx.x / ndm_blocks;
+    const int dmb = (int)(bid % ndm_blocks);
+    const int64_t tile = bid / ndm_blocks;
     const int d0 = dmb * kDmPerBlock;
     const int dlast = min(a.ndm, d0 + kDmPerBlock) - 1;
     const int64_t t0 = tile * kTau;
@@ -116,7 +122,10 @@ __global__ void __launch_bounds__(kDedispThreads, 2)
     const int64_t pitch_b = a.in_pitch * EB;
 
     if (tid == 0) {
-        for (int s = 0; s < nstage; ++s) mbar_init(&bars[s], 1);
+        for (int s = 0; s < nstage; ++s) {
+            if (reinit) mbar_inval(&bars[s]);
+            mbar_init(&bars[s], 1);
+        }
         mbar_fence_init();
     }
     __syncthreads();
@@ -335,6 +344,51 @@ __global__ void __launch_bounds__(kDedispThreads, 2)
     }
 }
 
+template <int SPW>
+__global__ void __launch_bounds__(kDedispThreads, 2)
+    dedisperse_kernel(DedispArgs a, int ndm_blocks, uint64_t wait_limit_ns, int fault_skip_chunk,
+                      uint32_t one) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    dedisperse_block<SPW>(a, ndm_blocks, blockIdx.x, wait_limit_ns, fault_skip_chunk, one, smem,
+                          false);
+}
+
+// Persistent form over several beams/ranges: CTAs pull work items from a
+// queue; item i belongs to descriptor k with first[k] <= i < first[k+1].
+__device__ __forceinline__ int find_desc(const int64_t* first, int n, int64_t item) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (first[mid] <= item) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(kDedispThreads, 1)
+    dedisperse_batch_kernel(const DedispArgs* __restrict__ descs, const int64_t* __restrict__ first,
+                            const int* __restrict__ ndm_blocks, int ndesc,
+                            unsigned long long* queue, uint64_t wait_limit_ns, uint32_t one) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ long long s_item;
+    const int64_t total = first[ndesc];
+    bool reinit = false;
+    for (;;) {
+        __syncthreads();  // previous item finished by every thread
+        if (threadIdx.x == 0) s_item = (long long)atomicAdd(queue, 1ull);
+        __syncthreads();
+        const int64_t item = s_item;
+        if (item >= total) break;
+        const int k = find_desc(first, ndesc, item);
+        const DedispArgs& a = descs[k];
+        if (a.elem == 1)
+            dedisperse_block<4>(a, ndm_blocks[k], item - first[k], wait_limit_ns, -1, one, smem, reinit);
+        else
+            dedisperse_block<2>(a, ndm_blocks[k], item - first[k], wait_limit_ns, -1, one, smem, reinit);
+        reinit = true;
+    }
+}
+
 // x_out[c][j] = sum_{k<factor} x_in[c][j*factor + k], j < nout.  One thread
 // per 4 outputs; grid-stride over (channel, quad).
 template <typename Tin>
@@ -361,10 +415,60 @@ __global__ void __launch_bounds__(256) decimate_kernel(const Tin* __restrict__ i
     }
 }
 
+// Several decimation jobs in one grid-stride launch (jobs of one cascade
+// level only: no job reads another's output).
+__global__ void __launch_bounds__(256) decimate_batch_kernel(const DecimateJob* __restrict__ jobs,
+                                                             const int64_t* __restrict__ first,
+                                                             int njobs) {
+    const int64_t total = first[njobs];
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int k = find_desc(first, njobs, q);
+        const DecimateJob& j = jobs[k];
+        const int64_t quads = (j.nout + 3) / 4;
+        const int64_t local = q - first[k];
+        const int64_t c = local / quads;
+        const int64_t j0 = (local - c * quads) * 4;
+        uint16_t* dst = j.out + c * j.out_pitch + j0;
+        for (int u = 0; u < 4; ++u) {
+            if (j0 + u >= j.nout) break;
+            uint32_t sum = 0;
+            if (j.in_elem == 1) {
+                const uint8_t* src = static_cast<const uint8_t*>(j.in) + c * j.in_pitch + (j0 + u) * j.factor;
+                for (int k2 = 0; k2 < j.factor; ++k2) sum += src[k2];
+            } else {
+                const uint16_t* src = static_cast<const uint16_t*>(j.in) + c * j.in_pitch + (j0 + u) * j.factor;
+                for (int k2 = 0; k2 < j.factor; ++k2) sum += src[k2];
+            }
+            dst[u] = (uint16_t)sum;
+        }
+    }
+}
+
 }  // namespace
 
 int g_fault_skip_chunk = -1;          // test hook: never issue this chunk
 uint64_t g_wait_limit_ns = kWaitLimitNs;
+
+cudaError_t launch_dedisperse_batch(const DedispArgs* d_descs, const int64_t* d_first,
+                                    const int* d_ndm_blocks, int ndesc, size_t smem,
+                                    unsigned long long* d_queue, int grid, cudaStream_t s) {
+    if (ndesc <= 0) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(dedisperse_batch_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dedisperse_batch_kernel<<<grid, kDedispThreads, smem, s>>>(d_descs, d_first, d_ndm_blocks, ndesc,
+                                                               d_queue, g_wait_limit_ns, 1u);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_decimate_batch(const DecimateJob* d_jobs, const int64_t* d_first, int njobs,
+                                  int grid, cudaStream_t s) {
+    if (njobs <= 0) return cudaSuccess;
+    decimate_batch_kernel<<<grid, 256, 0, s>>>(d_jobs, d_first, njobs);
+    return cudaGetLastError();
+}
+
 
 cudaError_t launch_dedisperse(const DedispArgs& a, cudaStream_t s) {
     if (a.length <= 0 || a.ndm <= 0) return cudaSuccess;

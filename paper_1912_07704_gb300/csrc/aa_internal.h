@@ -160,6 +160,24 @@ cudaError_t launch_decimate(const void* in, int in_elem, int64_t in_pitch, int32
                             int64_t nout, int factor, uint16_t* out, int64_t out_pitch,
                             cudaStream_t s);
 
+// ----------------------------------------------------- batched (persistent) --
+struct DecimateJob {
+    const void* in;
+    int32_t in_elem;
+    int32_t factor;
+    int64_t in_pitch;  // elements
+    int64_t nout;      // output samples per channel
+    uint16_t* out;
+    int64_t out_pitch;  // elements
+};
+// Work-queue kernels over several descriptors; first[] is the item prefix
+// (ndesc + 1 entries, device), queue a device counter cleared beforehand.
+cudaError_t launch_dedisperse_batch(const DedispArgs* d_descs, const int64_t* d_first,
+                                    const int* d_ndm_blocks, int ndesc, size_t smem,
+                                    unsigned long long* d_queue, int grid, cudaStream_t s);
+cudaError_t launch_decimate_batch(const DecimateJob* d_jobs, const int64_t* d_first, int njobs,
+                                  int grid, cudaStream_t s);
+
 struct SpsArgs {
     const float* dd;        // row 0 of this range
     int64_t pitch;          // floats between rows
@@ -179,12 +197,21 @@ struct SpsArgs {
     float* snr_out;         // optional, row 0 of this range (same pitch)
     unsigned* err;
     int32_t prune;          // skip width blocks bounded below the threshold
+    int32_t beam;           // beam id stored in candidate records (batched mode)
     CandChunk* chunks;      // chunk headers (all ranges)
     unsigned long long* nchunks;
     int64_t chunk_cap;
 };
 cudaError_t launch_sps_stats(const SpsArgs& a, cudaStream_t s);
 cudaError_t launch_sps_boxcar(const SpsArgs& a, cudaStream_t s);
+cudaError_t launch_sps_stats_batch(const SpsArgs* d_descs, const int64_t* d_first, int ndesc,
+                                   unsigned long long* d_queue, int grid, cudaStream_t s);
+cudaError_t launch_sps_boxcar_batch(const SpsArgs* d_descs, const int64_t* d_first,
+                                    const int* d_ntiles, int ndesc, int wpad,
+                                    unsigned long long* d_queue, int grid, cudaStream_t s);
+int sps_boxcar_tiles(int64_t length);
+size_t sps_boxcar_smem(int wpad);
+cudaError_t launch_rsqrt_table(double* t, int wpad, cudaStream_t s);
 
 // ---------------------------------------------------- differentiable form --
 struct F32FwdArgs {
@@ -228,5 +255,10 @@ int f32_adj_tiles(int64_t nsamp);
 cudaError_t launch_f32_forward(int mode, const F32FwdArgs& p, cudaStream_t s);
 cudaError_t launch_f32_adjoint(const F32AdjArgs& p, cudaStream_t s);
 cudaError_t launch_finish_loss(const double* sum, double n, double* loss, cudaStream_t s);
+
+// candidate-list objects shared by the single-beam and batched paths
+aa_candidates* candidates_new();
+std::vector<aa_candidate>& candidates_list(aa_candidates* c);
+void candidates_set_total(aa_candidates* c, int64_t total);
 
 }  // namespace aa

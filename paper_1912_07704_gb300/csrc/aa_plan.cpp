@@ -48,6 +48,8 @@ static size_t dedisp_smem(const RangePlan& r, int cc, int nstage) {
     return (size_t)nstage * (stage + tables) + 64;  // + mbarriers
 }
 
+size_t dedisp_smem_bytes(const RangePlan& r, int cc, int nstage) { return dedisp_smem(r, cc, nstage); }
+
 static aa_status build_strategy(aa_plan& p) {
     for (auto& r : p.ranges) {
         const int dec = r.desc.dec;

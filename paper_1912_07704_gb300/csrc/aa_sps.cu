@@ -46,11 +46,11 @@ __device__ __forceinline__ void add128(unsigned long long& hi, unsigned long lon
 
 constexpr int kStatsThreads = 512;
 
-__global__ void __launch_bounds__(kStatsThreads) sps_stats_kernel(SpsArgs a, const double* rsw) {
+// Statistics of one series (row) and its width table; whole CTA.
+__device__ __forceinline__ void stats_row(const SpsArgs& a, const double* rsw, int row) {
     __shared__ long long s1w[kStatsThreads / 32];
     __shared__ unsigned long long hiw[kStatsThreads / 32], low[kStatsThreads / 32];
     __shared__ double sh_f, sh_inv;
-    const int row = blockIdx.x;
     const float* y = a.dd + (int64_t)row * a.pitch;
     const int64_t n = a.length;
     long long s1 = 0;
@@ -116,6 +116,10 @@ __global__ void __launch_bounds__(kStatsThreads) sps_stats_kernel(SpsArgs a, con
             tab[i] = make_float2(0.0f, -FLT_MAX);
         }
     }
+}
+
+__global__ void __launch_bounds__(kStatsThreads) sps_stats_kernel(SpsArgs a, const double* rsw) {
+    stats_row(a, rsw, blockIdx.x);
 }
 
 // Block-wide exclusive scan of one int64 per thread.
@@ -246,16 +250,18 @@ __host__ __device__ constexpr int sps_region_bytes(int wpad) {
     return (wpad * 8 > kSpsTile * 6) ? wpad * 8 : kSpsTile * 6;
 }
 
-__global__ void __launch_bounds__(NT, 2) sps_boxcar_kernel(SpsArgs a, int ntiles) {
-    extern __shared__ __align__(16) float sm[];
+// One CTA's work item: series bid / ntiles, start-time tile bid % ntiles.
+// `sm` is the dynamic shared memory; the caller guarantees that every thread
+// has finished any previous item.
+__device__ __forceinline__ void boxcar_block(const SpsArgs& a, int ntiles, int64_t bid, float* sm) {
     __shared__ long long scratch[2 * NT / 32];
     __shared__ unsigned long long s_base;
     const int wpad = a.wpad;
     const int ylen = kSpsTile + wpad + M;
     float* ys = sm;
     float2* tab = reinterpret_cast<float2*>(sm + ((ylen + 3) & ~3));
-    const int row = blockIdx.x / ntiles;
-    const int64_t tile = blockIdx.x - (int64_t)row * ntiles;
+    const int row = (int)(bid / ntiles);
+    const int64_t tile = bid - (int64_t)row * ntiles;
     const int64_t t0 = tile * kSpsOwned;
     const int64_t L = a.length;
     const float* y = a.dd + (int64_t)row * a.pitch;
@@ -396,7 +402,7 @@ __global__ void __launch_bounds__(NT, 2) sps_boxcar_kernel(SpsArgs a, int ntiles
         s_base = atomicAdd(a.count, (unsigned long long)total);
         const unsigned long long ci = atomicAdd(a.nchunks, 1ull);
         if (ci < (unsigned long long)a.chunk_cap)
-            a.chunks[ci] = CandChunk{s_base, (uint32_t)total, dm_index, (uint32_t)t0, 0u};
+            a.chunks[ci] = CandChunk{s_base, (uint32_t)total, dm_index, (uint32_t)t0, (uint32_t)a.beam};
     }
     {
         int j = (int)my_off;
@@ -468,10 +474,59 @@ __global__ void __launch_bounds__(NT, 2) sps_boxcar_kernel(SpsArgs a, int ntiles
             c.t = (uint32_t)t;
             c.width = (uint16_t)bw;
             c.range = (uint8_t)a.range;
-            c.reserved = 0;
+            c.reserved = (uint8_t)a.beam;
             c.snr = best;
             a.cands[idx] = c;
         }
+    }
+}
+
+__global__ void __launch_bounds__(NT, 2) sps_boxcar_kernel(SpsArgs a, int ntiles) {
+    extern __shared__ __align__(16) float sm[];
+    boxcar_block(a, ntiles, blockIdx.x, sm);
+}
+
+__device__ __forceinline__ int find_desc(const int64_t* first, int n, int64_t item) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (first[mid] <= item) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Persistent forms over several beams/ranges (work queues).
+__global__ void __launch_bounds__(kStatsThreads) sps_stats_batch_kernel(
+    const SpsArgs* __restrict__ descs, const int64_t* __restrict__ first, int ndesc,
+    unsigned long long* queue) {
+    __shared__ long long s_item;
+    const int64_t total = first[ndesc];
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_item = (long long)atomicAdd(queue, 1ull);
+        __syncthreads();
+        const int64_t item = s_item;
+        if (item >= total) break;
+        const int k = find_desc(first, ndesc, item);
+        stats_row(descs[k], descs[k].rsqrt_w, (int)(item - first[k]));
+    }
+}
+
+__global__ void __launch_bounds__(NT, 2) sps_boxcar_batch_kernel(
+    const SpsArgs* __restrict__ descs, const int64_t* __restrict__ first,
+    const int* __restrict__ ntiles, int ndesc, unsigned long long* queue) {
+    extern __shared__ __align__(16) float sm[];
+    __shared__ long long s_item;
+    const int64_t total = first[ndesc];
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_item = (long long)atomicAdd(queue, 1ull);
+        __syncthreads();
+        const int64_t item = s_item;
+        if (item >= total) break;
+        const int k = find_desc(first, ndesc, item);
+        boxcar_block(descs[k], ntiles[k], item - first[k], sm);
     }
 }
 
@@ -505,5 +560,30 @@ cudaError_t launch_sps_boxcar(const SpsArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+
+}  // namespace aa
+
+namespace aa {
+
+cudaError_t launch_sps_stats_batch(const SpsArgs* d_descs, const int64_t* d_first, int ndesc,
+                                   unsigned long long* d_queue, int grid, cudaStream_t s) {
+    if (ndesc <= 0) return cudaSuccess;
+    sps_stats_batch_kernel<<<grid, kStatsThreads, 0, s>>>(d_descs, d_first, ndesc, d_queue);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sps_boxcar_batch(const SpsArgs* d_descs, const int64_t* d_first,
+                                    const int* d_ntiles, int ndesc, int wpad,
+                                    unsigned long long* d_queue, int grid, cudaStream_t s) {
+    if (ndesc <= 0) return cudaSuccess;
+    const size_t smem = sps_boxcar_smem(wpad);
+    cudaError_t e = cudaFuncSetAttribute(sps_boxcar_batch_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    sps_boxcar_batch_kernel<<<grid, NT, smem, s>>>(d_descs, d_first, d_ntiles, ndesc, d_queue);
+    return cudaGetLastError();
+}
+
+int sps_boxcar_tiles(int64_t length) { return (int)((length + kSpsOwned - 1) / kSpsOwned); }
 
 }  // namespace aa

@@ -192,3 +192,30 @@ def channel_weights(nchans: int, seed: int, device="cpu") -> torch.Tensor:
     gen = torch.Generator(device=torch.device(device))
     gen.manual_seed(seed)
     return torch.rand(nchans, generator=gen, device=device, dtype=torch.float32) + 0.5
+
+
+def clipped_ska_ranges(dm_max: float) -> tuple:
+    """The 4096-channel plan's DM ranges clipped at dm_max, plus
+    (2000, 2, ., dec 16) above DM 2000."""
+    out = []
+    for (lo, step, ndm, dec) in SKA_4096.ranges + ((2000.0, 2.0, 1 << 30, 16),):
+        if lo >= dm_max:
+            break
+        n = min(ndm, int(np.ceil((dm_max - lo) / step)))
+        out.append((lo, step, n, dec))
+    return tuple(out)
+
+
+def batched_beams(n: int = 32, seed: int = PULSE_SEED + 2) -> list:
+    """Uneven beams: channels 1024 or 4096 over the same 300 MHz band,
+    lengths U{2^17..2^20}, DM_max ~ U[500, 3000] with clipped plans."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    beams = []
+    for i in range(n):
+        C = int(rng.choice([1024, 4096]))
+        T = int(rng.integers(1 << 17, (1 << 20) + 1))
+        dm_max = float(rng.uniform(500.0, 3000.0))
+        foff = -300.0 / C
+        beams.append(Workload(f"beam{i}-{C}ch-{T}", C, 1508.0, foff, 64e-6, T,
+                              clipped_ska_ranges(dm_max), 8192, 6.0, 10 + i))
+    return beams
