@@ -270,6 +270,78 @@ aa_status aa_batch_run(aa_batch* batch, aa_stream_t stream);
  * AA_WARN_CAND_OVERFLOW if more than cand_capacity were found. */
 aa_status aa_batch_candidates(aa_batch* batch, aa_stream_t stream, aa_candidates** out);
 
+/* --------------------------------------------------- streaming server -- */
+
+/* Continuous-batching search server for streaming beams (Sec. 3.3: the
+ * pipeline iterates over the input in chunks and reports a status code per
+ * iteration).  Chunk k of a beam carries chunk_nsamp new samples and is
+ * searched as the block of full-rate samples [max(0, kN - H), (k+1)N), where
+ * the beam's resident history supplies the first samples and
+ * H = max_r dec_r * (maxshift_r + W + 2) rounded up to a multiple of 16.  The
+ * block runs through the whole pipeline with its own mean and standard
+ * deviation; the chunk reports the candidates of range r whose global start
+ * index j (decimated samples, record field t) lies in
+ * [kN/dec_r - maxshift_r - W - 1, (k+1)N/dec_r - maxshift_r - W - 1).
+ * Chunks queue on the host and are admitted into slots (own stream and device
+ * workspace; slot count = min(max_slots, what memory_budget allows after the
+ * beams' resident buffers)) as slots free up; a beam's chunks run in order,
+ * chunks of different beams overlap on the device. */
+typedef struct aa_server aa_server;
+
+typedef struct aa_chunk_info {
+    int32_t beam;
+    int32_t status;        /* AA_PENDING while queued or in flight */
+    int64_t chunk;         /* index of the chunk within its beam */
+    int64_t block_start;   /* full-rate index of the block's first sample */
+    int64_t total;         /* candidates found in the whole block */
+    double arrival;        /* caller's submission time (aa_server_clock) */
+    double admitted;       /* when the chunk entered a slot */
+    double done;           /* when its completion was observed */
+} aa_chunk_info;
+
+typedef struct aa_server_report {
+    int64_t submitted, completed;
+    int32_t slots, max_in_flight;
+    int64_t history_nsamp;               /* H */
+    double latency_p50, latency_p99, latency_max;  /* done - arrival, seconds */
+    double span;                         /* last completion - first arrival, seconds */
+} aa_server_report;
+
+/* memory_budget <= 0: half of the free device memory.  chunk_nsamp must be a
+ * positive multiple of 16.  The plan is bound to the current device if
+ * needed and must outlive the server.  AA_ERR_NOMEM if not even one slot
+ * fits. */
+aa_status aa_server_create(aa_plan* plan, int32_t nbeams, int64_t chunk_nsamp, int32_t max_width,
+                           float threshold, int64_t cand_capacity, int64_t memory_budget,
+                           int32_t max_slots, aa_server** out);
+void aa_server_destroy(aa_server* server);
+
+/* Queue the next chunk of `beam`: uint8 [nchans][host_pitch] host memory
+ * (first chunk_nsamp bytes of each row), read-only, owned by the caller and
+ * kept valid until the chunk completes.  arrival_time: the caller's clock
+ * (use aa_server_clock).  Returns AA_PENDING and the chunk's ticket. */
+aa_status aa_server_submit(aa_server* server, int32_t beam, const uint8_t* host_chunk,
+                           int64_t host_pitch, double arrival_time, int64_t* ticket);
+
+/* Non-blocking progress: collect finished chunks, admit queued ones.
+ * Returns AA_OK when nothing is queued or in flight, AA_PENDING otherwise. */
+aa_status aa_server_poll(aa_server* server, int32_t* ncompleted);
+
+/* Block until every submitted chunk has completed. */
+aa_status aa_server_drain(aa_server* server);
+
+/* Status and (once complete) the chunk's candidates, library-owned and
+ * sorted by (dm_index, t); t is the global start index, `reserved` the beam.
+ * Returns the chunk's status (AA_PENDING while not complete). */
+aa_status aa_server_result(aa_server* server, int64_t ticket, aa_chunk_info* info,
+                           aa_candidates** cands);
+
+/* Latency percentiles and counters of the completed chunks. */
+aa_status aa_server_stats(const aa_server* server, aa_server_report* out);
+
+/* Monotonic clock (seconds) used for arrival and completion times. */
+double aa_server_clock(void);
+
 /* ------------------------------------------------- differentiable form -- */
 
 /* Float input with per-channel weights (every range must have dec == 1,

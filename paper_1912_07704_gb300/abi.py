@@ -65,6 +65,21 @@ class aa_candidate(ctypes.Structure):
                 ("reserved", ctypes.c_uint8), ("snr", ctypes.c_float)]
 
 
+class aa_chunk_info(ctypes.Structure):
+    _fields_ = [("beam", ctypes.c_int32), ("status", ctypes.c_int32), ("chunk", ctypes.c_int64),
+                ("block_start", ctypes.c_int64), ("total", ctypes.c_int64),
+                ("arrival", ctypes.c_double), ("admitted", ctypes.c_double),
+                ("done", ctypes.c_double)]
+
+
+class aa_server_report(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("slots", ctypes.c_int32), ("max_in_flight", ctypes.c_int32),
+                ("history_nsamp", ctypes.c_int64), ("latency_p50", ctypes.c_double),
+                ("latency_p99", ctypes.c_double), ("latency_max", ctypes.c_double),
+                ("span", ctypes.c_double)]
+
+
 CANDIDATE_DTYPE = np.dtype([("dm_index", "<u4"), ("t", "<u4"), ("width", "<u2"),
                             ("range", "u1"), ("reserved", "u1"), ("snr", "<f4")])
 assert CANDIDATE_DTYPE.itemsize == ctypes.sizeof(aa_candidate) == 16
@@ -106,6 +121,15 @@ _SIG = {
     "aa_batch_info": (ctypes.c_int, [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I64)]),
     "aa_batch_run": (ctypes.c_int, [_P, _P]),
     "aa_batch_candidates": (ctypes.c_int, [_P, _P, ctypes.POINTER(_P)]),
+    "aa_server_create": (ctypes.c_int, [_P, _I32, _I64, _I32, _F32, _I64, _I64, _I32,
+                                        ctypes.POINTER(_P)]),
+    "aa_server_destroy": (None, [_P]),
+    "aa_server_submit": (ctypes.c_int, [_P, _I32, _P, _I64, ctypes.c_double, ctypes.POINTER(_I64)]),
+    "aa_server_poll": (ctypes.c_int, [_P, ctypes.POINTER(_I32)]),
+    "aa_server_drain": (ctypes.c_int, [_P]),
+    "aa_server_result": (ctypes.c_int, [_P, _I64, ctypes.POINTER(aa_chunk_info), ctypes.POINTER(_P)]),
+    "aa_server_stats": (ctypes.c_int, [_P, ctypes.POINTER(aa_server_report)]),
+    "aa_server_clock": (ctypes.c_double, []),
     "aa_profile_enable": (ctypes.c_int, [_I32]),
     "aa_profile_read": (ctypes.c_int, [_I32, ctypes.POINTER(_I64), ctypes.POINTER(ctypes.c_double)]),
     "aa_profile_kernel_name": (ctypes.c_char_p, [_I32]),
@@ -345,3 +369,54 @@ def aa_batch_candidates(batch, stream) -> tuple:
     st = check(lib().aa_batch_candidates(batch, stream, ctypes.byref(h)), "aa_batch_candidates",
                ok=(AA_OK, AA_WARN_CAND_OVERFLOW))
     return h.value, st
+
+
+def aa_server_create(plan, nbeams, chunk_nsamp, max_width, threshold, capacity, budget=0,
+                     max_slots=8) -> int:
+    h = ctypes.c_void_p()
+    check(lib().aa_server_create(plan, int(nbeams), int(chunk_nsamp), int(max_width),
+                                 float(threshold), int(capacity), int(budget), int(max_slots),
+                                 ctypes.byref(h)), "aa_server_create")
+    return h.value
+
+
+def aa_server_destroy(server) -> None:
+    lib().aa_server_destroy(server)
+
+
+def aa_server_submit(server, beam, host_ptr, host_pitch, arrival) -> int:
+    t = ctypes.c_int64()
+    check(lib().aa_server_submit(server, int(beam), host_ptr, int(host_pitch), float(arrival),
+                                 ctypes.byref(t)), "aa_server_submit", ok=(AA_PENDING,))
+    return t.value
+
+
+def aa_server_poll(server) -> tuple:
+    n = ctypes.c_int32()
+    st = check(lib().aa_server_poll(server, ctypes.byref(n)), "aa_server_poll",
+               ok=(AA_OK, AA_PENDING))
+    return st, n.value
+
+
+def aa_server_drain(server) -> None:
+    check(lib().aa_server_drain(server), "aa_server_drain")
+
+
+def aa_server_result(server, ticket, want_candidates=True) -> tuple:
+    info = aa_chunk_info()
+    h = ctypes.c_void_p()
+    st = lib().aa_server_result(server, int(ticket), ctypes.byref(info),
+                                ctypes.byref(h) if want_candidates else None)
+    if st not in (AA_OK, AA_PENDING, AA_WARN_CAND_OVERFLOW):
+        raise AAError(st, "aa_server_result")
+    return st, info, h.value
+
+
+def aa_server_stats(server) -> aa_server_report:
+    s = aa_server_report()
+    check(lib().aa_server_stats(server, ctypes.byref(s)), "aa_server_stats")
+    return s
+
+
+def aa_server_clock() -> float:
+    return lib().aa_server_clock()

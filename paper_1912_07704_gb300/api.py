@@ -315,3 +315,55 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+class Server:
+    """Streaming continuous-batching search server (see aa_server_create)."""
+
+    def __init__(self, plan, nbeams, chunk_nsamp, max_width, threshold, capacity=1 << 20,
+                 budget=0, max_slots=8):
+        plan.bind()
+        self.plan = plan
+        self.chunk_nsamp = int(chunk_nsamp)
+        self.handle = abi.aa_server_create(plan.handle, nbeams, chunk_nsamp, max_width, threshold,
+                                           capacity, budget, max_slots)
+
+    def submit(self, beam: int, host_chunk: np.ndarray, arrival=None) -> int:
+        """Queue the next chunk of a beam; host_chunk (uint8 [nchans][>= N],
+        unit stride rows) must stay valid until the chunk completes."""
+        assert host_chunk.dtype == np.uint8 and host_chunk.strides[1] == 1
+        t = abi.aa_server_clock() if arrival is None else arrival
+        return abi.aa_server_submit(self.handle, beam, host_chunk.ctypes.data,
+                                    host_chunk.strides[0], t)
+
+    def poll(self) -> tuple:
+        return abi.aa_server_poll(self.handle)
+
+    def drain(self):
+        abi.aa_server_drain(self.handle)
+
+    def result(self, ticket: int):
+        """(status, aa_chunk_info, candidates array or None)."""
+        st, info, h = abi.aa_server_result(self.handle, ticket)
+        arr = None
+        if h:
+            arr, _ = _candidates_array(h)
+        return st, info, arr
+
+    def stats(self):
+        return abi.aa_server_stats(self.handle)
+
+    @staticmethod
+    def clock() -> float:
+        return abi.aa_server_clock()
+
+    def close(self):
+        if getattr(self, "handle", None):
+            abi.aa_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

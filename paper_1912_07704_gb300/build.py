@@ -21,7 +21,8 @@ INCLUDE = os.path.join(ROOT, "include")
 OBJDIR = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libaa_gb300.so")
 SOURCES = ["aa_plan.cpp", "aa_api.cpp", "aa_api_f32.cpp", "aa_profile.cpp", "aa_dedisp.cu",
-           "aa_sps.cu", "aa_noalloc.cu", "aa_adjoint.cu", "aa_batch.cpp", "aa_autotune.cpp"]
+           "aa_sps.cu", "aa_noalloc.cu", "aa_adjoint.cu", "aa_batch.cpp", "aa_autotune.cpp",
+           "aa_server.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
