@@ -222,6 +222,11 @@ aa_status aa_sps_search_device(const aa_plan* plan, int64_t nsamp, const float* 
                                float* d_snr_out, void* d_ws, size_t ws_bytes,
                                aa_stream_t stream);
 
+/* Width-samples the last aa_sps_search_device call on this workspace actually
+ * evaluated (width blocks whose SNR bound is below the threshold are skipped
+ * when no B(t) output is requested).  Synchronises `stream`. */
+aa_status aa_sps_workspace_work(const void* d_ws, aa_stream_t stream, int64_t* evaluated);
+
 /* Read and clear the device error word kept at the start of a workspace used
  * by the calls above (synchronises `stream`).  AA_OK, or AA_ERR_TIMEOUT if a
  * bounded device-side wait gave up. */

@@ -99,6 +99,7 @@ _SIG = {
     "aa_sps_search_device": (ctypes.c_int, [_P, _I64, _P, _I32, _F32, _P, _I64, _P, _P, _P,
                                             ctypes.c_size_t, _P]),
     "aa_workspace_status": (ctypes.c_int, [_P, _P]),
+    "aa_sps_workspace_work": (ctypes.c_int, [_P, _P, ctypes.POINTER(_I64)]),
     "aa_dedisperse": (ctypes.c_int, [_P, _P, _I64, _I64, _P, ctypes.POINTER(_P)]),
     "aa_dd_result_view": (ctypes.c_int, [_P, ctypes.POINTER(_P), ctypes.POINTER(_I64)]),
     "aa_dd_result_destroy": (None, [_P]),
@@ -420,3 +421,9 @@ def aa_server_stats(server) -> aa_server_report:
 
 def aa_server_clock() -> float:
     return lib().aa_server_clock()
+
+
+def aa_sps_workspace_work(d_ws, stream) -> int:
+    v = ctypes.c_int64()
+    check(lib().aa_sps_workspace_work(d_ws, stream, ctypes.byref(v)), "aa_sps_workspace_work")
+    return v.value

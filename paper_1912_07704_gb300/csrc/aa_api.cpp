@@ -201,7 +201,7 @@ aa_status aa_sps_search_device(const aa_plan* p, int64_t nsamp, const float* d_d
     if (!d_dd) { set_error("d_dd is NULL"); return AA_ERR_ARG; }
     char* ws = static_cast<char*>(d_ws);
     unsigned* err = reinterpret_cast<unsigned*>(ws);
-    AA_CUDA(cudaMemsetAsync(err, 0, 16, s), "clear error word and chunk counter");
+    AA_CUDA(cudaMemsetAsync(err, 0, 24, s), "clear error word and counters");
     unsigned long long* nchunks = reinterpret_cast<unsigned long long*>(ws + kChunkCounterOffset);
     CandChunk* chunks = reinterpret_cast<CandChunk*>(ws + L.chunk_offset);
     double* rsw = reinterpret_cast<double*>(ws + kErrBlock);
@@ -236,6 +236,7 @@ aa_status aa_sps_search_device(const aa_plan* p, int64_t nsamp, const float* d_d
         a.chunks = chunks;
         a.nchunks = nchunks;
         a.chunk_cap = L.chunk_cap;
+        a.evaluated = reinterpret_cast<unsigned long long*>(ws + kEvaluatedOffset);
         if (a.length <= 0) continue;
         {
             ProfScope prof(kKStats, s);
@@ -244,6 +245,18 @@ aa_status aa_sps_search_device(const aa_plan* p, int64_t nsamp, const float* d_d
         ProfScope prof(kKBoxcar, s);
         AA_CUDA(launch_sps_boxcar(a, s), "sps boxcar launch");
     }
+    return AA_OK;
+}
+
+aa_status aa_sps_workspace_work(const void* d_ws, aa_stream_t stream, int64_t* evaluated) {
+    clear_error();
+    if (!d_ws || !evaluated) { set_error("d_ws/evaluated is NULL"); return AA_ERR_ARG; }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    unsigned long long v = 0;
+    AA_CUDA(cudaMemcpyAsync(&v, static_cast<const char*>(d_ws) + kEvaluatedOffset, sizeof v,
+                            cudaMemcpyDeviceToHost, s), "read work counter");
+    AA_CUDA(cudaStreamSynchronize(s), "synchronize");
+    *evaluated = (int64_t)v;
     return AA_OK;
 }
 

@@ -315,6 +315,7 @@ aa_status aa_batch_create(aa_plan* const* plans, const int64_t* nsamps, int32_t 
                 s.chunks = b->d_chunks;
                 s.nchunks = &b->d_counts[1];
                 s.chunk_cap = b->chunk_cap;
+                s.evaluated = nullptr;
                 T.sps.push_back(s);
                 T.st_first.push_back(T.st_first.back() + s.nrows);
                 const int nt = sps_boxcar_tiles(s.length);

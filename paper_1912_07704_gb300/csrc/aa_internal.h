@@ -116,7 +116,8 @@ struct CandChunk {
     uint32_t reserved;
 };
 static_assert(sizeof(CandChunk) == 24, "CandChunk layout");
-constexpr int64_t kChunkCounterOffset = 8;  // bytes into the error block
+constexpr int64_t kChunkCounterOffset = 8;   // bytes into the error block
+constexpr int64_t kEvaluatedOffset = 16;     // evaluated width-samples counter
 
 // ------------------------------------------------------------- profiling --
 enum KernelId {
@@ -198,6 +199,7 @@ struct SpsArgs {
     unsigned* err;
     int32_t prune;          // skip width blocks bounded below the threshold
     int32_t beam;           // beam id stored in candidate records (batched mode)
+    unsigned long long* evaluated;  // width-samples actually evaluated (instrumentation)
     CandChunk* chunks;      // chunk headers (all ranges)
     unsigned long long* nchunks;
     int64_t chunk_cap;

@@ -193,11 +193,12 @@ constexpr int NT = kSpsThreads;
 // the threshold by the caller).
 constexpr float kBig = 1.2676506002282294e30f;  // 2^100
 
-__device__ __forceinline__ void boxcar_prefix(const float* __restrict__ P,
-                                              const float2* __restrict__ tab, int wpad,
-                                              const float (&base)[M], unsigned skip,
-                                              float (&B)[M]) {
+__device__ __forceinline__ int boxcar_prefix(const float* __restrict__ P,
+                                             const float2* __restrict__ tab, int wpad,
+                                             const float (&base)[M], unsigned skip,
+                                             float (&B)[M]) {
     const float* pb = P + M * threadIdx.x;
+    int evaluated = 0;
 #pragma unroll
     for (int i = 0; i < M; ++i) B[i] = -FLT_MAX;
     for (int w0 = 0; w0 < wpad; w0 += M) {
@@ -206,6 +207,7 @@ __device__ __forceinline__ void boxcar_prefix(const float* __restrict__ P,
             w0 = (2 << (31 - __clz(w0))) - M;
             continue;
         }
+        ++evaluated;
         float win[2 * M];  // win[k] = P[p_thread + w0 + k]
 #pragma unroll
         for (int k = 0; k < 2 * M; k += 4) {
@@ -224,6 +226,7 @@ __device__ __forceinline__ void boxcar_prefix(const float* __restrict__ P,
             }
         }
     }
+    return evaluated;
 }
 
 // Exact int64 running sums for slot i, for tiles whose partial sums may
@@ -368,10 +371,14 @@ __device__ __forceinline__ void boxcar_block(const SpsArgs& a, int ntiles, int64
                     skip |= 1u << k;
             }
         }
-        boxcar_prefix(P, tab, wpad, base, skip, B);
+        const int chunks = boxcar_prefix(P, tab, wpad, base, skip, B);
+        if (a.evaluated && (threadIdx.x & 31) == 0)
+            atomicAdd(a.evaluated, (unsigned long long)chunks * 32ull * M * M);
     } else {
 #pragma unroll
         for (int i = 0; i < M; ++i) B[i] = boxcar_exact_slot(ys, tab, wpad, i);
+        if (a.evaluated && threadIdx.x == 0)
+            atomicAdd(a.evaluated, (unsigned long long)wpad * NT * M);
     }
 
     __syncthreads();  // everyone done with the table
