@@ -53,6 +53,21 @@ def dist_env():
     return ws, rank, local
 
 
+def job_totals(seconds: float, units: float):
+    """Whole-job (time, units) over all ranks: the slowest rank's time and the
+    sum of the units every rank processed.  Ranks work on independent beams, so
+    this is the only cross-rank exchange (host-side, gloo)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return seconds, units
+    tt = torch.tensor([seconds], dtype=torch.float64)
+    uu = torch.tensor([units], dtype=torch.float64)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    dist.all_reduce(uu, op=dist.ReduceOp.SUM)
+    return float(tt.item()), float(uu.item())
+
+
 def load_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -259,13 +274,9 @@ def bench_ours(args):
     abi.aa_profile_enable(False)
     prof = abi.profile_snapshot()
     clk = clocks.stop()
-    t = ev0.elapsed_time(ev1) / 1e3
-    if ws > 1:
-        tt = torch.tensor([t], dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t = float(tt.item())
+    t, units = job_totals(ev0.elapsed_time(ev1) / 1e3, alg["dm_samples"] * args.steps)
     ncand = int(count.item())
-    value = alg["dm_samples"] * args.steps * ws / t
+    value = units / t
     step_s = t / args.steps
     launches = sum(v[0] for v in prof.values())
 
@@ -290,12 +301,8 @@ def bench_ours(args):
             dd.close()
             d2h += 8 + arr.nbytes
         torch.cuda.synchronize()
-        te = time.perf_counter() - t0
-        if ws > 1:
-            tt = torch.tensor([te], dtype=torch.float64)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            te = float(tt.item())
-        e2e = {"value": alg["dm_samples"] * args.steps * ws / te, "unit": UNIT,
+        te, units_e = job_totals(time.perf_counter() - t0, alg["dm_samples"] * args.steps)
+        e2e = {"value": units_e / te, "unit": UNIT,
                "h2d_bytes_per_step": w.nchans * nsamp,
                "d2h_bytes_per_step": int(d2h / args.steps)}
 
