@@ -359,7 +359,7 @@ aa_status aa_batch_create(aa_plan* const* plans, const int64_t* nsamps, int32_t 
     cudaDeviceProp prop{};
     cudaGetDeviceProperties(&prop, dev);
     const int sms = prop.multiProcessorCount;
-    b->grid_dd = sms;  // one 512-thread CTA per SM (the staging ring uses ~120 KB)
+    b->grid_dd = sms * 2;  // two 512-thread CTAs per SM (each staging ring <= 113 KB)
     b->grid_st = sms * 4;
     b->grid_bx = sms * 2;
     b->grid_dec = sms * 16;

@@ -365,7 +365,7 @@ __device__ __forceinline__ int find_desc(const int64_t* first, int n, int64_t it
     return lo;
 }
 
-__global__ void __launch_bounds__(kDedispThreads, 1)
+__global__ void __launch_bounds__(kDedispThreads, 2)
     dedisperse_batch_kernel(const DedispArgs* __restrict__ descs, const int64_t* __restrict__ first,
                             const int* __restrict__ ndm_blocks, int ndesc,
                             unsigned long long* queue, uint64_t wait_limit_ns, uint32_t one) {

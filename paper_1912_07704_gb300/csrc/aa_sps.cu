@@ -188,24 +188,90 @@ constexpr int NT = kSpsThreads;
 // S_w(t) = P[p+w] - P[p] is an exact FP32 integer (the caller checked that
 // the prefix range of the tile is <= 2^24), so this is bit for bit the
 // running sum.  Thread owns slots p = M*tid + i; base[i] = P[p] (or +kBig for
-// a start outside the series).  Width blocks w-1 in [2^k, 2^(k+1)), k >= 4,
-// whose bit is set in `skip` are not evaluated (their SNRs are bounded below
-// the threshold by the caller).
+// a start outside the series).  C[i] receives w0 of the first chunk of M
+// widths (w0+1 .. w0+M) whose best SNR equals B[i]: the smallest maximising
+// width lies in that chunk, so the candidate's width is found by evaluating
+// it alone.
 constexpr float kBig = 1.2676506002282294e30f;  // 2^100
 
+// Bound of one warp over a width segment [w1, w2].  For every start slot p
+// of the warp and w in the segment, S_w(p) <= max P(ends) - min P(starts)
+// and -w f <= -w1 f (f >= 0) or -w2 f (f < 0), so SNR_w <= ub =
+// (pmax - pmin - drift) / (sigma sqrt(w1)) when positive.  Evaluated in FP32
+// with the rounding of each step bounded and added (|f| <= 1/2 since
+// m0 = round(mu); pmax - pmin is exact).
+struct WarpBound {
+    float pmin;        // min of P over the warp's valid starts (FLT_MAX: none)
+    float f;           // mu - m0
+    float inv_sigma;
+    float cut;         // blocks bounded below this are skipped (-FLT_MAX: none)
+    const double* rsqrt_w;
+    int max_width, ylen, p_first;
+    bool active;       // pruning enabled
+};
+
+__device__ __forceinline__ float warp_segment_bound(const float* __restrict__ P, const WarpBound& b,
+                                                    int w1, int w2) {
+    const int lane = threadIdx.x & 31;
+    const int lo = b.p_first + w1, hi = min(b.ylen - 1, b.p_first + M * 32 - 1 + w2);
+    float pmax = -FLT_MAX;
+    for (int j = lo + lane; j <= hi; j += 32) pmax = fmaxf(pmax, P[j]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) pmax = fmaxf(pmax, __shfl_xor_sync(0xffffffffu, pmax, o));
+    const float drift = b.f >= 0.0f ? (float)w1 * b.f : (float)w2 * b.f;
+    const float diff = pmax - b.pmin;
+    const float rs = (float)b.rsqrt_w[w1 - 1];
+    // 6 roundings of at most 2^-24 relative each on magnitudes <= |diff| + |drift|
+    const float slack = (fabsf(diff) + fabsf(drift)) * b.inv_sigma * rs * 1e-6f + 1e-6f;
+    const float ub = (diff - drift) * b.inv_sigma * rs + slack;
+    return ub * (1.0f + 1e-4f) + 1e-4f;
+}
+
+// Main loop.  With pruning, the widths after the first chunk are checked in
+// power-of-two blocks [w0+1, 2 w0] (w0 = 16, 32, ...), and inside a block
+// that survives and spans more than 128 widths, in segments [w0+1, w0+128].
+// A block or segment is skipped when its warp bound is below max(cut, min
+// over the warp's slots of the running B): below the running B it can
+// change neither B nor C of any slot (exact for every slot); below the
+// threshold cut it can only change sub-threshold values (exact for every
+// B >= threshold and for every peak decision).  Widths are visited in
+// increasing order, so the running B of the small widths prunes the wide
+// ones, and a warp far before a bright pulse evaluates only the segments
+// whose window ends can reach it.
 __device__ __forceinline__ int boxcar_prefix(const float* __restrict__ P,
                                              const float2* __restrict__ tab, int wpad,
-                                             const float (&base)[M], unsigned skip,
-                                             float (&B)[M]) {
+                                             const float (&base)[M], const WarpBound& bnd,
+                                             float (&B)[M], int (&C)[M]) {
     const float* pb = P + M * threadIdx.x;
     int evaluated = 0;
 #pragma unroll
-    for (int i = 0; i < M; ++i) B[i] = -FLT_MAX;
+    for (int i = 0; i < M; ++i) {
+        B[i] = -FLT_MAX;
+        C[i] = 0;
+    }
     for (int w0 = 0; w0 < wpad; w0 += M) {
-        if (w0 >= 16 && ((skip >> (31 - __clz(w0))) & 1u)) {
-            // jump to the next width block
-            w0 = (2 << (31 - __clz(w0))) - M;
-            continue;
+        const bool blk = (w0 & (w0 - 1)) == 0;  // first chunk of a power-of-two block
+        if (bnd.active && w0 >= 16 && (blk || (w0 >= 256 && (w0 & 127) == 0))) {
+            int w_end = blk ? 2 * w0 : w0 + 128;
+            bool skip = bnd.pmin == FLT_MAX;
+            if (!skip) {
+                float bmin = B[0];
+#pragma unroll
+                for (int i = 1; i < M; ++i) bmin = fminf(bmin, B[i]);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1)
+                    bmin = fminf(bmin, __shfl_xor_sync(0xffffffffu, bmin, o));
+                const float floor_b = fmaxf(bnd.cut, bmin);
+                skip = warp_segment_bound(P, bnd, w0 + 1, min(w_end, bnd.max_width)) < floor_b;
+                if (!skip && blk && w0 >= 256) {
+                    w_end = w0 + 128;
+                    skip = warp_segment_bound(P, bnd, w0 + 1, min(w_end, bnd.max_width)) < floor_b;
+                }
+            }
+            if (skip) {
+                w0 = w_end - M;  // next block or segment
+                continue;
+            }
         }
         ++evaluated;
         float win[2 * M];  // win[k] = P[p_thread + w0 + k]
@@ -214,15 +280,31 @@ __device__ __forceinline__ int boxcar_prefix(const float* __restrict__ P,
             const float4 v = *reinterpret_cast<const float4*>(pb + w0 + k);
             win[k] = v.x; win[k + 1] = v.y; win[k + 2] = v.z; win[k + 3] = v.w;
         }
+        float Bc[M];  // best SNR of this chunk, per slot
+        {
+            const float2 rc0 = tab[w0];
+            const float2 rc1 = tab[w0 + 1];
 #pragma unroll
-        for (int s = 0; s < M; s += 2) {
+            for (int i = 0; i < M; ++i)
+                Bc[i] = fmaxf(fmaf(win[i + 1] - base[i], rc0.x, rc0.y),
+                              fmaf(win[i + 2] - base[i], rc1.x, rc1.y));
+        }
+#pragma unroll
+        for (int s = 2; s < M; s += 2) {
             const float2 rc0 = tab[w0 + s];
             const float2 rc1 = tab[w0 + s + 1];
 #pragma unroll
             for (int i = 0; i < M; ++i) {
                 const float v0 = fmaf(win[i + s + 1] - base[i], rc0.x, rc0.y);
                 const float v1 = fmaf(win[i + s + 2] - base[i], rc1.x, rc1.y);
-                B[i] = max3f(B[i], v0, v1);
+                Bc[i] = max3f(Bc[i], v0, v1);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < M; ++i) {
+            if (Bc[i] > B[i]) {  // strict: an equal later chunk keeps the earlier one
+                B[i] = Bc[i];
+                C[i] = w0;
             }
         }
     }
@@ -248,9 +330,9 @@ __device__ __noinline__ float boxcar_exact_slot(const float* __restrict__ ys,
 }
 
 // Shared memory after the main loop: the table region is reused for B(t)
-// (kSpsTile floats) followed by the candidate positions (kSpsTile u16).
+// (kSpsTile floats) followed by the candidate entries (kSpsTile u32).
 __host__ __device__ constexpr int sps_region_bytes(int wpad) {
-    return (wpad * 8 > kSpsTile * 6) ? wpad * 8 : kSpsTile * 6;
+    return (wpad * 8 > kSpsTile * 8) ? wpad * 8 : kSpsTile * 8;
 }
 
 // One CTA's work item: series bid / ntiles, start-time tile bid % ntiles.
@@ -328,6 +410,7 @@ __device__ __forceinline__ void boxcar_block(const SpsArgs& a, int ntiles, int64
     const int vb = (int)min((int64_t)ylen - 1, L - t0);
 
     float B[M];
+    int C[M];  // per slot: w0 of the first width chunk reaching B (0 on the exact path)
     if (fast) {
         // ys -> prefix sums P, in place (exact FP32 integers)
         __syncthreads();
@@ -348,42 +431,35 @@ __device__ __forceinline__ void boxcar_block(const SpsArgs& a, int ntiles, int64
             base[i] = valid ? P[p] : kBig;
             if (valid) pmin = fminf(pmin, base[i]);
         }
-        // Per-warp bound on SNR over a width block: window sums are at most
-        // max P(ends) - min P(starts); SNR = (S - w f)/(sigma sqrt w).
-        unsigned skip = 0;
-        if (a.prune && a.threshold > 0.0f) {
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) pmin = fminf(pmin, __shfl_xor_sync(0xffffffffu, pmin, o));
-            const double f = st.mu - (double)m0;
-            const float inv_sigma = (float)st.inv_sigma;
-            const int p_first = M * 32 * warp;
-            for (int k = 4; (1 << k) < a.max_width; ++k) {
-                const int w1 = (1 << k) + 1, w2 = min(2 << k, a.max_width);
-                const int lo = p_first + w1, hi = min(ylen - 1, p_first + M * 32 - 1 + w2);
-                float pmax = -FLT_MAX;
-                for (int j = lo + lane; j <= hi; j += 32) pmax = fmaxf(pmax, P[j]);
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) pmax = fmaxf(pmax, __shfl_xor_sync(0xffffffffu, pmax, o));
-                const double drift = f >= 0 ? (double)w1 * f : (double)w2 * f;
-                const double num = (double)pmax - (double)pmin - drift;
-                const double ub = num > 0 ? num * (double)inv_sigma / sqrt((double)w1) : num;
-                if (pmin == FLT_MAX || ub * (1.0 + 1e-4) + 1e-4 < (double)a.threshold - 1e-3)
-                    skip |= 1u << k;
-            }
-        }
-        const int chunks = boxcar_prefix(P, tab, wpad, base, skip, B);
+        for (int o = 16; o > 0; o >>= 1) pmin = fminf(pmin, __shfl_xor_sync(0xffffffffu, pmin, o));
+        WarpBound bnd;
+        bnd.pmin = pmin;
+        bnd.f = (float)(st.mu - (double)m0);
+        bnd.inv_sigma = (float)st.inv_sigma;
+        bnd.cut = a.threshold > 0.0f ? a.threshold - 1e-3f : -FLT_MAX;
+        bnd.rsqrt_w = a.rsqrt_w;
+        bnd.max_width = a.max_width;
+        bnd.ylen = ylen;
+        bnd.p_first = M * 32 * warp;
+        bnd.active = a.prune != 0;
+        const int chunks = boxcar_prefix(P, tab, wpad, base, bnd, B, C);
         if (a.evaluated && (threadIdx.x & 31) == 0)
             atomicAdd(a.evaluated, (unsigned long long)chunks * 32ull * M * M);
     } else {
 #pragma unroll
-        for (int i = 0; i < M; ++i) B[i] = boxcar_exact_slot(ys, tab, wpad, i);
+        for (int i = 0; i < M; ++i) {
+            B[i] = boxcar_exact_slot(ys, tab, wpad, i);
+            C[i] = 0;
+        }
         if (a.evaluated && threadIdx.x == 0)
             atomicAdd(a.evaluated, (unsigned long long)wpad * NT * M);
     }
 
     __syncthreads();  // everyone done with the table
     float* Bs = reinterpret_cast<float*>(tab);  // B(t) of every slot
-    unsigned short* plist = reinterpret_cast<unsigned short*>(Bs + kSpsTile);
+    // candidate entries: slot p (bits 0-15) | first chunk w0 / M (bits 16-31)
+    uint32_t* plist = reinterpret_cast<uint32_t*>(Bs + kSpsTile);
 #pragma unroll
     for (int i = 0; i < M; ++i) Bs[M * threadIdx.x + i] = B[i];
     __syncthreads();
@@ -413,11 +489,10 @@ __device__ __forceinline__ void boxcar_block(const SpsArgs& a, int ntiles, int64
     }
     {
         int j = (int)my_off;
-        while (cmask) {
-            const int i = __ffs(cmask) - 1;
-            cmask &= cmask - 1;
-            plist[j++] = (unsigned short)(M * threadIdx.x + i);
-        }
+#pragma unroll
+        for (int i = 0; i < M; ++i)
+            if ((cmask >> i) & 1u)
+                plist[j++] = (uint32_t)(M * threadIdx.x + i) | ((uint32_t)(C[i] / M) << 16);
     }
     __syncthreads();
 
@@ -426,7 +501,8 @@ __device__ __forceinline__ void boxcar_block(const SpsArgs& a, int ntiles, int64
     // fmaf of the correctly rounded sum), one warp per candidate, widths
     // interleaved over lanes with a warp prefix sum.
     for (int q = warp; q < (int)total; q += NT / 32) {
-        const int p = plist[q];
+        const int p = (int)(plist[q] & 0xffffu);
+        const int cw0 = (int)(plist[q] >> 16) * M;
         const int64_t t = t0 - 1 + p;
         const int wmax = (int)min((int64_t)a.max_width, L - t);
         const float* yq = ys + p;  // exact path: yq[w-1] = y[t+w-1] - m0
@@ -437,7 +513,7 @@ __device__ __forceinline__ void boxcar_block(const SpsArgs& a, int ntiles, int64
             // prefix form: S_w = P[p+w] - P[p], exact
             const float* P = ys;
             const float b0 = P[p];
-            for (int w0 = 0; w0 < wmax; w0 += 32) {
+            for (int w0 = cw0; w0 < wmax; w0 += 32) {
                 const int w = w0 + lane + 1;
                 if (w <= wmax) {
                     const float2 rc = __ldg(gtab + w - 1);
