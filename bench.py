@@ -236,6 +236,10 @@ def bench_ours(args):
         dist.init_process_group("gloo")
     w = workload(args.workload)
     plan = Plan.from_workload(w)
+    if args.strategy != "auto":
+        for r in range(len(w.ranges)):
+            plan.set_strategy(r, abi.AA_DEDISP_GROUPED if args.strategy == "grouped"
+                              else abi.AA_DEDISP_DIRECT)
     plan.bind(local)
     info = plan.query(w.nsamp, w.max_width)
     x = build_input(plan, w, "cuda")
@@ -364,7 +368,10 @@ def bench_ours(args):
             "config": {"workload": w.name, "nchans": w.nchans, "nsamp": w.nsamp,
                        "dm_trials": sum(g.ndm for g in alg["lay"]), "max_width": w.max_width,
                        "threshold": w.threshold, "parallelism": f"beams x{ws}",
-                       "l2": "inputs larger than L2 (4.29 GB filterbank, 9.18 GB dedispersed)"},
+                       "dedispersion": [("grouped" if abi.aa_plan_range(plan.handle, nsamp, r).strategy
+                                         else "direct") for r in range(len(w.ranges))],
+                       "l2": (f"inputs larger than L2 ({alg['in_bytes'] / 1e9:.2f} GB filterbank, "
+                              f"{alg['dd_bytes'] / 1e9:.2f} GB dedispersed)")},
             "rtf": (w.nsamp * w.tsamp) / step_s,
             "hbm": {"effective_input_gbs": eff_in_gbs, "frac_of_measured": eff_in_gbs / hbm,
                     "algorithmic_gbs": (alg["in_bytes"] + alg["dd_bytes"]) / step_s / 1e9,
@@ -571,6 +578,8 @@ def main():
     ap.add_argument("--workload", choices=["ska", "ska-small", "adjoint", "batched", "stream"],
                     default="ska")
     ap.add_argument("--stream-chunks", type=int, default=6)
+    ap.add_argument("--strategy", choices=["auto", "direct", "grouped"], default="auto",
+                    help="dedispersion strategy of every range (auto: the plan's choice)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

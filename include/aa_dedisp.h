@@ -138,6 +138,9 @@ typedef struct aa_range_info {
     int32_t stages;          /* pipeline depth of the staging copies */
     int32_t span_max;        /* largest delay spread across one CTA's trials */
     int32_t smem_bytes;      /* dynamic shared memory per dedispersion CTA */
+    int32_t strategy;        /* aa_dedisp_strategy in use for this range */
+    int32_t grouped_available;  /* 1 if AA_DEDISP_GROUPED can be selected */
+    double grouped_work;     /* adds of the grouped strategy / adds of the direct one */
 } aa_range_info;
 
 /* Strategy and memory requests for `nsamp` samples and boxcar widths up to
@@ -234,10 +237,26 @@ aa_status aa_workspace_status(void* d_ws, aa_stream_t stream);
 
 /* ------------------------------------------------------------ autotuner -- */
 
+/* How a range's dedispersion is computed; the result is identical (exact
+ * integer sums, only their grouping differs).  No counterpart in the paper,
+ * which leaves the kernel to the library.
+ *   AA_DEDISP_DIRECT:  every trial adds every channel (shift-and-sum).
+ *   AA_DEDISP_GROUPED: within a block of 16 trials and a chunk of channels,
+ *     channels whose delays differ from the block's first trial by the same
+ *     amounts at every trial are first summed once; each trial then adds the
+ *     group sums.  Available when the plan could build the group tables. */
+typedef enum { AA_DEDISP_DIRECT = 0, AA_DEDISP_GROUPED = 1 } aa_dedisp_strategy;
+
+/* Select the strategy of range r (aa_plan_create picks one from the number
+ * of adds each needs).  AA_ERR_ARG for a bad range or strategy value,
+ * AA_ERR_CONFIG if the grouped tables are not available for that range.
+ * Like aa_plan_autotune, call it while no work of the plan is in flight. */
+aa_status aa_plan_set_strategy(aa_plan* plan, int32_t r, int32_t strategy);
+
 /* Time the dedispersion kernel of every range of a bound plan over a
- * synthetic probe input of nsamp_probe samples for each feasible tile shape
- * (channels per shared-memory stage x staging depth) and keep the fastest
- * in the plan's strategy.  Call before the plan's first dedispersion (the
+ * synthetic probe input of nsamp_probe samples for the grouped strategy (if
+ * available) and each feasible direct tile shape (channels per shared-memory
+ * stage x staging depth) and keep the fastest in the plan's strategy.  Call before the plan's first dedispersion (the
  * strategy is fixed from then on).  cache_path: optional text file; shapes
  * found there (keyed by GPU model, SM count, channels, decimation and the
  * staged row size) are applied without timing, new results are appended.

@@ -45,7 +45,8 @@ class aa_range_info(ctypes.Structure):
                 ("row_offset", ctypes.c_int64), ("tile_dms", ctypes.c_int32),
                 ("tile_samples", ctypes.c_int32), ("stage_channels", ctypes.c_int32),
                 ("stages", ctypes.c_int32), ("span_max", ctypes.c_int32),
-                ("smem_bytes", ctypes.c_int32)]
+                ("smem_bytes", ctypes.c_int32), ("strategy", ctypes.c_int32),
+                ("grouped_available", ctypes.c_int32), ("grouped_work", ctypes.c_double)]
 
 
 class aa_plan_info(ctypes.Structure):
@@ -116,6 +117,7 @@ _SIG = {
     "aa_dedisperse_f32_mse_device": (ctypes.c_int, [_P, _P, _I64, _I64, _P, _P, _P, _P, _P, _P,
                                                     ctypes.c_size_t, _P]),
     "aa_plan_autotune": (ctypes.c_int, [_P, _I64, ctypes.c_char_p]),
+    "aa_plan_set_strategy": (ctypes.c_int, [_P, _I32, _I32]),
     "aa_batch_create": (ctypes.c_int, [_P, _P, _I32, _I32, _F32, _I64, _I64, ctypes.POINTER(_P)]),
     "aa_batch_destroy": (None, [_P]),
     "aa_batch_input": (ctypes.c_int, [_P, _I32, ctypes.POINTER(_P), ctypes.POINTER(_I64)]),
@@ -326,6 +328,14 @@ def aa_dedisperse_f32_mse_device(plan, d_x, nsamp, x_pitch, d_w, d_tmpl, d_loss,
     check(lib().aa_dedisperse_f32_mse_device(plan, d_x, int(nsamp), int(x_pitch), d_w, d_tmpl,
                                              d_loss, d_gx, d_gw, d_ws, int(ws_bytes), stream),
           "aa_dedisperse_f32_mse_device")
+
+
+AA_DEDISP_DIRECT = 0
+AA_DEDISP_GROUPED = 1
+
+
+def aa_plan_set_strategy(plan, r: int, strategy: int) -> None:
+    check(lib().aa_plan_set_strategy(plan, int(r), int(strategy)), "aa_plan_set_strategy")
 
 
 def aa_plan_autotune(plan, nsamp_probe: int, cache_path=None) -> None:

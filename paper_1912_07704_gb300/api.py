@@ -89,6 +89,11 @@ class Plan:
     def shifts(self, r: int) -> np.ndarray:
         return abi.aa_plan_shifts(self.handle, r, self.ranges[r][2], self.nchans)
 
+    def set_strategy(self, r: int, strategy: int) -> None:
+        """Dedispersion strategy of range r: abi.AA_DEDISP_DIRECT or
+        abi.AA_DEDISP_GROUPED (same result, different grouping of the sums)."""
+        abi.aa_plan_set_strategy(self.handle, r, strategy)
+
     def autotune(self, nsamp_probe: int, cache_path=None):
         """Pick the dedispersion tile shapes of every range by timing them on
         the bound device (see aa_plan_autotune)."""

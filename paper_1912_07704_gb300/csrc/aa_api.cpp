@@ -160,12 +160,7 @@ aa_status aa_dedisperse_device(const aa_plan* p, const uint8_t* d_in, int64_t ns
         a.shifts = g.d_shifts;
         a.out = d_out + L.row_offset[r];
         a.out_pitch = L.pitch[r];
-        a.rw = g.rw;
-        a.cc = g.cc;
-        a.nstage = g.nstage;
-        a.flush = g.flush;
-        a.elem = g.elem;
-        a.smem = g.smem;
+        fill_strategy(a, g);
         a.err = err;
         if (a.length <= 0) continue;
         ProfScope prof(g.elem == 1 ? kKDedispU8 : kKDedispU16, s);

@@ -1,7 +1,8 @@
 // Autotuner for the dedispersion tile: for every range of a bound plan, time
-// the kernel over a synthetic probe input for each feasible stage shape
-// (channels per shared-memory stage x pipeline depth) and keep the fastest.
-// Results can be cached in a text file keyed by the GPU and the range's shape.
+// the kernel over a synthetic probe input for the grouped strategy (when the
+// plan built its tables) and each feasible direct stage shape (channels per
+// shared-memory stage x pipeline depth), and keep the fastest.  Results can
+// be cached in a text file keyed by the GPU and the range's shape.
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
@@ -26,18 +27,28 @@ std::string cache_key(const cudaDeviceProp& prop, const aa_plan& p, const RangeP
     std::string name = prop.name;
     std::replace(name.begin(), name.end(), ' ', '_');
     k << name << ";sm=" << prop.multiProcessorCount << ";C=" << p.nchans << ";dec=" << r.desc.dec
-      << ";rw=" << r.rw << ";ndm=" << std::min(r.desc.ndm, kDmPerBlock * 64);
+      << ";rw=" << r.rw << ";ndm=" << std::min(r.desc.ndm, kDmPerBlock * 64)
+      << ";dmstep=" << r.desc.dm_step << ";dmlo=" << r.desc.dm_lo;
     return k.str();
 }
 
-std::map<std::string, std::pair<int, int>> read_cache(const char* path) {
-    std::map<std::string, std::pair<int, int>> m;
+struct Choice {
+    int strategy, cc, ns;
+};
+
+// Lines: key strategy cc nstage ms
+std::map<std::string, Choice> read_cache(const char* path) {
+    std::map<std::string, Choice> m;
     if (!path) return m;
     std::ifstream f(path);
-    std::string key;
-    int cc, ns;
-    double ms;
-    while (f >> key >> cc >> ns >> ms) m[key] = {cc, ns};
+    std::string line;
+    while (std::getline(f, line)) {
+        std::istringstream in(line);
+        std::string key;
+        Choice c{};
+        double ms;
+        if (in >> key >> c.strategy >> c.cc >> c.ns >> ms) m[key] = c;
+    }
     return m;
 }
 
@@ -85,18 +96,26 @@ extern "C" aa_status aa_plan_autotune(aa_plan* p, int64_t nsamp_probe, const cha
         RangePlan& g = p->ranges[r];
         if (L.length[r] <= 0) continue;
         const std::string key = cache_key(prop, *p, g);
-        int best_cc = g.cc, best_ns = g.nstage;
+        int best_cc = g.cc, best_ns = g.nstage, best_strategy = g.strategy;
         auto hit = cache.find(key);
-        if (hit != cache.end()) {
-            best_cc = hit->second.first;
-            best_ns = hit->second.second;
+        if (hit != cache.end() && (hit->second.strategy == 0 || g.grouped_ok)) {
+            best_strategy = hit->second.strategy;
+            best_cc = hit->second.cc;
+            best_ns = hit->second.ns;
         } else {
             const int max_flush = 65535 / (255 * g.desc.dec);
             float best_ms = 1e30f;
-            for (int ns : {2, 3}) {
-                for (int cc : {8, 12, 16, 20, 24, 32}) {
-                    if (cc > max_flush || kDmPerBlock * cc > kDedispThreads) continue;
-                    const size_t smem = dedisp_smem_bytes(g, cc, ns);
+            // candidate list: the grouped strategy first (cc = 0), then the direct shapes
+            std::vector<std::pair<int, int>> shapes;
+            if (g.grouped_ok) shapes.push_back({0, 0});
+            for (int ns : {2, 3})
+                for (int cc : {8, 12, 16, 20, 24, 32}) shapes.push_back({cc, ns});
+            for (const auto& shape : shapes) {
+                {
+                    const int cc = shape.first, ns = shape.second;
+                    const bool grouped = cc == 0;
+                    if (!grouped && (cc > max_flush || kDmPerBlock * cc > kDedispThreads)) continue;
+                    const size_t smem = grouped ? g.gsmem : dedisp_smem_bytes(g, cc, ns);
                     if (smem > 227 * 1024) continue;
                     DedispArgs a{};
                     a.in = probe;
@@ -108,12 +127,16 @@ extern "C" aa_status aa_plan_autotune(aa_plan* p, int64_t nsamp_probe, const cha
                     a.shifts = g.d_shifts;
                     a.out = static_cast<float*>(out);
                     a.out_pitch = L.pitch[r];
-                    a.rw = g.rw;
-                    a.cc = cc;
-                    a.nstage = ns;
-                    a.flush = (std::min(max_flush, 256) / cc) * cc;
-                    a.elem = g.elem;
-                    a.smem = smem;
+                    const int saved = g.strategy;
+                    g.strategy = grouped ? 1 : 0;
+                    fill_strategy(a, g);
+                    g.strategy = saved;
+                    if (!grouped) {
+                        a.cc = cc;
+                        a.nstage = ns;
+                        a.flush = (std::min(max_flush, 256) / cc) * cc;
+                        a.smem = smem;
+                    }
                     a.err = err;
                     if (launch_dedisperse(a, nullptr) != cudaSuccess) { cudaGetLastError(); continue; }
                     cudaEventRecord(e0);
@@ -124,15 +147,19 @@ extern "C" aa_status aa_plan_autotune(aa_plan* p, int64_t nsamp_probe, const cha
                     cudaEventElapsedTime(&ms, e0, e1);
                     if (ms < best_ms) {
                         best_ms = ms;
-                        best_cc = cc;
-                        best_ns = ns;
+                        best_strategy = grouped ? 1 : 0;
+                        if (!grouped) {
+                            best_cc = cc;
+                            best_ns = ns;
+                        }
                     }
                 }
             }
             std::ostringstream line;
-            line << key << " " << best_cc << " " << best_ns << " " << best_ms / 3;
+            line << key << " " << best_strategy << " " << best_cc << " " << best_ns << " " << best_ms / 3;
             new_lines.push_back(line.str());
         }
+        g.strategy = best_strategy;
         g.cc = best_cc;
         g.nstage = best_ns;
         g.flush = (std::min(65535 / (255 * g.desc.dec), 256) / best_cc) * best_cc;

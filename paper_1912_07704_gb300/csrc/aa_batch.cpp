@@ -31,24 +31,25 @@ struct WaveTables {
     // host copies (uploaded into the arena)
     std::vector<DecimateJob> dec_jobs[4];  // one launch per cascade level
     std::vector<int64_t> dec_first[4];
-    std::vector<DedispArgs> dd;
-    std::vector<int64_t> dd_first;
-    std::vector<int> dd_ndmb;
+    // one persistent launch per kernel variant: [grouped * 2 + (16-bit input)]
+    std::vector<DedispArgs> dd[4];
+    std::vector<int64_t> dd_first[4];
+    std::vector<int> dd_ndmb[4];
     std::vector<SpsArgs> sps;
     std::vector<int64_t> st_first, bx_first;
     std::vector<int> bx_ntiles;
     // device copies
     DecimateJob* d_dec_jobs[4] = {};
     int64_t* d_dec_first[4] = {};
-    DedispArgs* d_dd = nullptr;
-    int64_t* d_dd_first = nullptr;
-    int* d_dd_ndmb = nullptr;
+    DedispArgs* d_dd[4] = {};
+    int64_t* d_dd_first[4] = {};
+    int* d_dd_ndmb[4] = {};
     SpsArgs* d_sps = nullptr;
     int64_t* d_st_first = nullptr;
     int64_t* d_bx_first = nullptr;
     int* d_bx_ntiles = nullptr;
-    unsigned long long* d_queues = nullptr;  // 3 counters
-    size_t dd_smem = 0;
+    unsigned long long* d_queues = nullptr;  // 6 counters: 4 dedispersion variants, stats, boxcar
+    size_t dd_smem[4] = {0, 0, 0, 0};
 };
 
 }  // namespace
@@ -169,16 +170,16 @@ aa_status aa_batch_create(aa_plan* const* plans, const int64_t* nsamps, int32_t 
     b->waves.push_back(w);
     wave_bytes = std::max(wave_bytes, cur);
 
-    // descriptor tables: 16 arrays per wave, each padded to 256 bytes
-    constexpr int64_t kArraysPerWave = 16;
+    // descriptor tables: 25 arrays per wave, each padded to 256 bytes
+    constexpr int64_t kArraysPerWave = 25;
     size_t table_bytes = 0;
     for (auto& wv : b->waves) {
         int64_t nr = 0;
         for (int i : wv) nr += (int64_t)plans[i]->ranges.size();
         table_bytes += (size_t)(kArraysPerWave * 256 +
-                                round_up(nr * (int64_t)sizeof(DedispArgs), 256) +
+                                4 * round_up(nr * (int64_t)sizeof(DedispArgs), 256) +
                                 round_up(nr * (int64_t)sizeof(SpsArgs), 256) +
-                                3 * round_up((nr + 1) * 8, 256) + 2 * round_up(nr * 4, 256) +
+                                6 * round_up((nr + 1) * 8, 256) + 5 * round_up(nr * 4, 256) +
                                 4 * round_up(nr * (int64_t)sizeof(DecimateJob), 256) +
                                 4 * round_up((nr + 1) * 8, 256));
     }
@@ -211,11 +212,10 @@ aa_status aa_batch_create(aa_plan* const* plans, const int64_t* nsamps, int32_t 
 
     // per-wave descriptors
     b->tables.resize(b->waves.size());
-    size_t dd_smem_max = 0;
     for (size_t wi = 0; wi < b->waves.size(); ++wi) {
         WaveTables& T = b->tables[wi];
         char* q = wave_area;
-        T.dd_first.push_back(0);
+        for (int v = 0; v < 4; ++v) T.dd_first[v].push_back(0);
         T.st_first.push_back(0);
         T.bx_first.push_back(0);
         for (int lv = 0; lv < 4; ++lv) T.dec_first[lv].push_back(0);
@@ -279,19 +279,15 @@ aa_status aa_batch_create(aa_plan* const* plans, const int64_t* nsamps, int32_t 
                 a.shifts = g.d_shifts;
                 a.out = dd + L.row_offset[r];
                 a.out_pitch = L.pitch[r];
-                a.rw = g.rw;
-                a.cc = g.cc;
-                a.nstage = g.nstage;
-                a.flush = g.flush;
-                a.elem = g.elem;
-                a.smem = g.smem;
+                fill_strategy(a, g);
                 a.err = b->d_err;
-                dd_smem_max = std::max(dd_smem_max, g.smem);
+                const int sg = (a.grouped ? 2 : 0) + (a.elem == 2 ? 1 : 0);
+                T.dd_smem[sg] = std::max(T.dd_smem[sg], a.smem);
                 const int ndmb = (a.ndm + kDmPerBlock - 1) / kDmPerBlock;
                 const int64_t ntiles = (a.length + kTau - 1) / kTau;
-                T.dd.push_back(a);
-                T.dd_ndmb.push_back(ndmb);
-                T.dd_first.push_back(T.dd_first.back() + (int64_t)ndmb * ntiles);
+                T.dd[sg].push_back(a);
+                T.dd_ndmb[sg].push_back(ndmb);
+                T.dd_first[sg].push_back(T.dd_first[sg].back() + (int64_t)ndmb * ntiles);
                 SpsArgs s{};
                 s.dd = dd + L.row_offset[r];
                 s.pitch = L.pitch[r];
@@ -323,7 +319,6 @@ aa_status aa_batch_create(aa_plan* const* plans, const int64_t* nsamps, int32_t 
                 T.bx_first.push_back(T.bx_first.back() + (int64_t)nt * s.nrows);
             }
         }
-        T.dd_smem = dd_smem_max;
         // upload tables
         bool overflow = false;
         auto put = [&](const void* src, size_t bytes) {
@@ -340,9 +335,11 @@ aa_status aa_batch_create(aa_plan* const* plans, const int64_t* nsamps, int32_t 
             T.d_dec_jobs[lv] = reinterpret_cast<DecimateJob*>(put(T.dec_jobs[lv].data(), T.dec_jobs[lv].size() * sizeof(DecimateJob)));
             T.d_dec_first[lv] = reinterpret_cast<int64_t*>(put(T.dec_first[lv].data(), T.dec_first[lv].size() * 8));
         }
-        T.d_dd = reinterpret_cast<DedispArgs*>(put(T.dd.data(), T.dd.size() * sizeof(DedispArgs)));
-        T.d_dd_first = reinterpret_cast<int64_t*>(put(T.dd_first.data(), T.dd_first.size() * 8));
-        T.d_dd_ndmb = reinterpret_cast<int*>(put(T.dd_ndmb.data(), T.dd_ndmb.size() * 4));
+        for (int sg = 0; sg < 4; ++sg) {
+            T.d_dd[sg] = reinterpret_cast<DedispArgs*>(put(T.dd[sg].data(), T.dd[sg].size() * sizeof(DedispArgs)));
+            T.d_dd_first[sg] = reinterpret_cast<int64_t*>(put(T.dd_first[sg].data(), T.dd_first[sg].size() * 8));
+            T.d_dd_ndmb[sg] = reinterpret_cast<int*>(put(T.dd_ndmb[sg].data(), T.dd_ndmb[sg].size() * 4));
+        }
         T.d_sps = reinterpret_cast<SpsArgs*>(put(T.sps.data(), T.sps.size() * sizeof(SpsArgs)));
         T.d_st_first = reinterpret_cast<int64_t*>(put(T.st_first.data(), T.st_first.size() * 8));
         T.d_bx_first = reinterpret_cast<int64_t*>(put(T.bx_first.data(), T.bx_first.size() * 8));
@@ -374,16 +371,17 @@ aa_status aa_batch_create(aa_plan* const* plans, const int64_t* nsamps, int32_t 
         cudaMemsetAsync(b->d_err, 0, 4, cs);
         launch_rsqrt_table(b->d_rsw, b->wpad, cs);
         for (auto& T : b->tables) {
-            cudaMemsetAsync(T.d_queues, 0, 3 * sizeof(unsigned long long), cs);
+            cudaMemsetAsync(T.d_queues, 0, 6 * sizeof(unsigned long long), cs);
             for (int lv = 0; lv < 4; ++lv)
                 launch_decimate_batch(T.d_dec_jobs[lv], T.d_dec_first[lv], (int)T.dec_jobs[lv].size(),
                                       b->grid_dec, cs);
-            launch_dedisperse_batch(T.d_dd, T.d_dd_first, T.d_dd_ndmb, (int)T.dd.size(), T.dd_smem,
-                                    &T.d_queues[0], b->grid_dd, cs);
-            launch_sps_stats_batch(T.d_sps, T.d_st_first, (int)T.sps.size(), &T.d_queues[1],
+            for (int sg = 0; sg < 4; ++sg)
+                launch_dedisperse_batch(T.d_dd[sg], T.d_dd_first[sg], T.d_dd_ndmb[sg], (int)T.dd[sg].size(),
+                                        T.dd_smem[sg], &T.d_queues[sg], b->grid_dd, sg >= 2, (sg & 1) + 1, cs);
+            launch_sps_stats_batch(T.d_sps, T.d_st_first, (int)T.sps.size(), &T.d_queues[4],
                                    b->grid_st, cs);
             launch_sps_boxcar_batch(T.d_sps, T.d_bx_first, T.d_bx_ntiles, (int)T.sps.size(), b->wpad,
-                                    &T.d_queues[2], b->grid_bx, cs);
+                                    &T.d_queues[5], b->grid_bx, cs);
         }
         e = cudaStreamEndCapture(cs, &b->graph);
     }

@@ -75,6 +75,7 @@ __device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32
 }
 
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s per stage: far beyond any real copy
+constexpr int kMaxStages = 4;                      // staging ring depth limit (mbarriers per CTA)
 
 // SPW = samples per 32-bit word: 4 for raw uint8 input, 2 for decimated uint16.
 // acc + x through the FMA pipe (integer multiply-add by a runtime 1): the byte
@@ -84,6 +85,21 @@ __device__ __forceinline__ uint32_t mad_add(uint32_t x, uint32_t one, uint32_t a
     asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(x), "r"(one), "r"(acc));
     return d;
 }
+
+// 16-byte asynchronous global -> shared copy (L2 only); completion tracked by
+// cp_async_mbar_arrive.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+// Arrive on the mbarrier once this thread's earlier cp.async copies have landed
+// (the barrier's expected count includes this arrival).
+__device__ __forceinline__ void cp_async_mbar_arrive(uint64_t* bar) {
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ void cp_async16_s(uint32_t dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 __device__ __forceinline__ void mbar_inval(uint64_t* bar) {
     asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
@@ -95,7 +111,8 @@ __device__ __forceinline__ void mbar_inval(uint64_t* bar) {
 template <int SPW>
 __device__ __forceinline__ void dedisperse_block(const DedispArgs& a, int ndm_blocks, int64_t bid,
                                                  uint64_t wait_limit_ns, int fault_skip_chunk,
-                                                 uint32_t one, unsigned char* smem, bool reinit) {
+                                                 uint32_t one, unsigned char* smem, uint64_t* bars,
+                                                 bool reinit) {
     constexpr int QW = kTau / (32 * SPW);  // words per lane per DM trial
     constexpr int NCOPY = SPW;             // shifted copies of each staged row
     constexpr int EB = 4 / SPW;            // bytes per sample
@@ -107,8 +124,6 @@ __device__ __forceinline__ void dedisperse_block(const DedispArgs& a, int ndm_bl
     uint32_t* stages = reinterpret_cast<uint32_t*>(smem);
     int* offs = reinterpret_cast<int*>(stages + nstage * stage_w);  // [nstage][16][cc]
     int* bases = offs + nstage * kDmPerBlock * cc;                   // [nstage][cc]
-    uint64_t* bars = reinterpret_cast<uint64_t*>(
-        (reinterpret_cast<uintptr_t>(bases + nstage * cc) + 15) & ~uintptr_t(15));
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int dmb = (int)(bid % ndm_blocks);
@@ -121,10 +136,10 @@ __device__ __forceinline__ void dedisperse_block(const DedispArgs& a, int ndm_bl
     const unsigned char* in_b = static_cast<const unsigned char*>(a.in);
     const int64_t pitch_b = a.in_pitch * EB;
 
-    if (tid == 0) {
-        for (int s = 0; s < nstage; ++s) {
-            if (reinit) mbar_inval(&bars[s]);
-            mbar_init(&bars[s], 1);
+    if (tid == 0) {  // every barrier of the fixed array, whatever the previous item used
+        for (int st = 0; st < kMaxStages; ++st) {
+            if (reinit) mbar_inval(&bars[st]);
+            mbar_init(&bars[st], 1);
         }
         mbar_fence_init();
     }
@@ -344,13 +359,298 @@ __device__ __forceinline__ void dedisperse_block(const DedispArgs& a, int ndm_bl
     }
 }
 
+// Grouped strategy (see GroupRec in aa_internal.h).  CTA = 16 DM trials x
+// kGroupTau output samples.  Channel chunks of a.cc rows stream through a
+// two-stage ring filled by 16-byte cp.async copies that every warp issues
+// (one small bulk copy per row would make the bulk-copy request rate the
+// limit); the raw rows are staged in the order of the chunk's member list, so
+// group g's members are rows [mstart, mstart + mcount).  The groups of a chunk are processed in batches
+// of at most a.gz:
+//   phase 1: z_g[u] = sum of the group's staged rows at u, u < kGroupTau +
+//            span_g, as packed 16-bit pairs, stored twice: copy A word j =
+//            (z[2j], z[2j+1]) and copy B word j = (z[2j+1], z[2j+2]);
+//            work unit = (group, 256 consecutive u), one warp per unit;
+//   phase 2: warp w (trial d0 + w) adds z_g[t + delta_g(w)] for its 16
+//            samples t: copy (delta & 1), word offset delta >> 1, aligned.
+// 16-bit lanes never overflow: a chunk holds at most 65535 / (255 dec)
+// channels, and trial accumulators are flushed every a.gflush chunks.
+template <int EB>
+__device__ __forceinline__ void dedisperse_grouped_block(const DedispArgs& a, int ndm_blocks,
+                                                         int64_t bid, uint64_t wait_limit_ns,
+                                                         int fault_skip_chunk, unsigned char* smem,
+                                                         uint64_t* bars, bool reinit) {
+    constexpr int T = kGroupTau;
+    constexpr int QW = T / 64;  // packed words (2 samples) per lane per trial
+    const int gcc = a.cc, grwx = a.grwx, gz = a.gz, gzw = a.gzw;
+    constexpr int NST = 2;
+    unsigned char* xst = smem;  // [NST][gcc][grwx] staged rows (member order)
+    uint32_t* zs = reinterpret_cast<uint32_t*>(xst + (size_t)NST * gcc * grwx);  // [gz][2][gzw]
+    // per-member staging records, 3-deep ring by chunk: (phase-1 word << 5 | shift,
+    // bytes to copy, global byte offset lo, hi)
+    int4* meta = reinterpret_cast<int4*>(zs + (size_t)gz * 2 * gzw);  // [3][gcc]
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int dmb = (int)(bid % ndm_blocks);
+    const int64_t tile = bid / ndm_blocks;
+    const int d0 = dmb * kDmPerBlock;
+    const int dlast = min(a.ndm, d0 + kDmPerBlock) - 1;
+    const int64_t t0 = tile * T;
+    const int C = a.nchans;
+    const int nchunks = (C + gcc - 1) / gcc;
+    const unsigned char* in_b = static_cast<const unsigned char*>(a.in);
+    const int64_t pitch_b = a.in_pitch * EB;
+    const GroupRec* recs = a.grec + (size_t)dmb * nchunks;
+    const GroupMember* mems = a.gmem + (size_t)dmb * nchunks * gcc;
+
+    if (tid == 0) {  // every barrier of the fixed array, whatever the previous item used
+        for (int st = 0; st < kMaxStages; ++st) {
+            if (reinit) mbar_inval(&bars[st]);
+            mbar_init(&bars[st], kDedispThreads);  // one cp.async arrival per thread
+        }
+        mbar_fence_init();
+    }
+
+    // Producer (warp 0): stage chunk k; lane l handles members l and l + 32.
+    // Member m of the chunk is channel k*gcc + ch[m]; its row holds the bytes
+    // from the 16-byte boundary below sample t0 + s0 up to the last sample its
+    // group reads (+ the words phase 1 over-reads).  The members' records are
+    // loaded one issue ahead (pre), so issuing waits on no global load.
+    int2 pre[2] = {make_int2(0, 0), make_int2(0, 0)};  // (s0, ch | span << 16)
+    auto prefetch = [&](int k) {
+        if (k >= nchunks) return;
+        const int nch = min(gcc, C - k * gcc);
+        const int2* mem = reinterpret_cast<const int2*>(mems + (size_t)k * gcc);
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+            if (lane + 32 * h < nch) pre[h] = __ldg(mem + lane + 32 * h);
+    };
+    // warp 0: staging records of chunk j from the prefetched member records
+    auto make_meta = [&](int j) {
+        if (j >= nchunks) return;
+        const int st = j % NST;
+        const int c0 = j * gcc;
+        const int nch = min(gcc, C - c0);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int m = lane + 32 * h;
+            if (m < nch) {
+                const int s0 = pre[h].x;
+                const int c = c0 + (pre[h].y & 0xffff), span = (int)((uint32_t)pre[h].y >> 16);
+                const int64_t start = (int64_t)EB * (t0 + s0);
+                const int64_t base = start & ~int64_t(15);
+                const int o = (int)(start - base);
+                int64_t nb = ((int64_t)o + (int64_t)EB * (T + span) + 12 + 15) / 16 * 16;
+                nb = min(nb, (int64_t)grwx);
+                nb = min(nb, pitch_b - base);
+                const int64_t src = (int64_t)c * pitch_b + base;
+                const int word = (int)(((size_t)(st * gcc + m) * grwx + o) >> 2);
+                meta[(j % 3) * gcc + m] = make_int4((word << 5) | ((o & 3) * 8), nb > 0 ? (int)nb : 0,
+                                                   (int)(uint32_t)src, (int)(src >> 32));
+            }
+        }
+        prefetch(j + 1);
+    };
+    // every thread: copy chunk j into stage j % NST (warp w: rows w, w + 16, ..),
+    // then arrive on the stage's barrier when its copies have landed
+    auto issue = [&](int j) {
+        if (j == fault_skip_chunk) return;  // fault injection: this stage never completes
+        const int st = j % NST;
+        const int nch = min(gcc, C - j * gcc);
+        const uint32_t xs = smem_addr(xst) + 16 * lane;
+        const int4* mj = meta + (j % 3) * gcc;
+        for (int m = warp; m < nch; m += kDedispWarps) {
+            const int4 md = mj[m];
+            const unsigned char* src = in_b + (((int64_t)md.w << 32) | (uint32_t)md.z) + 16 * lane;
+            const uint32_t dst = xs + (uint32_t)((st * gcc + m) * grwx);
+            for (int q = 16 * lane; q < md.y; q += 16 * 32)
+                cp_async16_s(dst + (q - 16 * lane), src + (q - 16 * lane));
+        }
+        cp_async_mbar_arrive(&bars[st]);
+    };
+
+    if (warp == 0) {
+        prefetch(0);
+        for (int j = 0; j <= NST && j < nchunks; ++j) make_meta(j);  // chunks 0 .. NST
+    }
+    __syncthreads();  // barriers initialised, first records written
+    for (int j = 0; j < min(NST, nchunks); ++j) issue(j);
+    int next_issue = min(NST, nchunks);
+
+    uint32_t acc[QW];
+    uint32_t tot[2 * QW];
+#pragma unroll
+    for (int q = 0; q < QW; ++q) {
+        acc[q] = 0;
+        tot[2 * q] = tot[2 * q + 1] = 0;
+    }
+    const bool has_trial = d0 + warp <= dlast;
+    int since_flush = 0;
+    const uint32_t* xw = reinterpret_cast<const uint32_t*>(xst);
+
+    const int nj = a.gnj;                        // 256-sample units per group sum
+    const int gstep = kDedispWarps / nj, jstep = kDedispWarps - gstep * nj;
+    const int gi0 = warp / nj, j0 = warp - gi0 * nj;  // this warp's first unit
+    GroupRec rec_next = recs[0];  // record of the next chunk, loaded one chunk ahead
+    for (int k = 0; k < nchunks; ++k) {
+        const int st = k % NST;
+        const uint32_t parity = (uint32_t)(k / NST) & 1u;
+        const GroupRec rec = rec_next;
+        if (k + 1 < nchunks) rec_next = recs[k + 1];
+        const GroupDesc* gd = a.gdesc + rec.first;
+        const int G = rec.ngroups;
+        // group fields of a batch, one group per lane (the first batch's are
+        // loaded before the wait): members (start | count << 16), span, and this
+        // warp's phase-2 word offset of the group sum at its trial's delay
+        uint32_t g_ms = 0, g_span = 0;
+        int g_p2 = 0;
+        auto load_batch = [&](int gb0) {
+            const int gl = gb0 + lane;
+            if (gl < min(G, gb0 + gz)) {
+                g_ms = (uint32_t)gd[gl].mstart | ((uint32_t)gd[gl].mcount << 16);
+                g_span = gd[gl].span;
+                const int dl = gd[gl].delta[warp];
+                g_p2 = (lane * 2 + (dl & 1)) * gzw + (dl >> 1);
+            }
+        };
+        load_batch(0);
+        const bool ok = mbar_wait_bounded(&bars[st], parity, wait_limit_ns);
+        for (int gb = 0; gb < G; gb += gz) {
+            const int ge = min(G, gb + gz);
+            if (gb > 0) load_batch(gb);
+            // ---- phase 1: group sums of this batch.  Unit u = (group gb + u / nj,
+            // samples 256 (u % nj) ..): warp w takes units w, w + 16, ...
+            if (ok) {
+                const int nunits = (ge - gb) * nj;
+                const int4* mk = meta + (k % 3) * gcc;
+                int gi = gi0, j = j0;  // unit u = gi * nj + j, stepped by 16 without dividing
+                for (int u = warp; u < nunits; u += kDedispWarps) {
+                    const uint32_t ms = __shfl_sync(0xffffffffu, g_ms, gi);
+                    const int zlen = T + (int)__shfl_sync(0xffffffffu, g_span, gi);
+                    const int mstart = (int)(ms & 0xffffu), mend = mstart + (int)(ms >> 16);
+                    uint32_t* zA = zs + gi * 2 * gzw;
+                    uint32_t* zB = zA + gzw;
+                    const int idx = 32 * j + lane;  // this lane: samples 8 idx .. 8 idx + 7
+                    // packed pairs (z0,z1) (z2,z3) (z4,z5) (z6,z7) and z8
+                    uint32_t A0 = 0, A1 = 0, A2 = 0, A3 = 0, E = 0;
+                    if (8 * idx < zlen) {
+#pragma unroll 2
+                        for (int m = mstart; m < mend; ++m) {
+                            const int pk = mk[m].x;
+                            const uint32_t sh = (uint32_t)pk & 31u;
+                            if constexpr (EB == 1) {
+                                const uint32_t* w = xw + (pk >> 5) + 2 * idx;
+                                const uint32_t w0 = w[0], w1 = w[1], w2 = w[2];
+                                const uint32_t v0 = __funnelshift_r(w0, w1, sh);
+                                const uint32_t v1 = __funnelshift_r(w1, w2, sh);
+                                A0 += __byte_perm(v0, 0u, 0x4140);
+                                A1 += __byte_perm(v0, 0u, 0x4342);
+                                A2 += __byte_perm(v1, 0u, 0x4140);
+                                A3 += __byte_perm(v1, 0u, 0x4342);
+                                E += (w2 >> sh) & 0xffu;
+                            } else {
+                                const uint32_t* w = xw + (pk >> 5) + 4 * idx;
+                                const uint32_t w0 = w[0], w1 = w[1], w2 = w[2], w3 = w[3], w4 = w[4];
+                                A0 += __funnelshift_r(w0, w1, sh);
+                                A1 += __funnelshift_r(w1, w2, sh);
+                                A2 += __funnelshift_r(w2, w3, sh);
+                                A3 += __funnelshift_r(w3, w4, sh);
+                                E += (w4 >> sh) & 0xffffu;
+                            }
+                        }
+                        *reinterpret_cast<uint4*>(zA + 4 * idx) = make_uint4(A0, A1, A2, A3);
+                        *reinterpret_cast<uint4*>(zB + 4 * idx) =
+                            make_uint4(__byte_perm(A0, A1, 0x5432), __byte_perm(A1, A2, 0x5432),
+                                       __byte_perm(A2, A3, 0x5432), __byte_perm(A3, E, 0x5432));
+                    }
+                    gi += gstep;
+                    j += jstep;
+                    if (j >= nj) {
+                        j -= nj;
+                        ++gi;
+                    }
+                }
+            }
+            const bool last_batch = ge == G;
+            if (gb == 0) {
+                if (!__syncthreads_and(ok)) {
+                    // A stage never arrived: report, drain the copies still in
+                    // flight (bounded), and leave without touching the output.
+                    if (tid == 0) atomicOr(a.err, 1u);
+                    cp_async_wait_all();  // this thread's copies in flight
+                    return;
+                }
+            } else {
+                __syncthreads();
+            }
+            // the staged rows of chunk k are no longer read: refill the stage
+            // with chunk k + 2 and prepare the records of chunk k + 3 (its slot
+            // held chunk k's, no longer read)
+            if (last_batch && next_issue < nchunks) {
+                issue(next_issue);
+                ++next_issue;
+                if (warp == 0) make_meta(next_issue);
+            }
+            // ---- phase 2: every trial adds every group sum at its relative delay
+            if (has_trial) {
+                const uint32_t* zl = zs + lane;
+#pragma unroll 2
+                for (int g = 0; g < ge - gb; ++g) {
+                    const uint32_t* src = zl + __shfl_sync(0xffffffffu, g_p2, g);
+#pragma unroll
+                    for (int q = 0; q < QW; ++q) acc[q] += src[32 * q];
+                }
+            }
+            // the next batch (or chunk) overwrites the group sums
+            if (!(last_batch && k + 1 == nchunks)) __syncthreads();
+        }
+        if (++since_flush >= a.gflush) {
+#pragma unroll
+            for (int q = 0; q < QW; ++q) {
+                tot[2 * q] += acc[q] & 0xffffu;
+                tot[2 * q + 1] += acc[q] >> 16;
+                acc[q] = 0;
+            }
+            since_flush = 0;
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < QW; ++q) {
+        tot[2 * q] += acc[q] & 0xffffu;
+        tot[2 * q + 1] += acc[q] >> 16;
+    }
+
+    // epilogue: exact integer totals -> FP32 rows
+    if (!has_trial) return;
+    float* row = a.out + (int64_t)(d0 + warp) * a.out_pitch;
+#pragma unroll
+    for (int q = 0; q < QW; ++q) {
+        const int64_t t = t0 + 2 * (lane + 32 * q);
+        if (t + 2 <= a.length) {
+            *reinterpret_cast<float2*>(row + t) = make_float2((float)tot[2 * q], (float)tot[2 * q + 1]);
+        } else if (t < a.length) {
+            row[t] = (float)tot[2 * q];
+        }
+    }
+}
+
+template <int EB>
+__global__ void __launch_bounds__(kDedispThreads, 2)
+    dedisperse_grouped_kernel(DedispArgs a, int ndm_blocks, uint64_t wait_limit_ns,
+                              int fault_skip_chunk) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ uint64_t bars[kMaxStages];
+    dedisperse_grouped_block<EB>(a, ndm_blocks, blockIdx.x, wait_limit_ns, fault_skip_chunk, smem,
+                                 bars, false);
+}
+
 template <int SPW>
 __global__ void __launch_bounds__(kDedispThreads, 2)
     dedisperse_kernel(DedispArgs a, int ndm_blocks, uint64_t wait_limit_ns, int fault_skip_chunk,
                       uint32_t one) {
     extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ uint64_t bars[kMaxStages];
     dedisperse_block<SPW>(a, ndm_blocks, blockIdx.x, wait_limit_ns, fault_skip_chunk, one, smem,
-                          false);
+                          bars, false);
 }
 
 // Persistent form over several beams/ranges: CTAs pull work items from a
@@ -365,11 +665,15 @@ __device__ __forceinline__ int find_desc(const int64_t* first, int n, int64_t it
     return lo;
 }
 
+// One instantiation per strategy and input width (every descriptor of a
+// launch uses it).
+template <bool GROUPED, int EB>
 __global__ void __launch_bounds__(kDedispThreads, 2)
     dedisperse_batch_kernel(const DedispArgs* __restrict__ descs, const int64_t* __restrict__ first,
                             const int* __restrict__ ndm_blocks, int ndesc,
                             unsigned long long* queue, uint64_t wait_limit_ns, uint32_t one) {
     extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ uint64_t bars[kMaxStages];  // fixed place: re-initialised per work item
     __shared__ long long s_item;
     const int64_t total = first[ndesc];
     bool reinit = false;
@@ -381,10 +685,12 @@ __global__ void __launch_bounds__(kDedispThreads, 2)
         if (item >= total) break;
         const int k = find_desc(first, ndesc, item);
         const DedispArgs& a = descs[k];
-        if (a.elem == 1)
-            dedisperse_block<4>(a, ndm_blocks[k], item - first[k], wait_limit_ns, -1, one, smem, reinit);
+        if constexpr (GROUPED)
+            dedisperse_grouped_block<EB>(a, ndm_blocks[k], item - first[k], wait_limit_ns, -1, smem,
+                                         bars, reinit);
         else
-            dedisperse_block<2>(a, ndm_blocks[k], item - first[k], wait_limit_ns, -1, one, smem, reinit);
+            dedisperse_block<4 / EB>(a, ndm_blocks[k], item - first[k], wait_limit_ns, -1, one, smem,
+                                     bars, reinit);
         reinit = true;
     }
 }
@@ -452,13 +758,15 @@ uint64_t g_wait_limit_ns = kWaitLimitNs;
 
 cudaError_t launch_dedisperse_batch(const DedispArgs* d_descs, const int64_t* d_first,
                                     const int* d_ndm_blocks, int ndesc, size_t smem,
-                                    unsigned long long* d_queue, int grid, cudaStream_t s) {
+                                    unsigned long long* d_queue, int grid, bool grouped, int elem,
+                                    cudaStream_t s) {
     if (ndesc <= 0) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(dedisperse_batch_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    auto kern = grouped ? (elem == 1 ? dedisperse_batch_kernel<true, 1> : dedisperse_batch_kernel<true, 2>)
+                        : (elem == 1 ? dedisperse_batch_kernel<false, 1> : dedisperse_batch_kernel<false, 2>);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    dedisperse_batch_kernel<<<grid, kDedispThreads, smem, s>>>(d_descs, d_first, d_ndm_blocks, ndesc,
-                                                               d_queue, g_wait_limit_ns, 1u);
+    kern<<<grid, kDedispThreads, smem, s>>>(d_descs, d_first, d_ndm_blocks, ndesc, d_queue,
+                                            g_wait_limit_ns, 1u);
     return cudaGetLastError();
 }
 
@@ -472,10 +780,18 @@ cudaError_t launch_decimate_batch(const DecimateJob* d_jobs, const int64_t* d_fi
 
 cudaError_t launch_dedisperse(const DedispArgs& a, cudaStream_t s) {
     if (a.length <= 0 || a.ndm <= 0) return cudaSuccess;
+    if (a.nstage < 1 || a.nstage > kMaxStages) return cudaErrorInvalidValue;
     const int ndmb = (a.ndm + kDmPerBlock - 1) / kDmPerBlock;
     const int64_t ntiles = (a.length + kTau - 1) / kTau;
     const int64_t nblocks = (int64_t)ndmb * ntiles;
     if (nblocks >= (1ll << 31)) return cudaErrorInvalidConfiguration;
+    if (a.grouped) {
+        auto kern = a.elem == 1 ? dedisperse_grouped_kernel<1> : dedisperse_grouped_kernel<2>;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)a.smem);
+        if (e != cudaSuccess) return e;
+        kern<<<(unsigned)nblocks, kDedispThreads, a.smem, s>>>(a, ndmb, g_wait_limit_ns, g_fault_skip_chunk);
+        return cudaGetLastError();
+    }
     auto kern = a.elem == 1 ? dedisperse_kernel<4> : dedisperse_kernel<2>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)a.smem);
     if (e != cudaSuccess) return e;

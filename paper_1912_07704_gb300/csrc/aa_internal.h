@@ -29,6 +29,35 @@ constexpr int kSpsSlots = 16;
 constexpr int kSpsTile = kSpsThreads * kSpsSlots;  // start times per CTA incl. 2 halo
 constexpr int kSpsOwned = kSpsTile - 2;              // start times owned per CTA
 
+// Grouped strategy.  Within one (DM block, channel chunk), channels whose
+// delays at every trial of the block exceed their delay at the block's first
+// trial by the same amounts (the same "delay pattern") are summed once, into a
+// group sum z_g[u] = sum_{c in g} x[c][t0 + s(c,d0) + u]; trial d of the block
+// then adds z_g[t + delta_g(d)] once per group instead of once per channel.
+// Integer sums regrouped: the result is bit-identical.
+constexpr int kGroupTau = 512;  // output samples per CTA (grouped strategy)
+
+struct GroupRec {       // one (DM block, channel chunk)
+    uint32_t first;     // index of its first GroupDesc
+    uint16_t ngroups;
+    uint16_t nch;       // channels in the chunk
+};
+struct GroupDesc {
+    uint16_t mstart;    // first member in the record's member list
+    uint16_t mcount;
+    uint16_t span;      // largest relative delay (delta at the block's last trial)
+    uint16_t pad;
+    uint16_t delta[kDmPerBlock];  // relative delay at each trial of the block
+};
+struct GroupMember {   // member m of a (DM block, channel chunk), in group order
+    int32_t s0;        // its delay at the block's first trial
+    uint16_t ch;       // channel within the chunk
+    uint16_t span;     // its delay at the block's last trial minus s0
+};
+static_assert(sizeof(GroupRec) == 8 && sizeof(GroupDesc) == 40 && sizeof(GroupMember) == 8,
+              "group table layout");
+static_assert(kGroupTau == kTau, "both strategies tile time alike (launch and queue sizing)");
+
 // Per-range strategy, derived once at plan creation (immutable afterwards).
 struct RangePlan {
     aa_dm_range desc{};
@@ -47,6 +76,23 @@ struct RangePlan {
     int f32_span = 0;      // differentiable form: delay spread over any 16 consecutive trials
     int f32_cspan = 0;     // ... and over any 16 consecutive channels
     int32_t* d_shifts = nullptr;  // device copy (inside the plan's table block)
+    // grouped strategy (aa_dedisp_strategy AA_DEDISP_GROUPED)
+    int strategy = 0;      // 0 direct, 1 grouped
+    bool grouped_ok = false;  // the grouped tables exist (spans fit)
+    int gcc = 0;           // channels per chunk
+    int gz = 0;            // group sums held in shared memory at once
+    int grwx = 0;          // bytes per staged channel row
+    int gzw = 0;           // 32-bit words per group-sum copy
+    int gflush = 1;        // chunks between SWAR flushes
+    int gnj = 3;           // 256-sample blocks covering kGroupTau + span_max
+    size_t gsmem = 0;      // dynamic shared memory per CTA
+    double gwork = 1.0;    // (group adds + pre-sum adds) / direct adds
+    std::vector<GroupRec> grec;    // [ndm blocks][chunks]
+    std::vector<GroupDesc> gdesc;
+    std::vector<GroupMember> gmem; // [ndm blocks][chunks][gcc] members in group order
+    GroupRec* d_grec = nullptr;
+    GroupDesc* d_gdesc = nullptr;
+    GroupMember* d_gmem = nullptr;
 };
 
 }  // namespace aa
@@ -154,7 +200,15 @@ struct DedispArgs {
     int rw, cc, nstage, flush, elem;
     size_t smem;
     unsigned* err;
+    // grouped strategy (used when grouped != 0; cc/nstage/smem then describe it)
+    int grouped;
+    int gz, grwx, gzw, gflush, gnj;  // gnj: 256-sample blocks of the longest group sum
+    const GroupRec* grec;
+    const GroupDesc* gdesc;
+    const GroupMember* gmem;
 };
+// Strategy fields of a range's kernel arguments.
+void fill_strategy(DedispArgs& a, const RangePlan& r);
 cudaError_t launch_dedisperse(const DedispArgs& a, cudaStream_t s);
 
 cudaError_t launch_decimate(const void* in, int in_elem, int64_t in_pitch, int32_t nchans,
@@ -175,7 +229,8 @@ struct DecimateJob {
 // (ndesc + 1 entries, device), queue a device counter cleared beforehand.
 cudaError_t launch_dedisperse_batch(const DedispArgs* d_descs, const int64_t* d_first,
                                     const int* d_ndm_blocks, int ndesc, size_t smem,
-                                    unsigned long long* d_queue, int grid, cudaStream_t s);
+                                    unsigned long long* d_queue, int grid, bool grouped, int elem,
+                                    cudaStream_t s);
 cudaError_t launch_decimate_batch(const DecimateJob* d_jobs, const int64_t* d_first, int njobs,
                                   int grid, cudaStream_t s);
 

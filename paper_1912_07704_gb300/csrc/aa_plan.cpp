@@ -50,6 +50,126 @@ static size_t dedisp_smem(const RangePlan& r, int cc, int nstage) {
 
 size_t dedisp_smem_bytes(const RangePlan& r, int cc, int nstage) { return dedisp_smem(r, cc, nstage); }
 
+// Shared memory of the grouped strategy: staged rows, group sums (two
+// copies each), a 3-deep ring of 16-byte per-member staging records.
+static size_t grouped_smem(int nstage, int gcc, int grwx, int gz, int gzw) {
+    return (size_t)nstage * gcc * grwx + (size_t)gz * 2 * gzw * 4 + (size_t)3 * gcc * 16;
+}
+
+// Delay-pattern groups of every (DM block, channel chunk) of a range, and the
+// grouped tile shape.  Two CTAs per SM must fit (<= kPairSmem each).
+static void build_groups(RangePlan& r, int C) {
+    constexpr size_t kPairSmem = 113 * 1024 - 512;
+    constexpr int B = kDmPerBlock;
+    r.grouped_ok = false;
+    const int dec = r.desc.dec;
+    const int lane_max = 65535 / (255 * dec);          // channels per 16-bit lane
+    if (r.span_max > 4096) return;
+    // staged row: alignment offset (< 16) + the samples read + the words phase 1
+    // reads past them (8 samples per lane: up to 20 bytes)
+    const int grwx = (int)round_up(15 + (int64_t)r.elem * (kGroupTau + r.span_max) + 20, 16);
+    const int gzw = (int)round_up((kGroupTau + r.span_max + 3) / 2 + 2, 4);
+    const int nstage = 2;
+    // the largest chunk (multiple of 8, <= 64 raw / 32 decimated rows) that
+    // leaves room for at least 8 group sums
+    int gcc = std::min(r.elem == 1 ? 64 : 32, lane_max) / 8 * 8, gz = 0;
+    for (; gcc >= 8; gcc -= 8) {
+        gz = 0;
+        while (grouped_smem(nstage, gcc, grwx, gz + 1, gzw) <= kPairSmem && gz < std::min(gcc, 32)) ++gz;
+        if (gz >= std::min(gcc, 8)) break;
+    }
+    if (gcc < 8) return;
+    const int ndm = r.desc.ndm;
+    const int nblk = (ndm + B - 1) / B, nchk = (C + gcc - 1) / gcc;
+    r.grec.assign((size_t)nblk * nchk, GroupRec{});
+    r.gmem.assign((size_t)nblk * nchk * gcc, GroupMember{});
+    r.gdesc.clear();
+    double direct = 0, grouped = 0;
+    std::vector<GroupDesc> local;
+    std::vector<std::vector<uint8_t>> members;
+    for (int b = 0; b < nblk; ++b) {
+        const int d0 = b * B, nb = std::min(B, ndm - d0);
+        for (int k = 0; k < nchk; ++k) {
+            const int c0 = k * gcc, nch = std::min(gcc, C - c0);
+            local.clear();
+            members.clear();
+            for (int cl = 0; cl < nch; ++cl) {
+                const int c = c0 + cl;
+                GroupDesc g{};
+                const int32_t s0 = r.shifts[(size_t)d0 * C + c];
+                for (int d = 0; d < B; ++d) {
+                    const int dd = d0 + std::min(d, nb - 1);  // pad a partial block with its last trial
+                    g.delta[d] = (uint16_t)(r.shifts[(size_t)dd * C + c] - s0);
+                }
+                g.span = g.delta[B - 1];
+                size_t gi = 0;
+                while (gi < local.size() && std::memcmp(local[gi].delta, g.delta, sizeof g.delta) != 0) ++gi;
+                if (gi == local.size()) {
+                    local.push_back(g);
+                    members.emplace_back();
+                }
+                members[gi].push_back((uint8_t)cl);
+            }
+            GroupRec& rec = r.grec[(size_t)b * nchk + k];
+            rec.first = (uint32_t)r.gdesc.size();
+            rec.ngroups = (uint16_t)local.size();
+            rec.nch = (uint16_t)nch;
+            GroupMember* mem = &r.gmem[((size_t)b * nchk + k) * gcc];
+            int m = 0;
+            for (size_t gi = 0; gi < local.size(); ++gi) {
+                local[gi].mstart = (uint16_t)m;
+                local[gi].mcount = (uint16_t)members[gi].size();
+                for (uint8_t cl : members[gi]) {
+                    const int32_t s0 = r.shifts[(size_t)d0 * C + c0 + cl];
+                    const int32_t s1 = r.shifts[(size_t)(d0 + nb - 1) * C + c0 + cl];
+                    mem[m++] = GroupMember{s0, (uint16_t)cl, (uint16_t)(s1 - s0)};
+                }
+                r.gdesc.push_back(local[gi]);
+            }
+            direct += (double)nch * nb;
+            grouped += (double)nch + (double)local.size() * nb;
+        }
+    }
+    r.gcc = gcc;
+    r.gz = gz;
+    r.grwx = grwx;
+    r.gzw = gzw;
+    r.gflush = std::max(1, lane_max / gcc);
+    r.gnj = (kGroupTau + r.span_max + 255) / 256;
+    r.gsmem = grouped_smem(nstage, gcc, grwx, gz, gzw);
+    r.gwork = direct > 0 ? grouped / direct : 1.0;
+    r.grouped_ok = true;
+}
+
+void fill_strategy(DedispArgs& a, const RangePlan& r) {
+    a.elem = r.elem;
+    a.rw = r.rw;
+    a.flush = r.flush;
+    if (r.strategy == 1) {
+        a.grouped = 1;
+        a.cc = r.gcc;
+        a.nstage = 2;
+        a.smem = r.gsmem;
+        a.gz = r.gz;
+        a.grwx = r.grwx;
+        a.gzw = r.gzw;
+        a.gflush = r.gflush;
+        a.gnj = r.gnj;
+        a.grec = r.d_grec;
+        a.gdesc = r.d_gdesc;
+        a.gmem = r.d_gmem;
+    } else {
+        a.grouped = 0;
+        a.cc = r.cc;
+        a.nstage = r.nstage;
+        a.smem = r.smem;
+        a.gz = a.grwx = a.gzw = a.gflush = a.gnj = 0;
+        a.grec = nullptr;
+        a.gdesc = nullptr;
+        a.gmem = nullptr;
+    }
+}
+
 static aa_status build_strategy(aa_plan& p) {
     for (auto& r : p.ranges) {
         const int dec = r.desc.dec;
@@ -97,6 +217,11 @@ static aa_status build_strategy(aa_plan& p) {
             r.f32_span = sp;
             r.f32_cspan = csp;
         }
+        // Grouped strategy where it removes enough adds: one pre-sum add per
+        // channel plus one add per group and trial, against one add per
+        // channel and trial (measured break-even well above 0.6).
+        build_groups(r, C);
+        r.strategy = (r.grouped_ok && r.gwork <= 0.6) ? 1 : 0;
     }
     // decimation cascade: each decimated buffer is built from the largest
     // already-built decimation that divides it (or from the raw input).
@@ -253,7 +378,12 @@ aa_status aa_plan_create(const aa_plan_desc* d, aa_plan** out) {
     }
     aa_status st = build_strategy(*p);
     if (st != AA_OK) { delete p; return st; }
-    for (auto& r : p->ranges) p->table_bytes += round_up((int64_t)r.shifts.size() * 4, 256);
+    for (auto& r : p->ranges) {
+        p->table_bytes += round_up((int64_t)r.shifts.size() * 4, 256);
+        p->table_bytes += round_up((int64_t)r.grec.size() * sizeof(GroupRec), 256);
+        p->table_bytes += round_up((int64_t)r.gdesc.size() * sizeof(GroupDesc), 256);
+        p->table_bytes += round_up((int64_t)r.gmem.size() * sizeof(GroupMember), 256);
+    }
     *out = p;
     return AA_OK;
 }
@@ -291,15 +421,27 @@ aa_status aa_plan_bind(aa_plan* p, int device) {
         return AA_ERR_NOMEM;
     }
     size_t off = 0;
+    auto upload = [&](const void* src, size_t bytes) -> char* {
+        char* dst = (char*)mem + off;
+        off += round_up((int64_t)bytes, 256);
+        if (bytes && e == cudaSuccess) e = cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice);
+        return dst;
+    };
     for (auto& r : p->ranges) {
-        r.d_shifts = (int32_t*)((char*)mem + off);
-        e = cudaMemcpy(r.d_shifts, r.shifts.data(), r.shifts.size() * 4, cudaMemcpyHostToDevice);
+        r.d_shifts = (int32_t*)upload(r.shifts.data(), r.shifts.size() * 4);
+        r.d_grec = (GroupRec*)upload(r.grec.data(), r.grec.size() * sizeof(GroupRec));
+        r.d_gdesc = (GroupDesc*)upload(r.gdesc.data(), r.gdesc.size() * sizeof(GroupDesc));
+        r.d_gmem = (GroupMember*)upload(r.gmem.data(), r.gmem.size() * sizeof(GroupMember));
         if (e != cudaSuccess) break;
-        off += round_up((int64_t)r.shifts.size() * 4, 256);
     }
     if (e != cudaSuccess) {
         cudaFree(mem);
-        for (auto& r : p->ranges) r.d_shifts = nullptr;
+        for (auto& r : p->ranges) {
+            r.d_shifts = nullptr;
+            r.d_grec = nullptr;
+            r.d_gdesc = nullptr;
+            r.d_gmem = nullptr;
+        }
         if (prev >= 0) cudaSetDevice(prev);
         set_error("delay table upload: %s", cudaGetErrorString(e));
         return AA_ERR_CUDA;
@@ -360,7 +502,32 @@ aa_status aa_plan_range(const aa_plan* p, int64_t nsamp, int32_t r, aa_range_inf
     info->stage_channels = g.cc;
     info->stages = g.nstage;
     info->span_max = g.span_max;
-    info->smem_bytes = (int32_t)g.smem;
+    info->smem_bytes = (int32_t)(g.strategy == 1 ? g.gsmem : g.smem);
+    if (g.strategy == 1) {
+        info->stage_channels = g.gcc;
+        info->stages = 2;
+        info->tile_samples = kGroupTau;
+    }
+    info->strategy = g.strategy;
+    info->grouped_available = g.grouped_ok ? 1 : 0;
+    info->grouped_work = g.gwork;
+    return AA_OK;
+}
+
+aa_status aa_plan_set_strategy(aa_plan* p, int32_t r, int32_t strategy) {
+    clear_error();
+    if (!p) { set_error("plan is NULL"); return AA_ERR_ARG; }
+    if (r < 0 || r >= (int32_t)p->ranges.size()) { set_error("range %d out of bounds", r); return AA_ERR_ARG; }
+    if (strategy != AA_DEDISP_DIRECT && strategy != AA_DEDISP_GROUPED) {
+        set_error("unknown strategy %d", strategy);
+        return AA_ERR_ARG;
+    }
+    RangePlan& g = p->ranges[r];
+    if (strategy == AA_DEDISP_GROUPED && !g.grouped_ok) {
+        set_error("range %d: the grouped strategy is not available (delay span %d)", r, g.span_max);
+        return AA_ERR_CONFIG;
+    }
+    g.strategy = strategy;
     return AA_OK;
 }
 
