@@ -144,6 +144,23 @@ def build_input(plan, w, device):
     return synth.make_filterbank(w, pulses, delays, device=device, pitch=pitch)
 
 
+# DRAM bytes per launch of the dominant kernels, from one ncu capture of the
+# small SKA-like case (2^17 samples, same plan) scaled to the full launch by its
+# output samples (traffic grows in proportion: input and output both scale with
+# the series length).  Each entry names the capture it comes from; set it to None
+# when the kernel changes until it is captured again.
+NCU_TRAFFIC = {
+    ("dedisperse_u8", "grouped"): {
+        "small_read_bytes": 550_991_872, "small_write_bytes": 742_857_984,
+        "small_output_samples": 1500 * 128687,
+        "capture": "profiles/dedisperse_grouped_u8_ska-4096ch-2^17.md"},
+    ("sps_boxcar", "pruned"): {
+        "small_read_bytes": 871_785_216, "small_write_bytes": 43_952_640,
+        "small_output_samples": 1500 * 128687,
+        "capture": "profiles/sps_boxcar_ska-4096ch-2^17.md"},
+}
+
+
 def workload_algorithmics(plan, w):
     from paper_1912_07704_gb300 import abi
     lay = plan.layout(w.nsamp)
@@ -339,11 +356,32 @@ def bench_ours(args):
         kern["sps_boxcar"]["exhaustive_width_samples"] = alg["width_samples"]
         kern["sps_boxcar"]["gws_evaluated_per_s"] = evaluated / box_s / 1e9
     dominant = max(kern, key=lambda k: kern[k]["ms_per_step"])
+
+    def traffic(key):
+        """DRAM bytes per launch of `key` from its ncu capture, scaled to this
+        workload's launches by output samples (None without a matching capture)."""
+        lay = alg["lay"]
+        if key == "sps_boxcar":
+            ent, rows = NCU_TRAFFIC.get(("sps_boxcar", "pruned")), lay
+        else:
+            sel = [r for r, g in enumerate(lay) if (g.dec == 1) == (key == "dedisperse_u8")]
+            strat = {("grouped" if abi.aa_plan_range(plan.handle, nsamp, r).strategy else "direct")
+                     for r in sel}
+            ent = NCU_TRAFFIC.get((key, strat.pop())) if len(strat) == 1 else None
+            rows = [lay[r] for r in sel]
+        if ent is None or not rows:
+            return None, None
+        samples = sum(g.ndm * g.length for g in rows)
+        scale = samples / ent["small_output_samples"]
+        per_launch = (ent["small_read_bytes"] + ent["small_write_bytes"]) * scale / len(rows)
+        return per_launch, f"ncu capture {ent['capture']}, scaled x{scale:.2f} by output samples"
+
     if dominant == "sps_boxcar":
         achieved = BOXCAR_OPS_PER_WS * evaluated / box_s
+        tb, tnote = traffic("sps_boxcar")
         roof = {"kernel": "sps_boxcar", "bound": "alu", "achieved": achieved / 1e9,
                 "peak": lane_peak / 1e9, "unit": "Gop/s", "frac": achieved / lane_peak,
-                "traffic": None,
+                "traffic": tb, "traffic_source": tnote,
                 "ops": f"{BOXCAR_OPS_PER_WS} lane instructions per evaluated width-sample "
                        f"(device-counted; blocks bounded below threshold skipped); peak = "
                        f"{SM_COUNT} SMs x 128 lanes x {sm_max:.0f} MHz"}
@@ -352,9 +390,13 @@ def bench_ours(args):
         s = kern[key]["ms_per_step"] / 1e3
         achieved = alg["adds"].get(key, 0) / s
         executed = alg["executed_adds"].get(key, 0) / s
+        tb, tnote = traffic(key)
+        nl = kern[key]["launches"] / max(args.steps, 1)
+        alg_bytes = sum((w.nchans * g.nsamp_dec * (1 if g.dec == 1 else 2) + 4 * g.ndm * g.length)
+                        for g in alg["lay"] if (g.dec == 1) == (key == "dedisperse_u8")) / max(nl, 1)
         roof = {"kernel": key, "bound": "alu", "achieved": achieved / 1e9,
                 "peak": lane_peak / 1e9, "unit": "Gop/s", "frac": achieved / lane_peak,
-                "traffic": None,
+                "traffic": tb, "traffic_source": tnote, "algorithmic_bytes_per_launch": alg_bytes,
                 "executed_gops": executed / 1e9, "executed_frac": executed / lane_peak,
                 "ops": "algorithmic channel-adds (sum over trials of nchans x L) per second; "
                        "executed_* counts the adds the chosen strategy performs (grouped: "
