@@ -621,13 +621,45 @@ def bench_stream(args):
     print(json.dumps(line), flush=True)
 
 
+def bench_cornerturn(args):
+    """Corner turn of a time-major 4096-channel x 2^20-sample block (the
+    filterbank-file input path) into channel-major rows: HBM-bound, one byte
+    read and one written per sample."""
+    import torch
+    from paper_1912_07704_gb300 import abi
+    C, T = 4096, 1 << 20
+    tm = torch.randint(0, 256, (T, C), dtype=torch.uint8, device="cuda")
+    out = torch.empty((C, T), dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    run = lambda: abi.aa_corner_turn_device(tm.data_ptr(), T, C, C, out.data_ptr(), T,
+                                            stream.cuda_stream)
+    for _ in range(args.warmup):
+        run()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        run()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    s = e0.elapsed_time(e1) / 1e3 / args.steps
+    ok = bool(torch.equal(out[:, :4096].cpu(), tm[:4096].cpu().T))
+    hbm = float(load_peaks().get("hbm_gbs", 6678.2))
+    gbs = 2 * C * T / s / 1e9
+    print(json.dumps({"metric": "corner turn: bytes moved per second", "workload": "4096ch x 2^20",
+                      "unit": "GB/s", "value": gbs, "ms": s * 1e3, "frac_of_measured_hbm": gbs / hbm,
+                      "peak_gbs": hbm, "steps": args.steps, "warmup": args.warmup,
+                      "sampled_check": ok}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["ska", "ska-small", "adjoint", "batched", "stream"],
+    ap.add_argument("--workload", choices=["ska", "ska-small", "adjoint", "batched", "stream",
+                                           "cornerturn"],
                     default="ska")
     ap.add_argument("--stream-chunks", type=int, default=6)
     ap.add_argument("--strategy", choices=["auto", "direct", "grouped"], default="auto",
@@ -643,6 +675,8 @@ def main():
         bench_batched(args)
     elif args.workload == "stream":
         bench_stream(args)
+    elif args.workload == "cornerturn":
+        bench_cornerturn(args)
     else:
         bench_ours(args)
 

@@ -474,6 +474,55 @@ aa_status aa_profile_read(int32_t kernel, int64_t* launches, double* total_ms);
 /* Static name of kernel id `kernel`, NULL past the last id. */
 const char* aa_profile_kernel_name(int32_t kernel);
 
+/* ------------------------------------------------- filterbank input (Sec. 4) */
+
+/* SIGPROC filterbank files: the paper's front-end can direct the library to a
+ * file on disk (Sec. 4).  A file is a header of keyword/value pairs between
+ * "HEADER_START" and "HEADER_END" (each string stored as a little-endian int32
+ * length followed by its bytes; integer values int32, real values IEEE
+ * double, string values as above), then the samples in time-major order: for
+ * each time sample, nifs x nchans values of nbits bits, channel 0 at fch1.
+ * Only nbits = 8 and nifs = 1 are read (the library's input type). */
+typedef struct aa_fil_header {
+    int32_t nchans;
+    int32_t nbits;
+    int32_t nifs;
+    int32_t data_type;     /* 0 if absent */
+    int32_t telescope_id;  /* -1 if absent */
+    int32_t machine_id;    /* -1 if absent */
+    double fch1_mhz;       /* centre frequency of channel 0 */
+    double foff_mhz;       /* channel spacing (negative: descending band) */
+    double tsamp_s;
+    double tstart_mjd;     /* 0 if absent */
+    int64_t header_bytes;  /* offset of the first sample in the file */
+    int64_t nsamples;      /* complete time samples in the file (from its size) */
+    char source_name[80];  /* NUL-terminated, empty if absent */
+} aa_fil_header;
+
+/* Parse the header of the file at `path` into *out.  AA_ERR_ARG for NULL
+ * arguments or a file that cannot be opened; AA_ERR_CONFIG for a malformed
+ * header (no HEADER_START, an unknown keyword, a truncated value, missing
+ * nchans/nbits/fch1/foff/tsamp, nbits != 8 or nifs != 1). */
+aa_status aa_fil_read_header(const char* path, aa_fil_header* out);
+
+/* Copy time samples [t0, t0 + nsamp) of the file (header `h` as returned by
+ * aa_fil_read_header) into the caller-owned host buffer host_tm, time-major:
+ * host_tm[t * nchans + c] (may be NULL when nsamp = 0).  AA_ERR_ARG if the range
+ * is outside the file or an argument is NULL; AA_ERR_CONFIG if the file is
+ * shorter than its header says. */
+aa_status aa_fil_read_block(const char* path, const aa_fil_header* h, int64_t t0, int64_t nsamp,
+                            uint8_t* host_tm);
+
+/* Corner turn on the device: d_cm[c * cm_pitch + t] = d_tm[t * tm_stride + c]
+ * for t < nsamp, c < nchans (time-major block -> the channel-major layout of
+ * aa_dedisperse_device).  tm_stride >= nchans and cm_pitch >= nsamp (bytes);
+ * the buffers must not overlap.  Asynchronous on `stream`; AA_ERR_ARG for bad
+ * sizes or NULL pointers, AA_ERR_CUDA if the launch fails.  No counterpart in
+ * the paper (its reader's data layout is internal). */
+aa_status aa_corner_turn_device(const uint8_t* d_tm, int64_t nsamp, int32_t nchans,
+                                int64_t tm_stride, uint8_t* d_cm, int64_t cm_pitch,
+                                aa_stream_t stream);
+
 /* ------------------------------------------------------------ test hooks -- */
 
 /* Fault injection for tests of the bounded device-side waits; affects every

@@ -60,6 +60,15 @@ class aa_plan_info(ctypes.Structure):
                 ("dm_max", ctypes.c_double), ("f32_ws_bytes", ctypes.c_int64)]
 
 
+class aa_fil_header(ctypes.Structure):
+    _fields_ = [("nchans", ctypes.c_int32), ("nbits", ctypes.c_int32), ("nifs", ctypes.c_int32),
+                ("data_type", ctypes.c_int32), ("telescope_id", ctypes.c_int32),
+                ("machine_id", ctypes.c_int32), ("fch1_mhz", ctypes.c_double),
+                ("foff_mhz", ctypes.c_double), ("tsamp_s", ctypes.c_double),
+                ("tstart_mjd", ctypes.c_double), ("header_bytes", ctypes.c_int64),
+                ("nsamples", ctypes.c_int64), ("source_name", ctypes.c_char * 80)]
+
+
 class aa_candidate(ctypes.Structure):
     _fields_ = [("dm_index", ctypes.c_uint32), ("t", ctypes.c_uint32),
                 ("width", ctypes.c_uint16), ("range", ctypes.c_uint8),
@@ -109,6 +118,9 @@ _SIG = {
                                           ctypes.POINTER(_I64)]),
     "aa_candidates_destroy": (None, [_P]),
     "aa_debug_inject": (ctypes.c_int, [_I32, _I64]),
+    "aa_fil_read_header": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(aa_fil_header)]),
+    "aa_fil_read_block": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(aa_fil_header), _I64, _I64, _P]),
+    "aa_corner_turn_device": (ctypes.c_int, [_P, _I64, _I32, _I64, _P, _I64, _P]),
     "aa_sps_search_device_noalloc": (ctypes.c_int, [_P, _I64, _P, _I32, _F32, _P, _I64, _P, _P,
                                                     _P]),
     "aa_dedisperse_f32_device": (ctypes.c_int, [_P, _P, _I64, _I64, _P, _P, _P]),
@@ -274,6 +286,23 @@ def aa_candidates_destroy(c) -> None:
 
 def aa_debug_inject(what: int, value: int = 0) -> None:
     check(lib().aa_debug_inject(int(what), int(value)), "aa_debug_inject")
+
+
+def aa_fil_read_header(path: str) -> aa_fil_header:
+    h = aa_fil_header()
+    check(lib().aa_fil_read_header(str(path).encode(), ctypes.byref(h)), "aa_fil_read_header")
+    return h
+
+
+def aa_fil_read_block(path: str, h: aa_fil_header, t0: int, nsamp: int, host_ptr: int) -> None:
+    check(lib().aa_fil_read_block(str(path).encode(), ctypes.byref(h), int(t0), int(nsamp),
+                                  host_ptr), "aa_fil_read_block")
+
+
+def aa_corner_turn_device(d_tm: int, nsamp: int, nchans: int, tm_stride: int, d_cm: int,
+                          cm_pitch: int, stream: int = 0) -> None:
+    check(lib().aa_corner_turn_device(d_tm, int(nsamp), int(nchans), int(tm_stride), d_cm,
+                                      int(cm_pitch), stream), "aa_corner_turn_device")
 
 
 def aa_profile_enable(on: bool) -> None:

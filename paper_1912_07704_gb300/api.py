@@ -56,6 +56,12 @@ class Plan:
     def from_workload(cls, w) -> "Plan":
         return cls(w.nchans, w.fch1, w.foff, w.tsamp, w.ranges)
 
+    @classmethod
+    def from_filterbank(cls, header, ranges) -> "Plan":
+        """Plan for the channels and sampling of a filterbank file header
+        (abi.aa_fil_header, see read_filterbank)."""
+        return cls(header.nchans, header.fch1_mhz, header.foff_mhz, header.tsamp_s, ranges)
+
     # lifetime ---------------------------------------------------------------
     def close(self):
         if getattr(self, "handle", None):
@@ -372,3 +378,30 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+# -- filterbank files ------------------------------------------------------------
+
+def read_filterbank(path, t0: int = 0, nsamp: int | None = None, pinned: bool = True):
+    """Header and time samples [t0, t0 + nsamp) of an 8-bit SIGPROC filterbank
+    file, as (abi.aa_fil_header, uint8 tensor [nsamp][nchans]) in host memory
+    (pinned by default, ready for an asynchronous copy)."""
+    h = abi.aa_fil_read_header(path)
+    n = h.nsamples - t0 if nsamp is None else int(nsamp)
+    buf = torch.empty((max(n, 0), h.nchans), dtype=torch.uint8,
+                      pin_memory=pinned and torch.cuda.is_available())
+    abi.aa_fil_read_block(path, h, t0, n, buf.data_ptr())
+    return h, buf
+
+
+def corner_turn(tm: torch.Tensor, pitch: int | None = None, stream=None) -> torch.Tensor:
+    """Device corner turn of a time-major uint8 block [nsamp][nchans] into a
+    channel-major [nchans][pitch] tensor (pitch >= nsamp, default nsamp rounded
+    up to 16, the dedispersion input's row alignment)."""
+    assert tm.is_cuda and tm.dtype == torch.uint8 and tm.dim() == 2
+    nsamp, nchans = tm.shape
+    pitch = (nsamp + 15) // 16 * 16 if pitch is None else int(pitch)
+    out = torch.zeros((nchans, pitch), dtype=torch.uint8, device=tm.device)
+    abi.aa_corner_turn_device(tm.data_ptr(), nsamp, nchans, tm.stride(0), out.data_ptr(), pitch,
+                              _stream_handle(stream))
+    return out

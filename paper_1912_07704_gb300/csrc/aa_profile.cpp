@@ -10,7 +10,7 @@ namespace aa {
 
 static const char* kKernelNames[kNumKernels] = {
     "decimate", "dedisperse_u8", "dedisperse_u16", "sps_rsqrt_table",
-    "sps_stats", "sps_boxcar", "f32_forward", "f32_adjoint"};
+    "sps_stats", "sps_boxcar", "f32_forward", "f32_adjoint", "corner_turn"};
 
 namespace {
 struct Pending {
