@@ -527,10 +527,11 @@ aa_status aa_corner_turn_device(const uint8_t* d_tm, int64_t nsamp, int32_t ncha
 
 /* Fault injection for tests of the bounded device-side waits; affects every
  * later launch in the process.  what = 0: reset all hooks; what = 1: the
- * dedispersion producer never issues the staging copy of channel chunk
- * `value` (that stage's barrier never completes, so every CTA gives up after
- * the wait limit, sets the workspace error word and exits without writing
- * output); what = 2: set the wait limit to `value` nanoseconds (default 2 s).
+ * direct-strategy dedispersion producer never issues the staging copy of
+ * channel chunk `value` (that stage's barrier never completes, so every CTA
+ * gives up after the wait limit, sets the workspace error word and exits
+ * without writing output; the grouped strategy has no staging waits); what =
+ * 2: set the wait limit to `value` nanoseconds (default 2 s).
  * Returns AA_ERR_ARG for an unknown `what` or a non-positive limit. */
 aa_status aa_debug_inject(int32_t what, int64_t value);
 

@@ -86,21 +86,6 @@ __device__ __forceinline__ uint32_t mad_add(uint32_t x, uint32_t one, uint32_t a
     return d;
 }
 
-// 16-byte asynchronous global -> shared copy (L2 only); completion tracked by
-// cp_async_mbar_arrive.
-__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
-}
-// Arrive on the mbarrier once this thread's earlier cp.async copies have landed
-// (the barrier's expected count includes this arrival).
-__device__ __forceinline__ void cp_async_mbar_arrive(uint64_t* bar) {
-    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
-}
-__device__ __forceinline__ void cp_async16_s(uint32_t dst, const void* src) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
-
 __device__ __forceinline__ void mbar_inval(uint64_t* bar) {
     asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
@@ -360,36 +345,30 @@ __device__ __forceinline__ void dedisperse_block(const DedispArgs& a, int ndm_bl
 }
 
 // Grouped strategy (see GroupRec in aa_internal.h).  CTA = 16 DM trials x
-// kGroupTau output samples.  Channel chunks of a.cc rows stream through a
-// two-stage ring filled by 16-byte cp.async copies that every warp issues
-// (one small bulk copy per row would make the bulk-copy request rate the
-// limit); the raw rows are staged in the order of the chunk's member list, so
-// group g's members are rows [mstart, mstart + mcount).  The groups of a chunk are processed in batches
-// of at most a.gz:
-//   phase 1: z_g[u] = sum of the group's staged rows at u, u < kGroupTau +
-//            span_g, as packed 16-bit pairs, stored twice: copy A word j =
+// kGroupTau output samples.  The channels stream through in chunks of a.cc;
+// the groups of a chunk are processed in batches of at most a.gz:
+//   phase 1: z_g[u] = sum over the group's members of x[c][t0 + s0_c + u],
+//            u < kGroupTau + span_g, read straight from global memory (each
+//            member row is read by one warp, coalesced 32-bit words; the rows
+//            of a chunk are shared by the CTAs of all DM blocks through L2),
+//            as packed 16-bit pairs stored twice: copy A word j =
 //            (z[2j], z[2j+1]) and copy B word j = (z[2j+1], z[2j+2]);
-//            work unit = (group, 256 consecutive u), one warp per unit;
+//            work unit = (group, 256 consecutive u), units round-robin over
+//            the warps;
 //   phase 2: warp w (trial d0 + w) adds z_g[t + delta_g(w)] for its 16
 //            samples t: copy (delta & 1), word offset delta >> 1, aligned.
 // 16-bit lanes never overflow: a chunk holds at most 65535 / (255 dec)
 // channels, and trial accumulators are flushed every a.gflush chunks.
+// `wait_limit_ns` and `fault_skip_chunk` are unused (no device-side waits).
 template <int EB>
 __device__ __forceinline__ void dedisperse_grouped_block(const DedispArgs& a, int ndm_blocks,
-                                                         int64_t bid, uint64_t wait_limit_ns,
-                                                         int fault_skip_chunk, unsigned char* smem,
-                                                         uint64_t* bars, bool reinit) {
+                                                         int64_t bid, unsigned char* smem) {
     constexpr int T = kGroupTau;
     constexpr int QW = T / 64;  // packed words (2 samples) per lane per trial
-    const int gcc = a.cc, grwx = a.grwx, gz = a.gz, gzw = a.gzw;
-    constexpr int NST = 2;
-    unsigned char* xst = smem;  // [NST][gcc][grwx] staged rows (member order)
-    uint32_t* zs = reinterpret_cast<uint32_t*>(xst + (size_t)NST * gcc * grwx);  // [gz][2][gzw]
-    // per-member staging records, 3-deep ring by chunk: (phase-1 word << 5 | shift,
-    // bytes to copy, global byte offset lo, hi)
-    int4* meta = reinterpret_cast<int4*>(zs + (size_t)gz * 2 * gzw);  // [3][gcc]
+    const int gcc = a.cc, gz = a.gz, gzw = a.gzw, nj = a.gnj;
+    uint32_t* zs = reinterpret_cast<uint32_t*>(smem);  // [gz][2][gzw]
 
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int dmb = (int)(bid % ndm_blocks);
     const int64_t tile = bid / ndm_blocks;
     const int d0 = dmb * kDmPerBlock;
@@ -401,80 +380,10 @@ __device__ __forceinline__ void dedisperse_grouped_block(const DedispArgs& a, in
     const int64_t pitch_b = a.in_pitch * EB;
     const GroupRec* recs = a.grec + (size_t)dmb * nchunks;
     const GroupMember* mems = a.gmem + (size_t)dmb * nchunks * gcc;
-
-    if (tid == 0) {  // every barrier of the fixed array, whatever the previous item used
-        for (int st = 0; st < kMaxStages; ++st) {
-            if (reinit) mbar_inval(&bars[st]);
-            mbar_init(&bars[st], kDedispThreads);  // one cp.async arrival per thread
-        }
-        mbar_fence_init();
-    }
-
-    // Producer (warp 0): stage chunk k; lane l handles members l and l + 32.
-    // Member m of the chunk is channel k*gcc + ch[m]; its row holds the bytes
-    // from the 16-byte boundary below sample t0 + s0 up to the last sample its
-    // group reads (+ the words phase 1 over-reads).  The members' records are
-    // loaded one issue ahead (pre), so issuing waits on no global load.
-    int2 pre[2] = {make_int2(0, 0), make_int2(0, 0)};  // (s0, ch | span << 16)
-    auto prefetch = [&](int k) {
-        if (k >= nchunks) return;
-        const int nch = min(gcc, C - k * gcc);
-        const int2* mem = reinterpret_cast<const int2*>(mems + (size_t)k * gcc);
-#pragma unroll
-        for (int h = 0; h < 2; ++h)
-            if (lane + 32 * h < nch) pre[h] = __ldg(mem + lane + 32 * h);
-    };
-    // warp 0: staging records of chunk j from the prefetched member records
-    auto make_meta = [&](int j) {
-        if (j >= nchunks) return;
-        const int st = j % NST;
-        const int c0 = j * gcc;
-        const int nch = min(gcc, C - c0);
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int m = lane + 32 * h;
-            if (m < nch) {
-                const int s0 = pre[h].x;
-                const int c = c0 + (pre[h].y & 0xffff), span = (int)((uint32_t)pre[h].y >> 16);
-                const int64_t start = (int64_t)EB * (t0 + s0);
-                const int64_t base = start & ~int64_t(15);
-                const int o = (int)(start - base);
-                int64_t nb = ((int64_t)o + (int64_t)EB * (T + span) + 12 + 15) / 16 * 16;
-                nb = min(nb, (int64_t)grwx);
-                nb = min(nb, pitch_b - base);
-                const int64_t src = (int64_t)c * pitch_b + base;
-                const int word = (int)(((size_t)(st * gcc + m) * grwx + o) >> 2);
-                meta[(j % 3) * gcc + m] = make_int4((word << 5) | ((o & 3) * 8), nb > 0 ? (int)nb : 0,
-                                                   (int)(uint32_t)src, (int)(src >> 32));
-            }
-        }
-        prefetch(j + 1);
-    };
-    // every thread: copy chunk j into stage j % NST (warp w: rows w, w + 16, ..),
-    // then arrive on the stage's barrier when its copies have landed
-    auto issue = [&](int j) {
-        if (j == fault_skip_chunk) return;  // fault injection: this stage never completes
-        const int st = j % NST;
-        const int nch = min(gcc, C - j * gcc);
-        const uint32_t xs = smem_addr(xst) + 16 * lane;
-        const int4* mj = meta + (j % 3) * gcc;
-        for (int m = warp; m < nch; m += kDedispWarps) {
-            const int4 md = mj[m];
-            const unsigned char* src = in_b + (((int64_t)md.w << 32) | (uint32_t)md.z) + 16 * lane;
-            const uint32_t dst = xs + (uint32_t)((st * gcc + m) * grwx);
-            for (int q = 16 * lane; q < md.y; q += 16 * 32)
-                cp_async16_s(dst + (q - 16 * lane), src + (q - 16 * lane));
-        }
-        cp_async_mbar_arrive(&bars[st]);
-    };
-
-    if (warp == 0) {
-        prefetch(0);
-        for (int j = 0; j <= NST && j < nchunks; ++j) make_meta(j);  // chunks 0 .. NST
-    }
-    __syncthreads();  // barriers initialised, first records written
-    for (int j = 0; j < min(NST, nchunks); ++j) issue(j);
-    int next_issue = min(NST, nchunks);
+    // units: warp w takes u = w, w + 16, ..; (group, block) = (u / nj, u % nj)
+    // stepped without dividing
+    const int gstep = kDedispWarps / nj, jstep = kDedispWarps - gstep * nj;
+    const int gi0 = warp / nj, j0 = warp - gi0 * nj;
 
     uint32_t acc[QW];
     uint32_t tot[2 * QW];
@@ -485,44 +394,30 @@ __device__ __forceinline__ void dedisperse_grouped_block(const DedispArgs& a, in
     }
     const bool has_trial = d0 + warp <= dlast;
     int since_flush = 0;
-    const uint32_t* xw = reinterpret_cast<const uint32_t*>(xst);
 
-    const int nj = a.gnj;                        // 256-sample units per group sum
-    const int gstep = kDedispWarps / nj, jstep = kDedispWarps - gstep * nj;
-    const int gi0 = warp / nj, j0 = warp - gi0 * nj;  // this warp's first unit
-    GroupRec rec_next = recs[0];  // record of the next chunk, loaded one chunk ahead
     for (int k = 0; k < nchunks; ++k) {
-        const int st = k % NST;
-        const uint32_t parity = (uint32_t)(k / NST) & 1u;
-        const GroupRec rec = rec_next;
-        if (k + 1 < nchunks) rec_next = recs[k + 1];
+        const GroupRec rec = recs[k];
         const GroupDesc* gd = a.gdesc + rec.first;
+        const GroupMember* mk = mems + (size_t)k * gcc;
+        const unsigned char* chunk_in = in_b + (int64_t)(k * gcc) * pitch_b;
         const int G = rec.ngroups;
-        // group fields of a batch, one group per lane (the first batch's are
-        // loaded before the wait): members (start | count << 16), span, and this
-        // warp's phase-2 word offset of the group sum at its trial's delay
-        uint32_t g_ms = 0, g_span = 0;
-        int g_p2 = 0;
-        auto load_batch = [&](int gb0) {
-            const int gl = gb0 + lane;
-            if (gl < min(G, gb0 + gz)) {
-                g_ms = (uint32_t)gd[gl].mstart | ((uint32_t)gd[gl].mcount << 16);
-                g_span = gd[gl].span;
-                const int dl = gd[gl].delta[warp];
-                g_p2 = (lane * 2 + (dl & 1)) * gzw + (dl >> 1);
-            }
-        };
-        load_batch(0);
-        const bool ok = mbar_wait_bounded(&bars[st], parity, wait_limit_ns);
         for (int gb = 0; gb < G; gb += gz) {
             const int ge = min(G, gb + gz);
-            if (gb > 0) load_batch(gb);
-            // ---- phase 1: group sums of this batch.  Unit u = (group gb + u / nj,
-            // samples 256 (u % nj) ..): warp w takes units w, w + 16, ...
-            if (ok) {
+            // group fields, one group per lane: members (start | count << 16),
+            // span, and this warp's phase-2 word offset at its trial's delay
+            uint32_t g_ms = 0, g_span = 0;
+            int g_p2 = 0;
+            if (gb + lane < ge) {
+                const GroupDesc& g = gd[gb + lane];
+                g_ms = (uint32_t)g.mstart | ((uint32_t)g.mcount << 16);
+                g_span = g.span;
+                const int dl = g.delta[warp];
+                g_p2 = (lane * 2 + (dl & 1)) * gzw + (dl >> 1);
+            }
+            // ---- phase 1: group sums of this batch
+            {
                 const int nunits = (ge - gb) * nj;
-                const int4* mk = meta + (k % 3) * gcc;
-                int gi = gi0, j = j0;  // unit u = gi * nj + j, stepped by 16 without dividing
+                int gi = gi0, j = j0;
                 for (int u = warp; u < nunits; u += kDedispWarps) {
                     const uint32_t ms = __shfl_sync(0xffffffffu, g_ms, gi);
                     const int zlen = T + (int)__shfl_sync(0xffffffffu, g_span, gi);
@@ -530,16 +425,23 @@ __device__ __forceinline__ void dedisperse_grouped_block(const DedispArgs& a, in
                     uint32_t* zA = zs + gi * 2 * gzw;
                     uint32_t* zB = zA + gzw;
                     const int idx = 32 * j + lane;  // this lane: samples 8 idx .. 8 idx + 7
-                    // packed pairs (z0,z1) (z2,z3) (z4,z5) (z6,z7) and z8
-                    uint32_t A0 = 0, A1 = 0, A2 = 0, A3 = 0, E = 0;
+                    uint32_t A0 = 0, A1 = 0, A2 = 0, A3 = 0, E = 0;  // (z0,z1) .. (z6,z7), z8
                     if (8 * idx < zlen) {
 #pragma unroll 2
                         for (int m = mstart; m < mend; ++m) {
-                            const int pk = mk[m].x;
-                            const uint32_t sh = (uint32_t)pk & 31u;
+                            const int2 rm = __ldg(reinterpret_cast<const int2*>(mk + m));  // (s0, ch | span << 16)
+                            // byte offset of this lane's first sample in the row.
+                            // Bytes at or past the row pitch are never used for an
+                            // output sample; their words are clamped to the row's
+                            // last word so no read leaves the buffer.
+                            const int64_t bo = (int64_t)EB * (t0 + rm.x + 8 * idx);
+                            const int wi = (int)(bo >> 2), wl = (int)(pitch_b >> 2) - 1;
+                            const uint32_t* w = reinterpret_cast<const uint32_t*>(
+                                chunk_in + (int64_t)(rm.y & 0xffff) * pitch_b);
+                            const uint32_t sh = (uint32_t)(bo & 3) * 8u;
                             if constexpr (EB == 1) {
-                                const uint32_t* w = xw + (pk >> 5) + 2 * idx;
-                                const uint32_t w0 = w[0], w1 = w[1], w2 = w[2];
+                                const uint32_t w0 = __ldg(w + min(wi, wl)), w1 = __ldg(w + min(wi + 1, wl)),
+                                               w2 = __ldg(w + min(wi + 2, wl));
                                 const uint32_t v0 = __funnelshift_r(w0, w1, sh);
                                 const uint32_t v1 = __funnelshift_r(w1, w2, sh);
                                 A0 += __byte_perm(v0, 0u, 0x4140);
@@ -548,8 +450,9 @@ __device__ __forceinline__ void dedisperse_grouped_block(const DedispArgs& a, in
                                 A3 += __byte_perm(v1, 0u, 0x4342);
                                 E += (w2 >> sh) & 0xffu;
                             } else {
-                                const uint32_t* w = xw + (pk >> 5) + 4 * idx;
-                                const uint32_t w0 = w[0], w1 = w[1], w2 = w[2], w3 = w[3], w4 = w[4];
+                                const uint32_t w0 = __ldg(w + min(wi, wl)), w1 = __ldg(w + min(wi + 1, wl)),
+                                               w2 = __ldg(w + min(wi + 2, wl)), w3 = __ldg(w + min(wi + 3, wl)),
+                                               w4 = __ldg(w + min(wi + 4, wl));
                                 A0 += __funnelshift_r(w0, w1, sh);
                                 A1 += __funnelshift_r(w1, w2, sh);
                                 A2 += __funnelshift_r(w2, w3, sh);
@@ -570,26 +473,7 @@ __device__ __forceinline__ void dedisperse_grouped_block(const DedispArgs& a, in
                     }
                 }
             }
-            const bool last_batch = ge == G;
-            if (gb == 0) {
-                if (!__syncthreads_and(ok)) {
-                    // A stage never arrived: report, drain the copies still in
-                    // flight (bounded), and leave without touching the output.
-                    if (tid == 0) atomicOr(a.err, 1u);
-                    cp_async_wait_all();  // this thread's copies in flight
-                    return;
-                }
-            } else {
-                __syncthreads();
-            }
-            // the staged rows of chunk k are no longer read: refill the stage
-            // with chunk k + 2 and prepare the records of chunk k + 3 (its slot
-            // held chunk k's, no longer read)
-            if (last_batch && next_issue < nchunks) {
-                issue(next_issue);
-                ++next_issue;
-                if (warp == 0) make_meta(next_issue);
-            }
+            __syncthreads();  // group sums complete
             // ---- phase 2: every trial adds every group sum at its relative delay
             if (has_trial) {
                 const uint32_t* zl = zs + lane;
@@ -600,8 +484,7 @@ __device__ __forceinline__ void dedisperse_grouped_block(const DedispArgs& a, in
                     for (int q = 0; q < QW; ++q) acc[q] += src[32 * q];
                 }
             }
-            // the next batch (or chunk) overwrites the group sums
-            if (!(last_batch && k + 1 == nchunks)) __syncthreads();
+            __syncthreads();  // the next batch (or chunk) overwrites the group sums
         }
         if (++since_flush >= a.gflush) {
 #pragma unroll
@@ -635,12 +518,9 @@ __device__ __forceinline__ void dedisperse_grouped_block(const DedispArgs& a, in
 
 template <int EB>
 __global__ void __launch_bounds__(kDedispThreads, 2)
-    dedisperse_grouped_kernel(DedispArgs a, int ndm_blocks, uint64_t wait_limit_ns,
-                              int fault_skip_chunk) {
+    dedisperse_grouped_kernel(DedispArgs a, int ndm_blocks) {
     extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ uint64_t bars[kMaxStages];
-    dedisperse_grouped_block<EB>(a, ndm_blocks, blockIdx.x, wait_limit_ns, fault_skip_chunk, smem,
-                                 bars, false);
+    dedisperse_grouped_block<EB>(a, ndm_blocks, blockIdx.x, smem);
 }
 
 template <int SPW>
@@ -686,8 +566,7 @@ __global__ void __launch_bounds__(kDedispThreads, 2)
         const int k = find_desc(first, ndesc, item);
         const DedispArgs& a = descs[k];
         if constexpr (GROUPED)
-            dedisperse_grouped_block<EB>(a, ndm_blocks[k], item - first[k], wait_limit_ns, -1, smem,
-                                         bars, reinit);
+            dedisperse_grouped_block<EB>(a, ndm_blocks[k], item - first[k], smem);
         else
             dedisperse_block<4 / EB>(a, ndm_blocks[k], item - first[k], wait_limit_ns, -1, one, smem,
                                      bars, reinit);
@@ -789,7 +668,7 @@ cudaError_t launch_dedisperse(const DedispArgs& a, cudaStream_t s) {
         auto kern = a.elem == 1 ? dedisperse_grouped_kernel<1> : dedisperse_grouped_kernel<2>;
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)a.smem);
         if (e != cudaSuccess) return e;
-        kern<<<(unsigned)nblocks, kDedispThreads, a.smem, s>>>(a, ndmb, g_wait_limit_ns, g_fault_skip_chunk);
+        kern<<<(unsigned)nblocks, kDedispThreads, a.smem, s>>>(a, ndmb);
         return cudaGetLastError();
     }
     auto kern = a.elem == 1 ? dedisperse_kernel<4> : dedisperse_kernel<2>;

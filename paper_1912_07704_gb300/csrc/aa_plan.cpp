@@ -50,11 +50,9 @@ static size_t dedisp_smem(const RangePlan& r, int cc, int nstage) {
 
 size_t dedisp_smem_bytes(const RangePlan& r, int cc, int nstage) { return dedisp_smem(r, cc, nstage); }
 
-// Shared memory of the grouped strategy: staged rows, group sums (two
-// copies each), a 3-deep ring of 16-byte per-member staging records.
-static size_t grouped_smem(int nstage, int gcc, int grwx, int gz, int gzw) {
-    return (size_t)nstage * gcc * grwx + (size_t)gz * 2 * gzw * 4 + (size_t)3 * gcc * 16;
-}
+// Shared memory of the grouped strategy: the group sums of one batch (two
+// copies each; the input rows are read from global memory).
+static size_t grouped_smem(int gz, int gzw) { return (size_t)gz * 2 * gzw * 4; }
 
 // Delay-pattern groups of every (DM block, channel chunk) of a range, and the
 // grouped tile shape.  Two CTAs per SM must fit (<= kPairSmem each).
@@ -65,20 +63,14 @@ static void build_groups(RangePlan& r, int C) {
     const int dec = r.desc.dec;
     const int lane_max = 65535 / (255 * dec);          // channels per 16-bit lane
     if (r.span_max > 4096) return;
-    // staged row: alignment offset (< 16) + the samples read + the words phase 1
-    // reads past them (8 samples per lane: up to 20 bytes)
-    const int grwx = (int)round_up(15 + (int64_t)r.elem * (kGroupTau + r.span_max) + 20, 16);
     const int gzw = (int)round_up((kGroupTau + r.span_max + 3) / 2 + 2, 4);
-    const int nstage = 2;
-    // the largest chunk (multiple of 8, <= 64 raw / 32 decimated rows) that
-    // leaves room for at least 8 group sums
-    int gcc = std::min(r.elem == 1 ? 64 : 32, lane_max) / 8 * 8, gz = 0;
-    for (; gcc >= 8; gcc -= 8) {
-        gz = 0;
-        while (grouped_smem(nstage, gcc, grwx, gz + 1, gzw) <= kPairSmem && gz < std::min(gcc, 32)) ++gz;
-        if (gz >= std::min(gcc, 8)) break;
-    }
-    if (gcc < 8) return;
+    // chunks of up to 64 channels (fewer when 16-bit lanes would overflow);
+    // as many group sums per batch as two CTAs per SM leave room for (<= 32,
+    // one per lane of the warps' group-field registers)
+    const int gcc = std::min(64, lane_max) / 8 * 8;
+    int gz = 0;
+    while (grouped_smem(gz + 1, gzw) <= kPairSmem && gz < std::min(gcc, 32)) ++gz;
+    if (gcc < 8 || gz < 1) return;
     const int ndm = r.desc.ndm;
     const int nblk = (ndm + B - 1) / B, nchk = (C + gcc - 1) / gcc;
     r.grec.assign((size_t)nblk * nchk, GroupRec{});
@@ -132,11 +124,11 @@ static void build_groups(RangePlan& r, int C) {
     }
     r.gcc = gcc;
     r.gz = gz;
-    r.grwx = grwx;
+    r.grwx = 0;
     r.gzw = gzw;
     r.gflush = std::max(1, lane_max / gcc);
     r.gnj = (kGroupTau + r.span_max + 255) / 256;
-    r.gsmem = grouped_smem(nstage, gcc, grwx, gz, gzw);
+    r.gsmem = grouped_smem(gz, gzw);
     r.gwork = direct > 0 ? grouped / direct : 1.0;
     r.grouped_ok = true;
 }

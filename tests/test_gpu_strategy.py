@@ -73,10 +73,10 @@ def test_synthetic_workload_with_pulses(oracle):
     _check_plan(oracle, w.nchans, w.fch1, w.foff, w.tsamp, w.ranges, x)
 
 
-def test_grouped_timeout_reports_and_recovers():
-    """A staging copy of the grouped kernel that is never issued (host-side
-    injection) makes every CTA give up after the bounded wait; the host reads
-    AA_ERR_TIMEOUT and the next run is clean."""
+def test_grouped_has_no_staging_waits():
+    """The grouped kernel reads its rows from global memory and has no
+    device-side waits: the staging-fault injection (which makes the direct
+    kernel time out) leaves it correct."""
     C, nsamp = 256, 4096
     p = Plan(C, 1500.0, -1.171875, 64e-6, [(0.0, 0.05, 16, 1)])
     p.set_strategy(0, abi.AA_DEDISP_GROUPED)
@@ -88,13 +88,11 @@ def test_grouped_timeout_reports_and_recovers():
     stream = torch.cuda.current_stream().cuda_stream
     try:
         abi.aa_debug_inject(2, 20_000_000)  # 20 ms
-        abi.aa_debug_inject(1, 1)           # chunk 1 never staged
+        abi.aa_debug_inject(1, 1)           # chunk 1 of the direct kernel never staged
         p.dedisperse_device(d, n, out=out, ws=ws)
-        assert abi.aa_workspace_status(ws.data_ptr(), stream) == abi.AA_ERR_TIMEOUT
+        assert abi.aa_workspace_status(ws.data_ptr(), stream) == abi.AA_OK
     finally:
         abi.aa_debug_inject(0, 0)
-    p.dedisperse_device(d, n, out=out, ws=ws)
-    assert abi.aa_workspace_status(ws.data_ptr(), stream) == abi.AA_OK
     torch.cuda.synchronize()
     assert torch.all(p.range_views(out, n)[0] == 7 * C)
 
