@@ -216,14 +216,7 @@ class Plan:
         """Sorted candidate records (numpy structured array) and the total found."""
         h, st = abi.aa_sps_search(self.handle, dd.handle, max_width, threshold, capacity,
                                   _stream_handle(stream))
-        try:
-            ptr, stored, total = abi.aa_candidates_view(h)
-            arr = np.zeros(stored, dtype=abi.CANDIDATE_DTYPE)
-            if stored:
-                ctypes.memmove(arr.ctypes.data, ptr, stored * abi.CANDIDATE_DTYPE.itemsize)
-        finally:
-            abi.aa_candidates_destroy(h)
-        return arr, total
+        return _candidates_array(h)
 
 
 class _DeviceArray:
@@ -271,15 +264,34 @@ def candidates_from_device(cands: torch.Tensor, count: torch.Tensor, capacity: i
     return arr[order]
 
 
+class _CandidatesOwner:
+    """Destroys a library candidate list when the last numpy view of it goes."""
+
+    def __init__(self, h):
+        self.h = h
+
+    def __del__(self):
+        try:
+            abi.aa_candidates_destroy(self.h)
+        except Exception:
+            pass
+
+
 def _candidates_array(h) -> tuple:
+    """Zero-copy numpy view (structured records) of a library candidate list,
+    and the total found; the list is freed with the last view."""
     try:
         ptr, stored, total = abi.aa_candidates_view(h)
-        arr = np.zeros(stored, dtype=abi.CANDIDATE_DTYPE)
-        if stored:
-            ctypes.memmove(arr.ctypes.data, ptr, stored * abi.CANDIDATE_DTYPE.itemsize)
-    finally:
+    except Exception:
         abi.aa_candidates_destroy(h)
-    return arr, total
+        raise
+    if not stored:
+        abi.aa_candidates_destroy(h)
+        return np.zeros(0, dtype=abi.CANDIDATE_DTYPE), total
+    nbytes = stored * abi.CANDIDATE_DTYPE.itemsize
+    buf = (ctypes.c_char * nbytes).from_address(ptr)
+    buf.owner = _CandidatesOwner(h)
+    return np.frombuffer(buf, dtype=abi.CANDIDATE_DTYPE, count=stored), total
 
 
 class Batch:

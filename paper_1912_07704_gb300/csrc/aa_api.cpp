@@ -3,6 +3,7 @@
 // memory requests, Sec. 2.4 ownership, Sec. 3.1 usage steps 4-8).
 #include <algorithm>
 #include <cstring>
+#include <memory>
 #include <new>
 #include <vector>
 
@@ -25,12 +26,16 @@ struct aa_dd_result {
 };
 
 struct aa_candidates {
-    std::vector<aa_candidate> list;
+    std::vector<aa_candidate> list;            // filled by the batch and server paths
+    std::unique_ptr<aa_candidate[]> ordered;   // filled by order_candidates
+    int64_t nordered = 0;
     int64_t total = 0;
 };
 
 namespace aa {
 aa_candidates* candidates_new() { return new (std::nothrow) aa_candidates(); }
+
+
 std::vector<aa_candidate>& candidates_list(aa_candidates* c) { return c->list; }
 void candidates_set_total(aa_candidates* c, int64_t total) { c->total = total; }
 }  // namespace aa
@@ -94,7 +99,85 @@ void keep_pool_memory(int device) {
     done[device] = true;
 }
 
+
+
 }  // namespace
+
+namespace aa {
+
+aa_status order_candidates(const aa_candidate* d_cands, int64_t stored, std::vector<CandChunk>& heads,
+                           bool by_beam, cudaStream_t s, aa_candidates* res) {
+    // counting sort of the runs by (beam, dm_index), then by t0 inside a bucket
+    uint32_t max_dm = 0, max_beam = 0;
+    for (const CandChunk& h : heads) {
+        max_dm = std::max(max_dm, h.dm_index);
+        if (by_beam) max_beam = std::max(max_beam, h.reserved);
+    }
+    const uint64_t kdm = (uint64_t)max_dm + 1;
+    const uint64_t nkeys = ((uint64_t)max_beam + 1) * kdm;
+    auto key = [&](const CandChunk& h) { return (by_beam ? (uint64_t)h.reserved * kdm : 0ull) + h.dm_index; };
+    std::vector<uint64_t> uk;  // bucket index -> key, used only when keys are sparse
+    const bool dense = nkeys <= 4 * (uint64_t)heads.size() + 65536;
+    if (!dense) {
+        uk.resize(heads.size());
+        for (size_t i = 0; i < heads.size(); ++i) uk[i] = key(heads[i]);
+        std::sort(uk.begin(), uk.end());
+        uk.erase(std::unique(uk.begin(), uk.end()), uk.end());
+    }
+    const size_t nb = dense ? (size_t)nkeys : uk.size();
+    std::vector<int64_t> start(nb + 1, 0);
+    std::vector<uint32_t> bucket(heads.size());
+    for (size_t i = 0; i < heads.size(); ++i) {
+        const uint64_t k = key(heads[i]);
+        bucket[i] = dense ? (uint32_t)k : (uint32_t)(std::lower_bound(uk.begin(), uk.end(), k) - uk.begin());
+        ++start[bucket[i] + 1];
+    }
+    for (size_t b = 0; b < nb; ++b) start[b + 1] += start[b];
+    std::vector<CandChunk> sorted(heads.size());
+    {
+        std::vector<int64_t> fill(start.begin(), start.end() - 1);
+        for (size_t i = 0; i < heads.size(); ++i) sorted[(size_t)fill[bucket[i]]++] = heads[i];
+    }
+    for (size_t b = 0; b < nb; ++b)
+        if (start[b + 1] - start[b] > 1)
+            std::sort(sorted.begin() + start[b], sorted.begin() + start[b + 1],
+                  [](const CandChunk& x, const CandChunk& y) { return x.t0 < y.t0; });
+    // destinations in that order (records past `stored` were not written)
+    std::vector<RunCopy> runs;
+    runs.reserve(sorted.size());
+    int64_t dst = 0;
+    for (const CandChunk& h : sorted) {
+        const int64_t src = (int64_t)h.base;
+        const int64_t n = std::min<int64_t>((int64_t)h.n, std::max<int64_t>(0, stored - src));
+        if (n > 0) {
+            runs.push_back(RunCopy{src, dst, n});
+            dst += n;
+        }
+    }
+    res->nordered = 0;
+    if (dst == 0) return AA_OK;
+    try {
+        res->ordered.reset(new aa_candidate[(size_t)dst]);
+    } catch (const std::bad_alloc&) {
+        set_error("host allocation of %lld candidates failed", (long long)dst);
+        return AA_ERR_NOMEM;
+    }
+    AsyncAllocs mem(s);
+    aa_candidate* d_out = static_cast<aa_candidate*>(mem.get((size_t)dst * sizeof(aa_candidate)));
+    RunCopy* d_runs = static_cast<RunCopy*>(mem.get(runs.size() * sizeof(RunCopy)));
+    if (!d_out || !d_runs) { set_error("device allocation failed"); return AA_ERR_NOMEM; }
+    AA_CUDA(cudaMemcpyAsync(d_runs, runs.data(), runs.size() * sizeof(RunCopy), cudaMemcpyHostToDevice, s),
+            "upload run order");
+    AA_CUDA(launch_gather_runs(d_cands, d_out, d_runs, (int64_t)runs.size(), s), "gather candidates");
+    AA_CUDA(cudaMemcpyAsync(res->ordered.get(), d_out, (size_t)dst * sizeof(aa_candidate),
+                            cudaMemcpyDeviceToHost, s),
+            "read candidates");
+    AA_CUDA(cudaStreamSynchronize(s), "synchronize");
+    res->nordered = dst;
+    return AA_OK;
+}
+
+}  // namespace aa
 
 extern "C" {
 
@@ -373,39 +456,22 @@ aa_status aa_sps_search(aa_plan* p, const aa_dd_result* dd, int32_t max_width, f
     if (e != cudaSuccess) { delete res; return cuda_fail(e, "read candidate count"); }
     const int64_t stored = std::min<int64_t>((int64_t)total, cand_capacity);
     // Records arrive as per-CTA runs (each ordered by t); order the runs by
-    // (dm_index, t0) through their headers and concatenate.
+    // (dm_index, t0) through their headers, gather on the device, copy once.
     unsigned long long nchunks = 0;
-    std::vector<aa_candidate> raw;
-    std::vector<CandChunk> heads;
-    try {
-        raw.resize((size_t)stored);
-        res->list.reserve((size_t)stored);
-    } catch (const std::bad_alloc&) {
-        delete res;
-        set_error("host allocation failed");
-        return AA_ERR_NOMEM;
-    }
     e = cudaMemcpyAsync(&nchunks, static_cast<char*>(d_ws) + kChunkCounterOffset, sizeof nchunks,
                         cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess && stored > 0)
-        e = cudaMemcpyAsync(raw.data(), d_c, (size_t)stored * sizeof(aa_candidate),
-                            cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) { delete res; return cuda_fail(e, "read candidates"); }
+    if (e != cudaSuccess) { delete res; return cuda_fail(e, "read candidate chunk count"); }
     const int64_t nh = std::min<int64_t>((int64_t)nchunks, L.chunk_cap);
-    heads.resize((size_t)nh);
+    std::vector<CandChunk> heads((size_t)nh);
     if (nh > 0) {
         e = cudaMemcpyAsync(heads.data(), static_cast<char*>(d_ws) + L.chunk_offset,
                             (size_t)nh * sizeof(CandChunk), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) { delete res; return cuda_fail(e, "read candidate chunks"); }
     }
-    std::sort(heads.begin(), heads.end(), [](const CandChunk& a, const CandChunk& b) {
-        return a.dm_index != b.dm_index ? a.dm_index < b.dm_index : a.t0 < b.t0;
-    });
-    for (const CandChunk& h : heads)
-        for (unsigned long long k = h.base; k < h.base + h.n && (int64_t)k < stored; ++k)
-            res->list.push_back(raw[(size_t)k]);
+    st = order_candidates(d_c, stored, heads, false, s, res);
+    if (st != AA_OK) { delete res; return st; }
     res->total = (int64_t)total;
     unsigned h = 0, h2 = 0;
     e = cudaMemcpyAsync(&h, d_ws, sizeof h, cudaMemcpyDeviceToHost, s);
@@ -422,8 +488,10 @@ aa_status aa_candidates_view(const aa_candidates* c, const aa_candidate** host, 
                              int64_t* total) {
     clear_error();
     if (!c) { set_error("candidates is NULL"); return AA_ERR_ARG; }
-    if (host) *host = c->list.empty() ? nullptr : c->list.data();
-    if (stored) *stored = (int64_t)c->list.size();
+    const bool ord = c->nordered > 0;
+    const int64_t n = ord ? c->nordered : (int64_t)c->list.size();
+    if (host) *host = n == 0 ? nullptr : (ord ? c->ordered.get() : c->list.data());
+    if (stored) *stored = n;
     if (total) *total = c->total;
     return AA_OK;
 }

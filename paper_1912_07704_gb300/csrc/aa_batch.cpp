@@ -438,22 +438,17 @@ aa_status aa_batch_candidates(aa_batch* b, aa_stream_t stream, aa_candidates** o
     if (err) { set_error("a bounded device-side wait gave up"); return AA_ERR_TIMEOUT; }
     const int64_t stored = std::min<int64_t>((int64_t)counts[0], b->capacity);
     const int64_t nh = std::min<int64_t>((int64_t)counts[1], b->chunk_cap);
-    std::vector<aa_candidate> raw((size_t)stored);
     std::vector<CandChunk> heads((size_t)nh);
-    if (stored) AA_CUDA(cudaMemcpyAsync(raw.data(), b->d_cands, stored * sizeof(aa_candidate), cudaMemcpyDeviceToHost, s), "read candidates");
     if (nh) AA_CUDA(cudaMemcpyAsync(heads.data(), b->d_chunks, nh * sizeof(CandChunk), cudaMemcpyDeviceToHost, s), "read chunks");
     AA_CUDA(cudaStreamSynchronize(s), "synchronize");
-    std::sort(heads.begin(), heads.end(), [](const CandChunk& x, const CandChunk& y) {
-        if (x.reserved != y.reserved) return x.reserved < y.reserved;  // beam
-        return x.dm_index != y.dm_index ? x.dm_index < y.dm_index : x.t0 < y.t0;
-    });
     aa_candidates* res = candidates_new();
     if (!res) { set_error("host allocation failed"); return AA_ERR_NOMEM; }
-    std::vector<aa_candidate>& list = candidates_list(res);
-    list.reserve((size_t)stored);
-    for (const CandChunk& h : heads)
-        for (unsigned long long k = h.base; k < h.base + h.n && (int64_t)k < stored; ++k)
-            list.push_back(raw[(size_t)k]);
+    // runs ordered by (beam, dm_index, t0), gathered on the device, copied once
+    const aa_status ost = order_candidates(b->d_cands, stored, heads, true, s, res);
+    if (ost != AA_OK) {
+        aa_candidates_destroy(res);
+        return ost;
+    }
     candidates_set_total(res, (int64_t)counts[0]);
     *out = res;
     return (int64_t)counts[0] > b->capacity ? AA_WARN_CAND_OVERFLOW : AA_OK;

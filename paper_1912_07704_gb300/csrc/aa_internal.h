@@ -270,6 +270,22 @@ int sps_boxcar_tiles(int64_t length);
 size_t sps_boxcar_smem(int wpad);
 cudaError_t launch_rsqrt_table(double* t, int wpad, cudaStream_t s);
 
+// Candidate runs moved into their final order: run i copies n[i] records
+// from src[i] to dst[i] (record indices).
+struct RunCopy {
+    int64_t src, dst;
+    int64_t n;
+};
+cudaError_t launch_gather_runs(const aa_candidate* d_in, aa_candidate* d_out, const RunCopy* d_runs,
+                               int64_t nruns, cudaStream_t s);
+
+// Host-path candidate list: order the CTA runs (headers `heads`, records
+// d_cands[0, stored)) by (beam when by_beam, dm_index, t0) with a counting sort
+// of the headers, gather them in that order on the device and copy the ordered
+// records into `res` with one device-to-host copy.
+aa_status order_candidates(const aa_candidate* d_cands, int64_t stored, std::vector<CandChunk>& heads,
+                           bool by_beam, cudaStream_t s, aa_candidates* res);
+
 // ---------------------------------------------------- differentiable form --
 struct F32FwdArgs {
     const float* x;

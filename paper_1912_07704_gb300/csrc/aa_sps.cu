@@ -14,6 +14,7 @@
 //             The CTA then resolves each of its candidates' width (the
 //             smallest maximising w) from the series it staged, with the same
 //             arithmetic bit for bit.
+#include <algorithm>
 #include <cfloat>
 #include <cstdint>
 
@@ -618,6 +619,29 @@ __global__ void __launch_bounds__(NT, 2) sps_boxcar_batch_kernel(
 cudaError_t launch_sps_stats(const SpsArgs& a, cudaStream_t s) {
     if (a.nrows <= 0) return cudaSuccess;
     sps_stats_kernel<<<a.nrows, kStatsThreads, 0, s>>>(a, a.rsqrt_w);
+    return cudaGetLastError();
+}
+
+namespace {
+// One CTA per run; 16-byte records copied as uint4.
+__global__ void __launch_bounds__(256) gather_runs_kernel(const uint4* __restrict__ in,
+                                                          uint4* __restrict__ out,
+                                                          const RunCopy* __restrict__ runs,
+                                                          int64_t nruns) {
+    for (int64_t r = blockIdx.x; r < nruns; r += gridDim.x) {
+        const RunCopy rc = runs[r];
+        for (int64_t k = threadIdx.x; k < rc.n; k += blockDim.x) out[rc.dst + k] = in[rc.src + k];
+    }
+}
+}  // namespace
+
+cudaError_t launch_gather_runs(const aa_candidate* d_in, aa_candidate* d_out, const RunCopy* d_runs,
+                               int64_t nruns, cudaStream_t s) {
+    if (nruns <= 0) return cudaSuccess;
+    static_assert(sizeof(aa_candidate) == sizeof(uint4), "candidate records are 16 bytes");
+    const unsigned grid = (unsigned)std::min<int64_t>(nruns, 152 * 16);
+    gather_runs_kernel<<<grid, 256, 0, s>>>(reinterpret_cast<const uint4*>(d_in),
+                                            reinterpret_cast<uint4*>(d_out), d_runs, nruns);
     return cudaGetLastError();
 }
 
