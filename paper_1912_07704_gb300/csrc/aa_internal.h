@@ -81,7 +81,6 @@ struct RangePlan {
     bool grouped_ok = false;  // the grouped tables exist (spans fit)
     int gcc = 0;           // channels per chunk
     int gz = 0;            // group sums held in shared memory at once
-    int grwx = 0;          // bytes per staged channel row
     int gzw = 0;           // 32-bit words per group-sum copy
     int gflush = 1;        // chunks between SWAR flushes
     int gnj = 3;           // 256-sample blocks covering kGroupTau + span_max
@@ -200,9 +199,9 @@ struct DedispArgs {
     int rw, cc, nstage, flush, elem;
     size_t smem;
     unsigned* err;
-    // grouped strategy (used when grouped != 0; cc/nstage/smem then describe it)
+    // grouped strategy (used when grouped != 0; cc and smem then describe it)
     int grouped;
-    int gz, grwx, gzw, gflush, gnj;  // gnj: 256-sample blocks of the longest group sum
+    int gz, gzw, gflush, gnj;  // gnj: 256-sample blocks of the longest group sum
     const GroupRec* grec;
     const GroupDesc* gdesc;
     const GroupMember* gmem;

@@ -124,7 +124,6 @@ static void build_groups(RangePlan& r, int C) {
     }
     r.gcc = gcc;
     r.gz = gz;
-    r.grwx = 0;
     r.gzw = gzw;
     r.gflush = std::max(1, lane_max / gcc);
     r.gnj = (kGroupTau + r.span_max + 255) / 256;
@@ -143,7 +142,6 @@ void fill_strategy(DedispArgs& a, const RangePlan& r) {
         a.nstage = 2;
         a.smem = r.gsmem;
         a.gz = r.gz;
-        a.grwx = r.grwx;
         a.gzw = r.gzw;
         a.gflush = r.gflush;
         a.gnj = r.gnj;
@@ -155,7 +153,7 @@ void fill_strategy(DedispArgs& a, const RangePlan& r) {
         a.cc = r.cc;
         a.nstage = r.nstage;
         a.smem = r.smem;
-        a.gz = a.grwx = a.gzw = a.gflush = a.gnj = 0;
+        a.gz = a.gzw = a.gflush = a.gnj = 0;
         a.grec = nullptr;
         a.gdesc = nullptr;
         a.gmem = nullptr;
