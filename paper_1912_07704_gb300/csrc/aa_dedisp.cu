@@ -380,10 +380,8 @@ __device__ __forceinline__ void dedisperse_grouped_block(const DedispArgs& a, in
     const int64_t pitch_b = a.in_pitch * EB;
     const GroupRec* recs = a.grec + (size_t)dmb * nchunks;
     const GroupMember* mems = a.gmem + (size_t)dmb * nchunks * gcc;
-    // units: warp w takes u = w, w + 16, ..; (group, block) = (u / nj, u % nj)
-    // stepped without dividing
-    const int gstep = kDedispWarps / nj, jstep = kDedispWarps - gstep * nj;
-    const int gi0 = warp / nj, j0 = warp - gi0 * nj;
+    // tail units: gtl lanes per group (a power of two), gpt groups per warp
+    const int gtl = a.gtl, gtl_log = gtl ? __ffs(gtl) - 1 : 0, gpt = gtl ? 32 / gtl : 1;
 
     uint32_t acc[QW];
     uint32_t tot[2 * QW];
@@ -414,19 +412,37 @@ __device__ __forceinline__ void dedisperse_grouped_block(const DedispArgs& a, in
                 const int dl = g.delta[warp];
                 g_p2 = (lane * 2 + (dl & 1)) * gzw + (dl >> 1);
             }
-            // ---- phase 1: group sums of this batch
+            // ---- phase 1: group sums of this batch.  With a.gtl > 0: two full
+            // units per group (samples 0..511), then tail units that cover the
+            // samples past 511 of 32 / gtl groups at once (gtl lanes each);
+            // otherwise gnj full units per group.
             {
-                const int nunits = (ge - gb) * nj;
-                int gi = gi0, j = j0;
+                const int ng = ge - gb;
+                const int nmain = gtl ? 2 * ng : ng * nj;
+                const int nunits = gtl ? nmain + (ng + gpt - 1) / gpt : nmain;
                 for (int u = warp; u < nunits; u += kDedispWarps) {
-                    const uint32_t ms = __shfl_sync(0xffffffffu, g_ms, gi);
-                    const int zlen = T + (int)__shfl_sync(0xffffffffu, g_span, gi);
+                    int gi, idx;  // this lane's group and sample block (samples 8 idx .. 8 idx + 7)
+                    if (gtl) {
+                        if (u < nmain) {
+                            gi = u >> 1;
+                            idx = 32 * (u & 1) + lane;
+                        } else {
+                            gi = (u - nmain) * gpt + (lane >> gtl_log);
+                            idx = 64 + (lane & (gtl - 1));
+                        }
+                    } else {
+                        gi = u / nj;
+                        idx = 32 * (u - gi * nj) + lane;
+                    }
+                    const bool gvalid = gi < ng;
+                    const int gs = gvalid ? gi : 0;
+                    const uint32_t ms = __shfl_sync(0xffffffffu, g_ms, gs);
+                    const int zlen = T + (int)__shfl_sync(0xffffffffu, g_span, gs);
                     const int mstart = (int)(ms & 0xffffu), mend = mstart + (int)(ms >> 16);
-                    uint32_t* zA = zs + gi * 2 * gzw;
+                    uint32_t* zA = zs + gs * 2 * gzw;
                     uint32_t* zB = zA + gzw;
-                    const int idx = 32 * j + lane;  // this lane: samples 8 idx .. 8 idx + 7
                     uint32_t A0 = 0, A1 = 0, A2 = 0, A3 = 0, E = 0;  // (z0,z1) .. (z6,z7), z8
-                    if (8 * idx < zlen) {
+                    if (gvalid && 8 * idx < zlen) {
 #pragma unroll 2
                         for (int m = mstart; m < mend; ++m) {
                             const int2 rm = __ldg(reinterpret_cast<const int2*>(mk + m));  // (s0, ch | span << 16)
@@ -464,12 +480,6 @@ __device__ __forceinline__ void dedisperse_grouped_block(const DedispArgs& a, in
                         *reinterpret_cast<uint4*>(zB + 4 * idx) =
                             make_uint4(__byte_perm(A0, A1, 0x5432), __byte_perm(A1, A2, 0x5432),
                                        __byte_perm(A2, A3, 0x5432), __byte_perm(A3, E, 0x5432));
-                    }
-                    gi += gstep;
-                    j += jstep;
-                    if (j >= nj) {
-                        j -= nj;
-                        ++gi;
                     }
                 }
             }

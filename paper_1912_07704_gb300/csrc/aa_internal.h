@@ -84,6 +84,7 @@ struct RangePlan {
     int gzw = 0;           // 32-bit words per group-sum copy
     int gflush = 1;        // chunks between SWAR flushes
     int gnj = 3;           // 256-sample blocks covering kGroupTau + span_max
+    int gtl = 0;           // lanes per group tail (power of two <= 32), 0: none
     size_t gsmem = 0;      // dynamic shared memory per CTA
     double gwork = 1.0;    // (group adds + pre-sum adds) / direct adds
     std::vector<GroupRec> grec;    // [ndm blocks][chunks]
@@ -202,6 +203,7 @@ struct DedispArgs {
     // grouped strategy (used when grouped != 0; cc and smem then describe it)
     int grouped;
     int gz, gzw, gflush, gnj;  // gnj: 256-sample blocks of the longest group sum
+    int gtl;                   // lanes per group in phase-1 tail units (0: no tail units)
     const GroupRec* grec;
     const GroupDesc* gdesc;
     const GroupMember* gmem;

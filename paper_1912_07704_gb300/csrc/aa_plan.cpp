@@ -127,6 +127,12 @@ static void build_groups(RangePlan& r, int C) {
     r.gzw = gzw;
     r.gflush = std::max(1, lane_max / gcc);
     r.gnj = (kGroupTau + r.span_max + 255) / 256;
+    {   // samples past kGroupTau (the span and the one sample after it) in lanes of 8
+        const int need = (r.span_max + 1 + 7) / 8;
+        int tl = 1;
+        while (tl < need) tl *= 2;
+        r.gtl = (kGroupTau % 256 == 0 && tl <= 32) ? tl : 0;
+    }
     r.gsmem = grouped_smem(gz, gzw);
     r.gwork = direct > 0 ? grouped / direct : 1.0;
     r.grouped_ok = true;
@@ -145,6 +151,7 @@ void fill_strategy(DedispArgs& a, const RangePlan& r) {
         a.gzw = r.gzw;
         a.gflush = r.gflush;
         a.gnj = r.gnj;
+        a.gtl = r.gtl;
         a.grec = r.d_grec;
         a.gdesc = r.d_gdesc;
         a.gmem = r.d_gmem;
@@ -153,7 +160,7 @@ void fill_strategy(DedispArgs& a, const RangePlan& r) {
         a.cc = r.cc;
         a.nstage = r.nstage;
         a.smem = r.smem;
-        a.gz = a.gzw = a.gflush = a.gnj = 0;
+        a.gz = a.gzw = a.gflush = a.gnj = a.gtl = 0;
         a.grec = nullptr;
         a.gdesc = nullptr;
         a.gmem = nullptr;
