@@ -459,6 +459,56 @@ aa_status aa_sps_search_device_noalloc(const aa_plan* plan, int64_t nsamp, const
                                        unsigned long long* d_count, float* d_snr_out,
                                        aa_stream_t stream);
 
+/* ------------------------------------- candidate post-processing (Sec. 1) */
+
+/* Device scratch (bytes) needed by aa_sps_order_device and
+ * aa_candidates_peaks2d_device for this plan, nsamp, max_width and candidate
+ * capacity.  AA_ERR_ARG for NULL/negative arguments, AA_ERR_CONFIG for a plan
+ * with more than 64 ranges. */
+aa_status aa_postprocess_ws_bytes(const aa_plan* plan, int64_t nsamp, int32_t max_width,
+                                  int64_t cand_capacity, size_t* bytes);
+
+/* Order the candidates of one aa_sps_search_device call on the device, by
+ * (dm_index, t) -- the order aa_sps_search returns on the host -- with no
+ * host round trip.
+ *   d_sps_ws      : the workspace that search used, unchanged since (its run
+ *                   headers describe where each boxcar CTA wrote its records);
+ *   d_cands, d_count, cand_capacity : that search's outputs and capacity;
+ *   d_sorted      : device array of cand_capacity records (16-byte aligned)
+ *                   receiving min(*d_count, cand_capacity) records in order;
+ *   d_tmp         : device scratch (16-byte aligned) of tmp_bytes >=
+ *                   aa_postprocess_ws_bytes.
+ * nsamp and max_width are those of the search.  Stream-ordered and
+ * asynchronous; AA_ERR_ARG on bad arguments, AA_ERR_CUDA if a launch fails. */
+aa_status aa_sps_order_device(const aa_plan* plan, int64_t nsamp, int32_t max_width,
+                              const void* d_sps_ws, const aa_candidate* d_cands,
+                              const unsigned long long* d_count, int64_t cand_capacity,
+                              aa_candidate* d_sorted, void* d_tmp, size_t tmp_bytes,
+                              aa_stream_t stream);
+
+/* 2-D peak filter over an ordered candidate list (as written by
+ * aa_sps_order_device).  The 1-D peak finding of the single-pulse search
+ * (Sec. 1) reports a pulse once per trial it shows in; this keeps the local
+ * maxima of the DM-time plane.  Candidate c is kept iff no other candidate o
+ * of the same range with |o.dm_index - c.dm_index| <= dm_radius and
+ * |o.t - c.t| <= t_radius has o.snr > c.snr, or o.snr == c.snr and
+ * (o.dm_index, o.t) < (c.dm_index, c.t) lexicographically.  Suppressed
+ * candidates still suppress (no chaining).
+ *   d_sorted, d_count, cand_capacity : the ordered list; its length is
+ *                   min(*d_count, cand_capacity);
+ *   d_peaks       : device array of cand_capacity records receiving the kept
+ *                   candidates, still in (dm_index, t) order;
+ *   d_npeaks      : device uint64 receiving their number;
+ *   d_tmp         : as for aa_sps_order_device (may be the same scratch).
+ * nsamp and max_width are those of the search.  AA_ERR_ARG for negative radii
+ * or bad arguments.  Stream-ordered and asynchronous. */
+aa_status aa_candidates_peaks2d_device(const aa_plan* plan, int64_t nsamp, int32_t max_width,
+                                       const aa_candidate* d_sorted,
+                                       const unsigned long long* d_count, int64_t cand_capacity,
+                                       int32_t dm_radius, int32_t t_radius, aa_candidate* d_peaks,
+                                       unsigned long long* d_npeaks, void* d_tmp, size_t tmp_bytes,
+                                       aa_stream_t stream);
+
 /* ------------------------------------------------------------- profiling -- */
 
 /* Kernel timing (tracing).  While enabled, every kernel the library launches

@@ -297,3 +297,48 @@ def adjoint_f64(x: np.ndarray, w: np.ndarray, shift_table: np.ndarray, gy: np.nd
 def mse_f64(x, w, shift_table, L, template) -> float:
     y = forward_f64(x, w, shift_table, L)
     return float(np.mean((y - template) ** 2)) if y.size else 0.0
+
+
+# ----------------------------------------------------------------------------
+# 2-D DM-time peak filter over a candidate list (post-processing of the
+# single-pulse search, Sec. 1: boxcar filters with peak finding)
+# ----------------------------------------------------------------------------
+
+def _beaten(dm, t, snr, c_dm, c_t, c_snr):
+    """Mask of the records that beat candidate c: a larger SNR, or the same
+    SNR and a smaller (dm_index, t) pair."""
+    smaller_key = (dm < c_dm) | ((dm == c_dm) & (t < c_t))
+    return (snr > c_snr) | ((snr == c_snr) & smaller_key)
+
+
+def peaks2d(recs: np.ndarray, dm_radius: int, t_radius: int, idx=None) -> np.ndarray:
+    """Keep-mask of the 2-D peak filter for the records `idx` (default all).
+
+    recs: structured array with fields dm_index, t, range, snr (any order; the
+    SNRs are compared as stored, float32).  Candidate c is kept iff no other
+    record of the same range within +-dm_radius trials and +-t_radius samples
+    beats it.  Brute force per candidate; when recs is sorted by dm_index the
+    records are first narrowed to the candidate's DM window with a binary
+    search (a plain lookup), otherwise every record is examined.
+    """
+    dm = recs["dm_index"].astype(np.int64)
+    t = recs["t"].astype(np.int64)
+    rg = recs["range"].astype(np.int64)
+    snr = recs["snr"].astype(np.float32)
+    n = dm.size
+    idx = np.arange(n) if idx is None else np.asarray(idx, dtype=np.int64)
+    by_dm = n < 2 or bool(np.all(dm[1:] >= dm[:-1]))
+    keep = np.ones(idx.size, bool)
+    for k, i in enumerate(idx.tolist()):
+        if by_dm:
+            a = int(np.searchsorted(dm, dm[i] - dm_radius, side="left"))
+            b = int(np.searchsorted(dm, dm[i] + dm_radius, side="right"))
+        else:
+            a, b = 0, n
+        sl = slice(a, b)
+        near = ((rg[sl] == rg[i]) & (np.abs(dm[sl] - dm[i]) <= dm_radius)
+                & (np.abs(t[sl] - t[i]) <= t_radius))
+        near[i - a] = False  # a candidate does not suppress itself
+        beat = near & _beaten(dm[sl], t[sl], snr[sl], dm[i], t[i], snr[i])
+        keep[k] = not bool(beat.any())
+    return keep

@@ -121,6 +121,12 @@ _SIG = {
     "aa_fil_read_header": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(aa_fil_header)]),
     "aa_fil_read_block": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(aa_fil_header), _I64, _I64, _P]),
     "aa_corner_turn_device": (ctypes.c_int, [_P, _I64, _I32, _I64, _P, _I64, _P]),
+    "aa_postprocess_ws_bytes": (ctypes.c_int, [_P, _I64, _I32, _I64,
+                                               ctypes.POINTER(ctypes.c_size_t)]),
+    "aa_sps_order_device": (ctypes.c_int, [_P, _I64, _I32, _P, _P, _P, _I64, _P, _P,
+                                           ctypes.c_size_t, _P]),
+    "aa_candidates_peaks2d_device": (ctypes.c_int, [_P, _I64, _I32, _P, _P, _I64, _I32, _I32, _P,
+                                                    _P, _P, ctypes.c_size_t, _P]),
     "aa_sps_search_device_noalloc": (ctypes.c_int, [_P, _I64, _P, _I32, _F32, _P, _I64, _P, _P,
                                                     _P]),
     "aa_dedisperse_f32_device": (ctypes.c_int, [_P, _P, _I64, _I64, _P, _P, _P]),
@@ -303,6 +309,28 @@ def aa_corner_turn_device(d_tm: int, nsamp: int, nchans: int, tm_stride: int, d_
                           cm_pitch: int, stream: int = 0) -> None:
     check(lib().aa_corner_turn_device(d_tm, int(nsamp), int(nchans), int(tm_stride), d_cm,
                                       int(cm_pitch), stream), "aa_corner_turn_device")
+
+
+def aa_postprocess_ws_bytes(plan, nsamp: int, max_width: int, capacity: int) -> int:
+    out = ctypes.c_size_t(0)
+    check(lib().aa_postprocess_ws_bytes(plan, int(nsamp), int(max_width), int(capacity),
+                                        ctypes.byref(out)), "aa_postprocess_ws_bytes")
+    return out.value
+
+
+def aa_sps_order_device(plan, nsamp, max_width, d_sps_ws, d_cands, d_count, capacity, d_sorted,
+                        d_tmp, tmp_bytes, stream=0) -> None:
+    check(lib().aa_sps_order_device(plan, int(nsamp), int(max_width), d_sps_ws, d_cands, d_count,
+                                    int(capacity), d_sorted, d_tmp, int(tmp_bytes), stream),
+          "aa_sps_order_device")
+
+
+def aa_candidates_peaks2d_device(plan, nsamp, max_width, d_sorted, d_count, capacity, dm_radius,
+                                 t_radius, d_peaks, d_npeaks, d_tmp, tmp_bytes, stream=0) -> None:
+    check(lib().aa_candidates_peaks2d_device(plan, int(nsamp), int(max_width), d_sorted, d_count,
+                                             int(capacity), int(dm_radius), int(t_radius), d_peaks,
+                                             d_npeaks, d_tmp, int(tmp_bytes), stream),
+          "aa_candidates_peaks2d_device")
 
 
 def aa_profile_enable(on: bool) -> None:

@@ -155,6 +155,40 @@ class Plan:
                                  ws.data_ptr(), ws.numel(), _stream_handle(stream))
         return cands, count, snr_out
 
+    def postprocess_scratch(self, nsamp: int, max_width: int, capacity: int) -> torch.Tensor:
+        """Device scratch for sps_order_device / peaks2d_device."""
+        self.bind()
+        n = abi.aa_postprocess_ws_bytes(self.handle, nsamp, max_width, capacity)
+        return torch.empty(max(n, 256), dtype=torch.uint8, device="cuda")
+
+    def sps_order_device(self, nsamp: int, max_width: int, ws: torch.Tensor, cands: torch.Tensor,
+                         count: torch.Tensor, capacity: int, out=None, tmp=None, stream=None):
+        """Candidates of the search that used workspace `ws`, in (dm_index, t)
+        order, into `out` (uint8 [capacity*16]); returns `out`."""
+        self.bind()
+        out = (torch.empty(max(capacity, 1) * 16, dtype=torch.uint8, device="cuda")
+               if out is None else out)
+        tmp = self.postprocess_scratch(nsamp, max_width, capacity) if tmp is None else tmp
+        abi.aa_sps_order_device(self.handle, nsamp, max_width, ws.data_ptr(), cands.data_ptr(),
+                                count.data_ptr(), capacity, out.data_ptr(), tmp.data_ptr(),
+                                tmp.numel(), _stream_handle(stream))
+        return out
+
+    def peaks2d_device(self, nsamp: int, max_width: int, sorted_cands: torch.Tensor,
+                       count: torch.Tensor, capacity: int, dm_radius: int, t_radius: int,
+                       out=None, npeaks=None, tmp=None, stream=None):
+        """2-D DM-time peaks of an ordered list; returns (out, npeaks)."""
+        self.bind()
+        out = (torch.empty(max(capacity, 1) * 16, dtype=torch.uint8, device="cuda")
+               if out is None else out)
+        npeaks = torch.zeros(1, dtype=torch.int64, device="cuda") if npeaks is None else npeaks
+        tmp = self.postprocess_scratch(nsamp, max_width, capacity) if tmp is None else tmp
+        abi.aa_candidates_peaks2d_device(self.handle, nsamp, max_width, sorted_cands.data_ptr(),
+                                         count.data_ptr(), capacity, dm_radius, t_radius,
+                                         out.data_ptr(), npeaks.data_ptr(), tmp.data_ptr(),
+                                         tmp.numel(), _stream_handle(stream))
+        return out, npeaks
+
     # differentiable form ------------------------------------------------------
     def f32_forward(self, x: torch.Tensor, w: torch.Tensor, out=None, stream=None) -> torch.Tensor:
         """y = sum_c w_c x[c][t + s(c,d)] for float x [nchans][>= nsamp] (row

@@ -168,7 +168,7 @@ constexpr int64_t kEvaluatedOffset = 16;     // evaluated width-samples counter
 // ------------------------------------------------------------- profiling --
 enum KernelId {
     kKDecimate = 0, kKDedispU8, kKDedispU16, kKRsqrt, kKStats, kKBoxcar, kKF32Fwd, kKF32Adj,
-    kKCornerTurn, kNumKernels
+    kKCornerTurn, kKOrder, kKPeaks2d, kNumKernels
 };
 
 // RAII: records CUDA events around a launch on `s` while profiling is on.

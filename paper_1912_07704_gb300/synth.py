@@ -219,3 +219,68 @@ def batched_beams(n: int = 32, seed: int = PULSE_SEED + 2) -> list:
         beams.append(Workload(f"beam{i}-{C}ch-{T}", C, 1508.0, foff, 64e-6, T,
                               clipped_ska_ranges(dm_max), 8192, 6.0, 10 + i))
     return beams
+
+
+# Record layout of a single-pulse candidate (16 bytes, the library's format).
+CANDIDATE_RECORD = np.dtype([("dm_index", "<u4"), ("t", "<u4"), ("width", "<u2"),
+                             ("range", "u1"), ("reserved", "u1"), ("snr", "<f4")])
+
+
+def candidate_field(range_ndm: Sequence[int], range_len: Sequence[int], n_pulses: int,
+                    n_noise: int, seed: int, snr_quantum: float = 0.0,
+                    threshold: float = 6.0) -> np.ndarray:
+    """Seeded synthetic candidate list with the structure of a single-pulse
+    search's output, sorted by (dm_index, t), one record per (dm_index, t).
+
+    * pulses: a range r, a centre trial and time, a peak SNR U[8, 40] and a
+      half-extent h U{1..40} trials; trial c+k carries a record at
+      t_c + round(slope*k) (slope U[-3, 3]) with SNR falling linearly to
+      the threshold at |k| = h + 1, plus 0-3 weaker side records per trial at
+      gaps U{2..24} samples;
+    * noise: uniform (range, trial, t) with SNR threshold + Exp(0.5);
+    * snr_quantum > 0 rounds every SNR to a multiple of it (equal SNRs);
+    * dm_index is global: the ranges' trials concatenated in order.
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    offs = np.concatenate([[0], np.cumsum(range_ndm)]).astype(np.int64)
+    recs = []  # (dm_global, t, width, range, snr)
+
+    def add(r, d, t, snr):
+        if 0 <= d < range_ndm[r] and 0 <= t < range_len[r]:
+            recs.append((int(offs[r] + d), int(t), int(rng.integers(1, 64)), r, float(snr)))
+
+    live = [r for r in range(len(range_ndm)) if range_ndm[r] > 0 and range_len[r] > 0]
+    for _ in range(n_pulses if live else 0):
+        r = int(rng.choice(live))
+        c = int(rng.integers(0, range_ndm[r]))
+        tc = int(rng.integers(0, range_len[r]))
+        peak = rng.uniform(8.0, 40.0)
+        h = int(rng.integers(1, 41))
+        slope = rng.uniform(-3.0, 3.0)
+        for k in range(-h, h + 1):
+            s = threshold + (peak - threshold) * (1.0 - abs(k) / (h + 1)) + rng.normal(0, 0.3)
+            t = tc + int(round(slope * k))
+            add(r, c + k, t, s)
+            for _ in range(int(rng.integers(0, 4))):
+                add(r, c + k, t + int(rng.choice([-1, 1])) * int(rng.integers(2, 25)),
+                    threshold + rng.uniform(0.0, 1.0) * (s - threshold))
+    for _ in range(n_noise if live else 0):
+        r = int(rng.choice(live))
+        add(r, int(rng.integers(0, range_ndm[r])), int(rng.integers(0, range_len[r])),
+            threshold + rng.exponential(0.5))
+    out = np.zeros(len(recs), dtype=CANDIDATE_RECORD)
+    if recs:
+        a = np.array(recs, dtype=np.float64)
+        out["dm_index"] = a[:, 0].astype(np.uint32)
+        out["t"] = a[:, 1].astype(np.uint32)
+        out["width"] = a[:, 2].astype(np.uint16)
+        out["range"] = a[:, 3].astype(np.uint8)
+        snr = a[:, 4]
+        if snr_quantum > 0:
+            snr = np.round(snr / snr_quantum) * snr_quantum
+        out["snr"] = snr.astype(np.float32)
+    # one record per (dm_index, t): the first drawn
+    key = out["dm_index"].astype(np.int64) * (1 << 32) + out["t"].astype(np.int64)
+    _, first = np.unique(key, return_index=True)
+    out = out[np.sort(first)]
+    return out[np.lexsort((out["t"], out["dm_index"]))]

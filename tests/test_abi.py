@@ -95,3 +95,21 @@ def test_query_does_not_touch_device():
     assert info.table_bytes >= 4250 * 4096 * 4
     assert info.sps_ws_bytes >= 4250 * 8192 * 8
     p.close()
+
+
+def test_postprocess_scratch_and_argument_checks():
+    p = Plan(100, 1400.0, -2.0, 64e-6, [(0.0, 3.0, 37, 1), (100.0, 5.0, 9, 3)])
+    small = abi.aa_postprocess_ws_bytes(p.handle, 5000, 16, 1000)
+    large = abi.aa_postprocess_ws_bytes(p.handle, 5000, 16, 1 << 20)
+    assert 256 < small < large
+    # 8 bytes per candidate at least (the keep flags), and no more than ~9
+    assert 8 * (1 << 20) <= large - small + 8 * 1000 < 9 * (1 << 20)
+    assert abi.aa_postprocess_ws_bytes(p.handle, 0, 16, 0) >= 256
+    for args in [(5000, 0, 10), (-1, 16, 10), (5000, 16, -1)]:
+        with pytest.raises(abi.AAError):
+            abi.aa_postprocess_ws_bytes(p.handle, *args)
+    with pytest.raises(abi.AAError):  # NULL device pointers are rejected before any launch
+        abi.aa_sps_order_device(p.handle, 5000, 16, 0, 0, 0, 10, 0, 0, 1 << 20)
+    with pytest.raises(abi.AAError):  # negative radius
+        abi.aa_candidates_peaks2d_device(p.handle, 5000, 16, 1 << 12, 1 << 12, 10, -1, 4,
+                                         1 << 12, 1 << 12, 1 << 12, 1 << 20)

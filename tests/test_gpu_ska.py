@@ -1,7 +1,10 @@
 """Full-size 4096-channel, 2^20-sample, four-range plan with W = 8192, run
 exactly as bench.py runs it; the oracle checks sampled DM rows in full
 (dedispersion) and sampled time windows (boxcar SNR and candidates), and
-every strong injected pulse must be detected near its DM and arrival time."""
+every strong injected pulse must be detected near its DM and arrival time.
+The bench's post-processing runs on the same output: the device ordering must
+equal a numpy sort of the records, and the 2-D peak filter must agree with the
+oracle on sampled candidates."""
 import numpy as np
 import pytest
 import torch
@@ -9,10 +12,15 @@ import torch
 from gpu_common import check_snr_rows, compare_candidate_lists, oracle_candidates
 from paper_1912_07704_gb300 import synth
 from paper_1912_07704_gb300.api import Plan, candidates_from_device
+from paper_1912_07704_gb300.synth import CANDIDATE_RECORD
 
 pytestmark = pytest.mark.gpu
 
 W = synth.SKA_4096
+
+
+PEAK_DM_RADIUS, PEAK_T_RADIUS = 8, 256  # bench.py's 2-D peak window
+post = {}
 
 
 @pytest.fixture(scope="module")
@@ -27,10 +35,20 @@ def ska_run(oracle):
     # the bench configuration: no B output
     out = plan.dedisperse_device(x, nsamp)
     cap = 1 << 25
-    cands, count, _ = plan.sps_search_device(out, nsamp, W.max_width, W.threshold, cap)
+    ws = plan.alloc_workspace(plan.query(nsamp, W.max_width).sps_ws_bytes)
+    cands, count, _ = plan.sps_search_device(out, nsamp, W.max_width, W.threshold, cap, ws=ws)
     torch.cuda.synchronize()
     assert int(count.item()) <= cap, int(count.item())
     bench_cands = candidates_from_device(cands, count, cap)
+    # device ordering and 2-D peaks, as bench.py runs them
+    n = int(count.item())
+    srt = plan.sps_order_device(nsamp, W.max_width, ws, cands, count, cap)
+    peaks, npeaks = plan.peaks2d_device(nsamp, W.max_width, srt, count, cap, PEAK_DM_RADIUS,
+                                        PEAK_T_RADIUS)
+    torch.cuda.synchronize()
+    dev_sorted = srt[: n * 16].cpu().numpy().view(CANDIDATE_RECORD)
+    dev_peaks = peaks[: int(npeaks.item()) * 16].cpu().numpy().view(CANDIDATE_RECORD)
+    del srt, peaks, ws
     # the same call with the optional B(t) output
     snr = torch.full_like(out, float("nan"))
     cands2, count2, _ = plan.sps_search_device(out, nsamp, W.max_width, W.threshold, cap,
@@ -41,6 +59,7 @@ def ska_run(oracle):
     xh = x[:, :nsamp].cpu().numpy()
     del x, cands, cands2
     torch.cuda.empty_cache()
+    post["sorted"], post["peaks"] = dev_sorted, dev_peaks
     yield plan, xh, out, snr, bench_cands, snr_cands, pulses
     del out, snr
     torch.cuda.empty_cache()
@@ -112,3 +131,27 @@ def test_strong_pulses_detected(ska_run):
             assert len(sel) > 0, (p, r)
             checked += 1
     assert checked >= 5
+
+
+def test_device_order_full_size(ska_run):
+    bc = ska_run[4]
+    assert bc.size > 1 << 20
+    assert np.array_equal(post["sorted"], bc)
+
+
+def test_peaks2d_full_size_sampled(oracle, ska_run):
+    bc = ska_run[4]
+    pk = post["peaks"]
+    assert 0 < pk.size < bc.size
+    key = lambda a: a["dm_index"].astype(np.int64) * (1 << 32) + a["t"].astype(np.int64)
+    kb, kp = key(bc), key(pk)
+    assert np.all(np.diff(kp) > 0)  # ordered, and a subset of the list below
+    pos = np.searchsorted(kb, kp)
+    assert np.array_equal(bc[pos], pk)
+    rng = np.random.Generator(np.random.PCG64(77))
+    idx = np.unique(np.concatenate([rng.integers(0, bc.size, 3000), pos[:200], pos[-200:],
+                                    [int(np.argmax(bc["snr"]))]]))
+    want = oracle.peaks2d(bc, PEAK_DM_RADIUS, PEAK_T_RADIUS, idx)
+    got = np.isin(kb[idx], kp)
+    assert np.array_equal(got, want)
+    assert got[idx == int(np.argmax(bc["snr"]))].all()  # the strongest candidate survives
