@@ -30,6 +30,8 @@ struct RangeTable {
     int32_t dm_offset[kMaxRanges + 1];  // first global trial of each range (+ the total)
     int32_t ntiles[kMaxRanges];         // boxcar CTAs per trial
     int64_t slot_base[kMaxRanges];      // first run slot of each range
+    int32_t nbuckets[kMaxRanges];       // time buckets per trial (peak filter index)
+    int64_t bucket_base[kMaxRanges];    // first bucket entry of each range
 };
 
 __device__ __forceinline__ int range_of(const RangeTable& rt, uint32_t dm) {
@@ -194,41 +196,197 @@ __device__ __forceinline__ bool beats(const aa_candidate& o, const aa_candidate&
     return o.dm_index != c.dm_index ? o.dm_index < c.dm_index : o.t < c.t;
 }
 
-// flag[i] = 1 iff candidate i is a peak; last = flag[n - 1]
-__global__ void peak_flags_kernel(const aa_candidate* __restrict__ c, const unsigned long long* dn, int64_t cap,
-                                  const int64_t* __restrict__ row_start, const int64_t* __restrict__ row_end,
-                                  RangeTable rt, int32_t dm_radius, int32_t t_radius, int64_t* flag,
-                                  int64_t* last) {
+// Time-bucket index of the ordered list: for trial d of range r and bucket b
+// (kBucketShift-bit buckets of t, the last one open-ended), the offset from
+// the row's first record of its first record with t >= b << kBucketShift.
+// Every bucket of a non-empty row is written exactly once: a record fills the
+// buckets after its predecessor's, the row's last record the rest.
+constexpr int kBucketShift = 8;
+
+__device__ __forceinline__ uint32_t bucket_of(uint32_t t, int32_t nb) {
+    return min(t >> kBucketShift, (uint32_t)(nb - 1));
+}
+
+__global__ void bucket_index_kernel(const aa_candidate* __restrict__ c, const unsigned long long* dn, int64_t cap,
+                                    const int64_t* __restrict__ row_start, const int64_t* __restrict__ row_end,
+                                    RangeTable rt, uint32_t* __restrict__ first) {
     const int64_t n = live_count(dn, cap);
+    const uint32_t ndm = (uint32_t)rt.dm_offset[rt.n];
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const aa_candidate me = c[i];
-        bool peak = me.dm_index < (uint32_t)rt.dm_offset[rt.n];
+        if (me.dm_index >= ndm) continue;
+        const int r = range_of(rt, me.dm_index);
+        const int32_t nb = rt.nbuckets[r];
+        uint32_t* row = first + rt.bucket_base[r] + (int64_t)(me.dm_index - (uint32_t)rt.dm_offset[r]) * nb;
+        const int64_t rs = row_start[me.dm_index];
+        const uint32_t rel = (uint32_t)(i - rs);
+        const int64_t b = bucket_of(me.t, nb);
+        const int64_t bp = i == rs ? -1 : (int64_t)bucket_of(c[i - 1].t, nb);
+        for (int64_t k = bp + 1; k <= b; ++k) row[k] = rel;
+        if (i + 1 == row_end[me.dm_index]) {
+            const uint32_t len = (uint32_t)(row_end[me.dm_index] - rs);
+            for (int64_t k = b + 1; k < nb; ++k) row[k] = len;
+        }
+    }
+}
+
+// The peak test runs in two passes.  Pass 1, one thread per candidate,
+// visits rows from the candidate's own trial outwards and each row from the
+// candidate's time outwards, four records a side per load round, so that a
+// stronger neighbour (on the rising side of a pulse it is usually a few
+// samples away) ends the search early; a candidate still undecided after
+// kPass1Budget records is queued.  Pass 2 gives each queued candidate a warp
+// that walks every row's window 32 records at a time.  flag[i] = 1 iff
+// candidate i is a peak; last = flag[n - 1].
+constexpr int kPass1Budget = 24;
+constexpr int kSide = 4;
+
+struct PeakCtx {
+    int64_t dlo, dhi, tlo, thi, d0;
+    const uint32_t* rows;  // bucket entries of trial d at rows + d * nb
+    int32_t nb;
+};
+
+__device__ __forceinline__ PeakCtx peak_ctx(const RangeTable& rt, const uint32_t* first, const aa_candidate& me,
+                                            int32_t dm_radius, int32_t t_radius) {
+    PeakCtx k;
+    const int r = range_of(rt, me.dm_index);
+    k.nb = rt.nbuckets[r];
+    k.d0 = me.dm_index;
+    k.dlo = max((int64_t)rt.dm_offset[r], k.d0 - dm_radius);
+    k.dhi = min((int64_t)rt.dm_offset[r + 1] - 1, k.d0 + dm_radius);
+    k.rows = first + rt.bucket_base[r] - (int64_t)rt.dm_offset[r] * k.nb;
+    k.tlo = (int64_t)me.t - t_radius;
+    k.thi = (int64_t)me.t + t_radius;
+    return k;
+}
+
+// First index of row d (records [rs, end)) with t >= tt: the time index
+// bounds it to one bucket, a binary search finds it there.
+__device__ __forceinline__ int64_t lower_t(const aa_candidate* __restrict__ c, const PeakCtx& k, int64_t d,
+                                           int64_t rs, int64_t end, int64_t tt) {
+    if (tt <= 0) return rs;
+    const uint32_t b = bucket_of((uint32_t)min(tt, (int64_t)UINT32_MAX), k.nb);
+    const uint32_t* row = k.rows + d * k.nb;
+    int64_t lo = rs + (int64_t)row[b];
+    int64_t hi = b + 1 < (uint32_t)k.nb ? rs + (int64_t)row[b + 1] : end;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if ((int64_t)c[mid].t < tt) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// trial visited k-th: d0, d0-1, d0+1, d0-2, d0+2, ...
+__device__ __forceinline__ int64_t kth_row(int64_t d0, int64_t k) { return (k & 1) ? d0 - (k + 1) / 2 : d0 + k / 2; }
+
+__global__ void __launch_bounds__(256) peak_pass1_kernel(const aa_candidate* __restrict__ c,
+                                                         const unsigned long long* dn, int64_t cap,
+                                                         const int64_t* __restrict__ row_start,
+                                                         const int64_t* __restrict__ row_end,
+                                                         const uint32_t* __restrict__ first, RangeTable rt,
+                                                         int32_t dm_radius, int32_t t_radius, int64_t* flag,
+                                                         int64_t* last, int64_t* queue,
+                                                         unsigned long long* nqueue) {
+    const int64_t n = live_count(dn, cap);
+    const uint32_t ndm = (uint32_t)rt.dm_offset[rt.n];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const aa_candidate me = c[i];
+        bool peak = me.dm_index < ndm;
+        bool decided = true;
         if (peak) {
-            const int r = range_of(rt, me.dm_index);
-            const int64_t dlo = max((int64_t)rt.dm_offset[r], (int64_t)me.dm_index - dm_radius);
-            const int64_t dhi = min((int64_t)rt.dm_offset[r + 1] - 1, (int64_t)me.dm_index + dm_radius);
-            const int64_t tlo = (int64_t)me.t - t_radius, thi = (int64_t)me.t + t_radius;
-            for (int64_t d = dlo; d <= dhi && peak; ++d) {
-                int64_t lo = row_start[d];
-                const int64_t end = row_end[d];
-                int64_t hi = end;
-                while (lo < hi) {  // first candidate of row d with t >= tlo
-                    const int64_t mid = (lo + hi) >> 1;
-                    if ((int64_t)c[mid].t < tlo) lo = mid + 1;
-                    else hi = mid;
-                }
-                for (int64_t j = lo; j < end; ++j) {
-                    const aa_candidate o = c[j];
-                    if ((int64_t)o.t > thi) break;
-                    if (j != i && beats(o, me)) {
-                        peak = false;
+            const PeakCtx k = peak_ctx(rt, first, me, dm_radius, t_radius);
+            int budget = kPass1Budget;
+            for (int64_t kk = 0; peak && decided && kk <= 2 * (int64_t)dm_radius; ++kk) {
+                const int64_t d = kth_row(k.d0, kk);
+                if (d < k.dlo || d > k.dhi) continue;
+                const int64_t rs = row_start[d], end = row_end[d];
+                if (rs == end) continue;
+                // in its own row the candidate itself is the first record with t >= its t
+                int64_t right = d == k.d0 ? i : lower_t(c, k, d, rs, end, (int64_t)me.t);
+                int64_t left = right - 1;
+                bool go_r = right < end, go_l = left >= rs;
+                while (go_r || go_l) {
+                    if (budget <= 0) {
+                        decided = false;
                         break;
                     }
+                    aa_candidate R[kSide], L[kSide];
+#pragma unroll
+                    for (int j = 0; j < kSide; ++j) {
+                        if (go_r && right + j < end) R[j] = c[right + j];
+                        if (go_l && left - j >= rs) L[j] = c[left - j];
+                    }
+#pragma unroll
+                    for (int j = 0; j < kSide; ++j) {
+                        if (go_r) {
+                            if (right + j >= end || (int64_t)R[j].t > k.thi) go_r = false;
+                            else if (right + j != i && beats(R[j], me)) peak = false;
+                        }
+                        if (go_l) {
+                            if (left - j < rs || (int64_t)L[j].t < k.tlo) go_l = false;
+                            else if (left - j != i && beats(L[j], me)) peak = false;
+                        }
+                    }
+                    if (!peak) break;
+                    right += kSide;
+                    left -= kSide;
+                    budget -= 2 * kSide;
                 }
             }
         }
-        flag[i] = peak ? 1 : 0;
-        if (i == n - 1) *last = peak ? 1 : 0;
+        if (!decided && peak) {
+            queue[atomicAdd(nqueue, 1ull)] = i;
+        } else {
+            flag[i] = peak ? 1 : 0;
+            if (i == n - 1) *last = peak ? 1 : 0;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) peak_pass2_kernel(const aa_candidate* __restrict__ c,
+                                                         const unsigned long long* dn, int64_t cap,
+                                                         const int64_t* __restrict__ row_start,
+                                                         const int64_t* __restrict__ row_end,
+                                                         const uint32_t* __restrict__ first, RangeTable rt,
+                                                         int32_t dm_radius, int32_t t_radius, int64_t* flag,
+                                                         int64_t* last, const int64_t* __restrict__ queue,
+                                                         const unsigned long long* nqueue) {
+    const int64_t n = live_count(dn, cap);
+    const int64_t nq = (int64_t)*nqueue;
+    const int lane = threadIdx.x & 31;
+    for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nq;
+         w += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        const int64_t i = queue[w];
+        const aa_candidate me = c[i];
+        const PeakCtx k = peak_ctx(rt, first, me, dm_radius, t_radius);
+        bool peak = true;
+        for (int64_t kk = 0; peak && kk <= 2 * (int64_t)dm_radius; ++kk) {
+            const int64_t d = kth_row(k.d0, kk);
+            if (d < k.dlo || d > k.dhi) continue;
+            const int64_t rs = row_start[d], end = row_end[d];
+            if (rs == end) continue;
+            // the window from its first record, 32 records per step
+            for (int64_t q0 = lower_t(c, k, d, rs, end, k.tlo); q0 < end; q0 += 32) {
+                const int64_t q = q0 + lane;
+                bool past = q >= end, beat = false;
+                if (!past) {
+                    const aa_candidate o = c[q];
+                    past = (int64_t)o.t > k.thi;
+                    beat = !past && (int64_t)o.t >= k.tlo && q != i && beats(o, me);
+                }
+                if (__any_sync(0xffffffffu, beat)) {
+                    peak = false;
+                    break;
+                }
+                if (__any_sync(0xffffffffu, past)) break;
+            }
+        }
+        if (lane == 0) {
+            flag[i] = peak ? 1 : 0;
+            if (i == n - 1) *last = peak ? 1 : 0;
+        }
     }
 }
 
@@ -249,18 +407,23 @@ __global__ void compact_kernel(const aa_candidate* __restrict__ c, const unsigne
     }
 }
 
-RangeTable range_table(const aa_plan& p, const Layout& L, int64_t& nslots) {
+RangeTable range_table(const aa_plan& p, const Layout& L, int64_t& nslots, int64_t& nbucket_entries) {
     RangeTable rt{};
     rt.n = (int32_t)p.ranges.size();
-    int64_t base = 0;
+    int64_t base = 0, bbase = 0;
     for (int r = 0; r < rt.n; ++r) {
+        const int64_t ndm = p.ranges[r].desc.ndm;
         rt.dm_offset[r] = p.ranges[r].dm_offset;
         rt.ntiles[r] = (int32_t)((L.length[r] + kSpsOwned - 1) / kSpsOwned);
         rt.slot_base[r] = base;
-        base += (int64_t)p.ranges[r].desc.ndm * rt.ntiles[r];
+        base += ndm * rt.ntiles[r];
+        rt.nbuckets[r] = (int32_t)std::max<int64_t>(1, (L.length[r] + (1 << kBucketShift) - 1) >> kBucketShift);
+        rt.bucket_base[r] = bbase;
+        bbase += ndm * rt.nbuckets[r];
     }
     rt.dm_offset[rt.n] = p.ndm_total;
     nslots = base;
+    nbucket_entries = bbase;
     return rt;
 }
 
@@ -284,10 +447,10 @@ aa_status check_post_args(const aa_plan* p, int64_t nsamp, int32_t max_width, in
 
 int64_t post_scratch_elems(const aa_plan& p, int64_t nsamp, int32_t max_width, int64_t cap) {
     const Layout L = make_layout(p, nsamp, max_width);
-    int64_t nslots = 0;
-    range_table(p, L, nslots);
+    int64_t nslots = 0, nbe = 0;
+    range_table(p, L, nslots, nbe);
     const int64_t ordering = 3 * nslots + scan_scratch(nslots);
-    const int64_t peaks = 2 * (int64_t)p.ndm_total + cap + 1 + scan_scratch(cap);
+    const int64_t peaks = 2 * (int64_t)p.ndm_total + 2 * cap + 2 + scan_scratch(cap) + (nbe + 1) / 2;
     return std::max(ordering, peaks);
 }
 
@@ -329,8 +492,8 @@ extern "C" aa_status aa_sps_order_device(const aa_plan* p, int64_t nsamp, int32_
         return AA_ERR_ARG;
     }
     const Layout L = make_layout(*p, nsamp, max_width);
-    int64_t nslots = 0;
-    const RangeTable rt = range_table(*p, L, nslots);
+    int64_t nslots = 0, nbe = 0;
+    const RangeTable rt = range_table(*p, L, nslots, nbe);
     if (cand_capacity == 0 || nslots == 0) return AA_OK;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     int64_t* cnt = static_cast<int64_t*>(d_tmp);
@@ -388,22 +551,35 @@ extern "C" aa_status aa_candidates_peaks2d_device(const aa_plan* p, int64_t nsam
         return e == cudaSuccess ? AA_OK : post_fail(e, "clear peak count");
     }
     const Layout L = make_layout(*p, nsamp, max_width);
-    int64_t nslots = 0;
-    const RangeTable rt = range_table(*p, L, nslots);
+    int64_t nslots = 0, nbe = 0;
+    const RangeTable rt = range_table(*p, L, nslots, nbe);
     const int64_t ndm = p->ndm_total;
     int64_t* row_start = static_cast<int64_t*>(d_tmp);
     int64_t* row_end = row_start + ndm;
     int64_t* flag = row_end + ndm;
     int64_t* last = flag + cand_capacity;
     int64_t* scratch = last + 1;
+    int64_t* queue = scratch + scan_scratch(cand_capacity);
+    unsigned long long* nqueue = reinterpret_cast<unsigned long long*>(queue + cand_capacity);
+    uint32_t* first = reinterpret_cast<uint32_t*>(queue + cand_capacity + 1);
     ProfScope prof(kKPeaks2d, s);
     if ((e = cudaMemsetAsync(row_start, 0, (size_t)(2 * ndm) * 8, s)) != cudaSuccess)
         return post_fail(e, "clear row index");
+    if ((e = cudaMemsetAsync(nqueue, 0, sizeof(unsigned long long), s)) != cudaSuccess)
+        return post_fail(e, "clear peak queue");
     row_index_kernel<<<grid_for(cand_capacity, 256), 256, 0, s>>>(d_sorted, d_count, cand_capacity,
                                                                   (int32_t)ndm, row_start, row_end);
     if ((e = cudaGetLastError()) != cudaSuccess) return post_fail(e, "row index");
-    peak_flags_kernel<<<grid_for(cand_capacity, 256), 256, 0, s>>>(d_sorted, d_count, cand_capacity, row_start,
-                                                                   row_end, rt, dm_radius, t_radius, flag, last);
+    bucket_index_kernel<<<grid_for(cand_capacity, 256), 256, 0, s>>>(d_sorted, d_count, cand_capacity, row_start,
+                                                                     row_end, rt, first);
+    if ((e = cudaGetLastError()) != cudaSuccess) return post_fail(e, "bucket index");
+    peak_pass1_kernel<<<grid_for(cand_capacity, 256), 256, 0, s>>>(d_sorted, d_count, cand_capacity, row_start,
+                                                                   row_end, first, rt, dm_radius, t_radius, flag,
+                                                                   last, queue, nqueue);
+    if ((e = cudaGetLastError()) != cudaSuccess) return post_fail(e, "peak flags");
+    peak_pass2_kernel<<<grid_for(cand_capacity * 32, 256), 256, 0, s>>>(d_sorted, d_count, cand_capacity,
+                                                                         row_start, row_end, first, rt, dm_radius,
+                                                                         t_radius, flag, last, queue, nqueue);
     if ((e = cudaGetLastError()) != cudaSuccess) return post_fail(e, "peak flags");
     if ((e = exclusive_scan(flag, d_count, cand_capacity, scratch, s)) != cudaSuccess)
         return post_fail(e, "scan peak flags");

@@ -102,8 +102,8 @@ def test_postprocess_scratch_and_argument_checks():
     small = abi.aa_postprocess_ws_bytes(p.handle, 5000, 16, 1000)
     large = abi.aa_postprocess_ws_bytes(p.handle, 5000, 16, 1 << 20)
     assert 256 < small < large
-    # 8 bytes per candidate at least (the keep flags), and no more than ~9
-    assert 8 * (1 << 20) <= large - small + 8 * 1000 < 9 * (1 << 20)
+    # 16 bytes per candidate (keep flag and work-queue entry) plus the scan's share
+    assert 16 * (1 << 20) <= large - small + 16 * 1000 < 17 * (1 << 20)
     assert abi.aa_postprocess_ws_bytes(p.handle, 0, 16, 0) >= 256
     for args in [(5000, 0, 10), (-1, 16, 10), (5000, 16, -1)]:
         with pytest.raises(abi.AAError):

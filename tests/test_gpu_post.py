@@ -124,3 +124,14 @@ def test_order_then_peaks_on_search_output(oracle):
     k = int(npeaks.item())
     got = peaks[: k * 16].cpu().numpy().view(synth.CANDIDATE_RECORD)
     assert np.array_equal(got, ref[oracle.peaks2d(ref, 3, 16)])
+
+
+def test_peaks2d_times_past_series_end(oracle):
+    """Records with t beyond a range's series length (not produced by the
+    search, but a valid list): the time index's last bucket is open-ended."""
+    plan, T, f = _plan_field(33, 30, 5000, 0.25)
+    f["t"] = f["t"] * 3 + 5
+    f = f[np.lexsort((f["t"], f["dm_index"]))]
+    for R, Tr in [(2, 40), (5, 700)]:
+        got = _peaks_gpu(plan, T, 64, f, f.size, R, Tr)
+        assert np.array_equal(got, f[oracle.peaks2d(f, R, Tr)])
