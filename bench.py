@@ -262,6 +262,9 @@ def bench_ours(args):
         for r in range(len(w.ranges)):
             plan.set_strategy(r, abi.AA_DEDISP_GROUPED if args.strategy == "grouped"
                               else abi.AA_DEDISP_DIRECT)
+    if args.sps_clip:
+        c16, iters = (int(v) for v in args.sps_clip.split(","))
+        plan.set_sps_clip(c16, iters)
     plan.bind(local)
     info = plan.query(w.nsamp, w.max_width)
     x = build_input(plan, w, "cuda")
@@ -420,6 +423,9 @@ def bench_ours(args):
             "config": {"workload": w.name, "nchans": w.nchans, "nsamp": w.nsamp,
                        "dm_trials": sum(g.ndm for g in alg["lay"]), "max_width": w.max_width,
                        "threshold": w.threshold, "parallelism": f"beams x{ws}",
+                       "statistics": (f"k-sigma clipped, k = {args.sps_clip.split(',')[0]}/16, "
+                                      f"<= {args.sps_clip.split(',')[1]} passes"
+                                      if args.sps_clip else "plain mean and sigma"),
                        "dedispersion": [("grouped" if abi.aa_plan_range(plan.handle, nsamp, r).strategy
                                          else "direct") for r in range(len(w.ranges))],
                        "l2": (f"inputs larger than L2 ({alg['in_bytes'] / 1e9:.2f} GB filterbank, "
@@ -737,6 +743,8 @@ def main():
     ap.add_argument("--stream-chunks", type=int, default=6)
     ap.add_argument("--strategy", choices=["auto", "direct", "grouped"], default="auto",
                     help="dedispersion strategy of every range (auto: the plan's choice)")
+    ap.add_argument("--sps-clip", default="",
+                    help="C16,ITERS: k-sigma clipped statistics (k = C16/16), e.g. 48,4")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

@@ -253,6 +253,25 @@ typedef enum { AA_DEDISP_DIRECT = 0, AA_DEDISP_GROUPED = 1 } aa_dedisp_strategy;
  * Like aa_plan_autotune, call it while no work of the plan is in flight. */
 aa_status aa_plan_set_strategy(aa_plan* plan, int32_t r, int32_t strategy);
 
+/* Robust statistics for the single-pulse search (outlier rejection).  The
+ * mean and standard deviation that normalise each dedispersed series' SNR
+ * (Sec. 1: boxcar filters with peak finding) are by default those of all its
+ * samples.  With max_iters > 0 they are those of iterative k-sigma clipping,
+ * k = c16 / 16 with c16 in [1, 255]: the first pass takes every sample; each
+ * further pass keeps the samples y with |y - mu| <= k*sigma of the previous
+ * kept set (bounds inclusive, population sigma), decided exactly in integers
+ * as 256 (N y - S1)^2 <= c16^2 (N S2 - S1^2) over that set's count N,
+ * S1 = sum y and S2 = sum y^2; at most max_iters such passes, ending early at
+ * a fixed point (same N, S1, S2); a pass that keeps nothing is dropped.
+ * No counterpart in the paper's text, which cites the search method; the
+ * clipping rule is this library's.  max_iters = 0 restores the plain
+ * statistics.  Applies to the searches started and batches created after the
+ * call (device, host, no-allocation, streaming and batched paths).
+ * AA_ERR_ARG for max_iters outside [0, 64], or c16 outside [1, 255] with
+ * max_iters > 0.  While clipping is on, searches of series of 2^31 samples or
+ * more return AA_ERR_CONFIG. */
+aa_status aa_plan_set_sps_clip(aa_plan* plan, int32_t c16, int32_t max_iters);
+
 /* Time the dedispersion kernel of every range of a bound plan over a
  * synthetic probe input of nsamp_probe samples for the grouped strategy (if
  * available) and each feasible direct tile shape (channels per shared-memory

@@ -21,7 +21,8 @@
  *   s(c,i)  = round_half_away(((K*DM_i)*Delta_c) / (tsamp*dec)),  K = 4.148808e3
  *   x_r[c][j] = sum_{k<dec} x[c][j*dec+k],  j < floor(T/dec)
  *   y[i][t]   = sum_c x_r[c][t + s(c,i)],   t < L = floor(T/dec) - max s
- *   mu, sigma = population mean / std of y[i][0..L)
+ *   mu, sigma = population mean / std of y[i][0..L)  (optionally of the
+ *               samples kept by iterative k-sigma clipping, see below)
  *   SNR_w(t)  = (sum_{k<w} y[t+k] - w*mu) / (sigma*sqrt(w)),  1 <= w <= min(W, L-t)
  *   B(t)      = max_w SNR_w(t)  (smallest w on ties)
  *   peak at t iff B(t) >= thr and B(t) > B(t-1) and B(t) >= B(t+1)
@@ -128,6 +129,73 @@ void oracle_moments(const int64_t* y, int64_t n, double* mu, double* sigma)
     }
     *mu = m;
     *sigma = sqrt(ss / (double)n);
+}
+
+/* Robust mean / standard deviation by iterative k-sigma clipping (outlier
+ * rejection for the single-pulse search's statistics), k = c16/16, inclusive
+ * bounds, population sigma.  Pass 0 takes every sample; each clipping pass
+ * keeps the samples with |y - mu| <= k*sigma of the previous kept set.  With
+ * N, S1 = sum y and S2 = sum y^2 of that set, mu = S1/N and
+ * sigma = sqrt(N*S2 - S1^2)/N, so (multiplying by 16N and squaring, both
+ * sides being >= 0) the test is decided exactly in integers:
+ *     256*(N*y - S1)^2 <= c16^2 * (N*S2 - S1^2).
+ * At most max_iters clipping passes; a pass that keeps nothing is dropped and
+ * ends the iteration; a pass whose kept set has the same (N, S1, S2) as the
+ * previous one is a fixed point (the next pass would keep the same set) and
+ * ends it too.  mu, sigma: two-pass FP64 over the final kept set. */
+void oracle_moments_clipped(const int64_t* y, int64_t n, int32_t c16, int32_t max_iters,
+                            double* mu, double* sigma, int64_t* nkept)
+{
+    *mu = 0.0;
+    *sigma = 0.0;
+    *nkept = 0;
+    if (n <= 0) return;
+    unsigned char* keep = (unsigned char*)malloc((size_t)n);
+    unsigned char* next = (unsigned char*)malloc((size_t)n);
+    if (!keep || !next) { free(keep); free(next); return; }
+    __int128 N = 0, S1 = 0, S2 = 0;
+    for (int64_t t = 0; t < n; ++t) {
+        keep[t] = 1;
+        N += 1;
+        S1 += y[t];
+        S2 += (__int128)y[t] * y[t];
+    }
+    for (int32_t it = 0; it < max_iters; ++it) {
+        const __int128 V = N * S2 - S1 * S1;
+        const __int128 R = (__int128)c16 * c16 * V;
+        __int128 N2 = 0, T1 = 0, T2 = 0;
+        for (int64_t t = 0; t < n; ++t) {
+            const __int128 d = N * y[t] - S1;
+            next[t] = 256 * d * d <= R;
+            if (next[t]) {
+                N2 += 1;
+                T1 += y[t];
+                T2 += (__int128)y[t] * y[t];
+            }
+        }
+        if (N2 == 0) break;
+        const int same = N2 == N && T1 == S1 && T2 == S2;
+        memcpy(keep, next, (size_t)n);
+        N = N2;
+        S1 = T1;
+        S2 = T2;
+        if (same) break;
+    }
+    int64_t cnt = 0, s = 0;
+    for (int64_t t = 0; t < n; ++t)
+        if (keep[t]) { ++cnt; s += y[t]; }
+    const double m = (double)s / (double)cnt;
+    double ss = 0.0;
+    for (int64_t t = 0; t < n; ++t)
+        if (keep[t]) {
+            const double d = (double)y[t] - m;
+            ss += d * d;
+        }
+    *mu = m;
+    *sigma = sqrt(ss / (double)cnt);
+    *nkept = cnt;
+    free(keep);
+    free(next);
 }
 
 /* Exhaustive boxcar search for t in [t0, t1) of a series of length n.

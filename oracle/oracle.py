@@ -68,6 +68,9 @@ def lib():
         L.oracle_dedisperse.restype = None
         L.oracle_moments.argtypes = [vp, i64, ctypes.POINTER(f64), ctypes.POINTER(f64)]
         L.oracle_moments.restype = None
+        L.oracle_moments_clipped.argtypes = [vp, i64, i32, i32, ctypes.POINTER(f64),
+                                             ctypes.POINTER(f64), ctypes.POINTER(i64)]
+        L.oracle_moments_clipped.restype = None
         L.oracle_boxcar.argtypes = [vp, i64, f64, f64, i32, i64, i64, vp, vp, vp]
         L.oracle_boxcar.restype = None
         L.oracle_peaks.argtypes = [vp, i64, f64, vp, i64]
@@ -191,6 +194,24 @@ def moments(y: np.ndarray):
     return mu.value, sg.value
 
 
+def moments_clipped(y: np.ndarray, c16: int, max_iters: int):
+    """(mu, sigma, kept) of iterative k-sigma clipping, k = c16/16."""
+    y = np.ascontiguousarray(y, dtype=np.int64)
+    mu, sg, nk = ctypes.c_double(), ctypes.c_double(), ctypes.c_int64()
+    lib().oracle_moments_clipped(_ptr(y), y.size, int(c16), int(max_iters), ctypes.byref(mu),
+                                 ctypes.byref(sg), ctypes.byref(nk))
+    return mu.value, sg.value, nk.value
+
+
+def row_moments(y: np.ndarray, clip=None):
+    """Plain moments, or clipped ones for clip = (c16, max_iters) with
+    max_iters > 0."""
+    if clip and clip[1] > 0:
+        mu, sg, _ = moments_clipped(y, clip[0], clip[1])
+        return mu, sg
+    return moments(y)
+
+
 def boxcar(y: np.ndarray, mu: float, sigma: float, W: int, t0: int = 0, t1: int | None = None):
     """(B, wbest, margin) for t in [t0, t1)."""
     y = np.ascontiguousarray(y, dtype=np.int64)
@@ -224,10 +245,11 @@ class Candidate:
 
 
 def search_row(y: np.ndarray, W: int, thr: float, dm_index: int, rng: int,
-               t_lo: int = 0, t_hi: int | None = None):
+               t_lo: int = 0, t_hi: int | None = None, clip=None):
     """Candidates of one DM series with t in [t_lo, t_hi).
 
     Returns (candidates, B, wbest, mu, sigma) with B/wbest over [t_lo, t_hi).
+    clip = (c16, max_iters) takes mu, sigma from iterative k-sigma clipping.
     Rows with sigma == 0 have B = 0 and no candidates.  Near-decision entries
     (|B - thr| < FRAGILE_THR, neighbour or width-argmax margin < FRAGILE_CMP)
     are flagged fragile; entries just below the threshold that could flip
@@ -236,7 +258,7 @@ def search_row(y: np.ndarray, W: int, thr: float, dm_index: int, rng: int,
     y = np.ascontiguousarray(y, dtype=np.int64)
     n = y.size
     t_hi = n if t_hi is None else min(t_hi, n)
-    mu, sigma = moments(y)
+    mu, sigma = row_moments(y, clip)
     a, b = max(0, t_lo - 1), min(n, t_hi + 1)
     B, wb, mg = boxcar(y, mu, sigma, W, a, b)
     cands = []

@@ -121,6 +121,7 @@ _SIG = {
     "aa_fil_read_header": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(aa_fil_header)]),
     "aa_fil_read_block": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(aa_fil_header), _I64, _I64, _P]),
     "aa_corner_turn_device": (ctypes.c_int, [_P, _I64, _I32, _I64, _P, _I64, _P]),
+    "aa_plan_set_sps_clip": (ctypes.c_int, [_P, _I32, _I32]),
     "aa_postprocess_ws_bytes": (ctypes.c_int, [_P, _I64, _I32, _I64,
                                                ctypes.POINTER(ctypes.c_size_t)]),
     "aa_sps_order_device": (ctypes.c_int, [_P, _I64, _I32, _P, _P, _P, _I64, _P, _P,
@@ -309,6 +310,10 @@ def aa_corner_turn_device(d_tm: int, nsamp: int, nchans: int, tm_stride: int, d_
                           cm_pitch: int, stream: int = 0) -> None:
     check(lib().aa_corner_turn_device(d_tm, int(nsamp), int(nchans), int(tm_stride), d_cm,
                                       int(cm_pitch), stream), "aa_corner_turn_device")
+
+
+def aa_plan_set_sps_clip(plan, c16: int, max_iters: int) -> None:
+    check(lib().aa_plan_set_sps_clip(plan, int(c16), int(max_iters)), "aa_plan_set_sps_clip")
 
 
 def aa_postprocess_ws_bytes(plan, nsamp: int, max_width: int, capacity: int) -> int:

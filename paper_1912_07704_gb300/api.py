@@ -95,6 +95,11 @@ class Plan:
     def shifts(self, r: int) -> np.ndarray:
         return abi.aa_plan_shifts(self.handle, r, self.ranges[r][2], self.nchans)
 
+    def set_sps_clip(self, c16: int, max_iters: int) -> None:
+        """k-sigma clipped statistics for later searches (k = c16/16,
+        max_iters passes; 0 = plain mean and sigma)."""
+        abi.aa_plan_set_sps_clip(self.handle, c16, max_iters)
+
     def set_strategy(self, r: int, strategy: int) -> None:
         """Dedispersion strategy of range r: abi.AA_DEDISP_DIRECT or
         abi.AA_DEDISP_GROUPED (same result, different grouping of the sums)."""

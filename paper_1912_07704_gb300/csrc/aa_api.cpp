@@ -269,6 +269,12 @@ aa_status aa_sps_search_device(const aa_plan* p, int64_t nsamp, const float* d_d
         set_error("workspace %zu bytes < required %lld", ws_bytes, (long long)L.sps_ws);
         return AA_ERR_ARG;
     }
+    if (p->clip_iters > 0)
+        for (int64_t len : L.length)
+            if (len >= (int64_t(1) << 31)) {  // keeps the clipping test inside 128-bit integers
+                set_error("k-sigma clipping supports series shorter than 2^31 samples");
+                return AA_ERR_CONFIG;
+            }
     if (!aligned(d_ws, 256) || (d_dd && !aligned(d_dd, 16)) || (d_snr_out && !aligned(d_snr_out, 16))) {
         set_error("d_ws must be 256-byte and d_dd/d_snr_out 16-byte aligned");
         return AA_ERR_ARG;
@@ -310,6 +316,8 @@ aa_status aa_sps_search_device(const aa_plan* p, int64_t nsamp, const float* d_d
         a.count = d_count;
         a.snr_out = d_snr_out ? d_snr_out + L.row_offset[r] : nullptr;
         a.prune = d_snr_out ? 0 : 1;  // B(t) everywhere requested: exhaustive
+        a.clip_c16 = p->clip_c16;
+        a.clip_iters = p->clip_iters;
         a.err = err;
         a.chunks = chunks;
         a.nchunks = nchunks;

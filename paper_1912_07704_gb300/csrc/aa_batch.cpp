@@ -121,6 +121,10 @@ aa_status aa_batch_create(aa_plan* const* plans, const int64_t* nsamps, int32_t 
     for (int i = 0; i < nbeams; ++i) {
         if (!plans[i]) { set_error("plan %d is NULL", i); return AA_ERR_ARG; }
         if (nsamps[i] < 0) { set_error("nsamp of beam %d is negative", i); return AA_ERR_ARG; }
+        if (plans[i]->clip_iters > 0 && nsamps[i] >= (int64_t(1) << 31)) {
+            set_error("beam %d: k-sigma clipping supports series shorter than 2^31 samples", i);
+            return AA_ERR_CONFIG;
+        }
         if (!plans[i]->ready) {
             aa_status st = aa_plan_bind(plans[i], dev);
             if (st != AA_OK) return st;
@@ -307,6 +311,8 @@ aa_status aa_batch_create(aa_plan* const* plans, const int64_t* nsamps, int32_t 
                 s.snr_out = nullptr;
                 s.err = b->d_err;
                 s.prune = 1;
+                s.clip_c16 = pl.clip_c16;
+                s.clip_iters = pl.clip_iters;
                 s.beam = bi;
                 s.chunks = b->d_chunks;
                 s.nchunks = &b->d_counts[1];

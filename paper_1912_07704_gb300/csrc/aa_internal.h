@@ -104,6 +104,9 @@ struct aa_plan {
     std::vector<int> decs;  // distinct decimations > 1, ascending
     int32_t ndm_total = 0;
     double dm_max = 0;
+    // single-pulse statistics: iterative k-sigma clipping, k = clip_c16 / 16,
+    // at most clip_iters clipping passes (0: plain mean and sigma)
+    int32_t clip_c16 = 0, clip_iters = 0;
     int device = -1;
     bool ready = false;
     void* d_tables = nullptr;
@@ -254,6 +257,8 @@ struct SpsArgs {
     float* snr_out;         // optional, row 0 of this range (same pitch)
     unsigned* err;
     int32_t prune;          // skip width blocks bounded below the threshold
+    int32_t clip_c16;       // k-sigma clipping of the statistics, k = clip_c16 / 16
+    int32_t clip_iters;     // clipping passes (0: plain statistics)
     int32_t beam;           // beam id stored in candidate records (batched mode)
     unsigned long long* evaluated;  // width-samples actually evaluated (instrumentation)
     CandChunk* chunks;      // chunk headers (all ranges)

@@ -528,6 +528,16 @@ aa_status aa_plan_set_strategy(aa_plan* p, int32_t r, int32_t strategy) {
     return AA_OK;
 }
 
+aa_status aa_plan_set_sps_clip(aa_plan* p, int32_t c16, int32_t max_iters) {
+    clear_error();
+    if (!p) { set_error("plan is NULL"); return AA_ERR_ARG; }
+    if (max_iters < 0 || max_iters > 64) { set_error("max_iters %d outside [0, 64]", max_iters); return AA_ERR_ARG; }
+    if (max_iters > 0 && (c16 < 1 || c16 > 255)) { set_error("c16 %d outside [1, 255]", c16); return AA_ERR_ARG; }
+    p->clip_c16 = max_iters > 0 ? c16 : 0;
+    p->clip_iters = max_iters;
+    return AA_OK;
+}
+
 aa_status aa_plan_shifts(const aa_plan* p, int32_t r, int32_t* out, int64_t cap) {
     clear_error();
     if (!p || !out) { set_error("plan/out is NULL"); return AA_ERR_ARG; }

@@ -48,55 +48,107 @@ __device__ __forceinline__ void add128(unsigned long long& hi, unsigned long lon
 constexpr int kStatsThreads = 512;
 
 // Statistics of one series (row) and its width table; whole CTA.
+//
+// Exact integer sums N, S1 = sum y, S2 = sum y^2 (128-bit) over the kept
+// samples; pass 0 keeps every sample.  With k-sigma clipping (k = c16/16),
+// each further pass keeps the samples with |y - mu| <= k sigma of the previous
+// set, i.e. (times 16N, squared) 256 (N y - S1)^2 <= c16^2 (N S2 - S1^2),
+// decided exactly in 128-bit integers; it stops after clip_iters passes, at a
+// pass keeping nothing (dropped) or at a fixed point (same N, S1, S2).
 __device__ __forceinline__ void stats_row(const SpsArgs& a, const double* rsw, int row) {
-    __shared__ long long s1w[kStatsThreads / 32];
-    __shared__ unsigned long long hiw[kStatsThreads / 32], low[kStatsThreads / 32];
+    constexpr int NW = kStatsThreads / 32;
+    __shared__ long long s1w[NW], cw[NW];
+    __shared__ unsigned long long hiw[NW], low[NW];
+    __shared__ long long sh_N, sh_S1;           // sums of the accepted set
+    __shared__ unsigned long long sh_H, sh_L;   // its S2 (high, low words)
+    __shared__ unsigned long long sh_Rh, sh_Rl; // clipping bound c16^2 (N S2 - S1^2)
+    __shared__ int sh_go;
     __shared__ double sh_f, sh_inv;
     const float* y = a.dd + (int64_t)row * a.pitch;
     const int64_t n = a.length;
-    long long s1 = 0;
-    unsigned long long hi = 0, lo = 0;
-    for (int64_t i = threadIdx.x; i < n; i += kStatsThreads) {
-        const long long v = (long long)y[i];
-        s1 += v;
-        add128(hi, lo, 0ull, (unsigned long long)(v * v));
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
-        const unsigned long long h2 = __shfl_xor_sync(0xffffffffu, hi, o);
-        const unsigned long long l2 = __shfl_xor_sync(0xffffffffu, lo, o);
-        add128(hi, lo, h2, l2);
-    }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (lane == 0) {
-        s1w[warp] = s1;
-        hiw[warp] = hi;
-        low[warp] = lo;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        long long S1 = 0;
-        unsigned long long H = 0, Lo = 0;
-        for (int w = 0; w < kStatsThreads / 32; ++w) {
-            S1 += s1w[w];
-            add128(H, Lo, hiw[w], low[w]);
+    const int iters = a.clip_iters;
+    for (int pass = 0; pass <= iters; ++pass) {
+        const bool clip = pass > 0;
+        const long long N = clip ? sh_N : 0, S1p = clip ? sh_S1 : 0;
+        const unsigned __int128 R = clip ? (((unsigned __int128)sh_Rh << 64) | sh_Rl) : 0;
+        long long cnt = 0, s1 = 0;
+        unsigned long long hi = 0, lo = 0;
+        for (int64_t i = threadIdx.x; i < n; i += kStatsThreads) {
+            const long long v = (long long)y[i];
+            if (clip) {
+                const long long d = N * v - S1p;  // |d| < 2^56 (N < 2^31, |v| < 2^24)
+                const unsigned long long ad = (unsigned long long)(d < 0 ? -d : d);
+                if ((((unsigned __int128)ad * ad) << 8) > R) continue;
+            }
+            ++cnt;
+            s1 += v;
+            add128(hi, lo, 0ull, (unsigned long long)(v * v));
         }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+            s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+            const unsigned long long h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+            const unsigned long long l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+            add128(hi, lo, h2, l2);
+        }
+        if (lane == 0) {
+            cw[warp] = cnt;
+            s1w[warp] = s1;
+            hiw[warp] = hi;
+            low[warp] = lo;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            long long C = 0, S1 = 0;
+            unsigned long long H = 0, Lo = 0;
+            for (int w = 0; w < NW; ++w) {
+                C += cw[w];
+                S1 += s1w[w];
+                add128(H, Lo, hiw[w], low[w]);
+            }
+            int go;
+            if (clip && C == 0) {
+                go = 0;  // nothing kept: keep the previous set
+            } else {
+                const bool same = clip && C == sh_N && S1 == sh_S1 && H == sh_H && Lo == sh_L;
+                sh_N = C;
+                sh_S1 = S1;
+                sh_H = H;
+                sh_L = Lo;
+                go = pass < iters && !same;
+            }
+            if (go) {
+                const unsigned __int128 S2 = ((unsigned __int128)sh_H << 64) | sh_L;
+                const __int128 V = (__int128)sh_N * (__int128)S2 - (__int128)sh_S1 * (__int128)sh_S1;
+                const unsigned __int128 Rn =
+                    (unsigned __int128)(a.clip_c16 * a.clip_c16) * (V > 0 ? (unsigned __int128)V : 0);
+                sh_Rh = (unsigned long long)(Rn >> 64);
+                sh_Rl = (unsigned long long)Rn;
+            }
+            sh_go = go;
+        }
+        __syncthreads();
+        if (!sh_go) break;
+    }
+    if (threadIdx.x == 0) {
+        const long long N = sh_N, S1 = sh_S1;
         RowStats st{};
-        if (n > 0) {
+        if (N > 0) {
             // N^2 var = N * sum y^2 - (sum y)^2, exact in 128 bits
-            const unsigned __int128 S2 = ((unsigned __int128)H << 64) | Lo;
-            const __int128 num = (__int128)n * (__int128)S2 - (__int128)S1 * (__int128)S1;
+            const unsigned __int128 S2 = ((unsigned __int128)sh_H << 64) | sh_L;
+            const __int128 num = (__int128)N * (__int128)S2 - (__int128)S1 * (__int128)S1;
             const unsigned __int128 un = num > 0 ? (unsigned __int128)num : 0;
             const double numd = (double)(unsigned long long)(un >> 64) * 18446744073709551616.0 +
                                 (double)(unsigned long long)un;
-            st.mu = (double)S1 / (double)n;
-            st.sigma = sqrt(numd) / (double)n;
+            st.mu = (double)S1 / (double)N;
+            st.sigma = sqrt(numd) / (double)N;
             const long long m0 = llround(st.mu);
             st.m0 = (float)m0;
             st.inv_sigma = st.sigma > 0 ? 1.0 / st.sigma : 0.0;
             st.zero_sigma = st.sigma > 0 ? 0 : 1;
-            sh_f = (double)(S1 - m0 * (long long)n) / (double)n;  // mu - m0
+            sh_f = (double)(S1 - m0 * N) / (double)N;  // mu - m0
         } else {
             st.zero_sigma = 1;
             sh_f = 0.0;

@@ -31,13 +31,14 @@ def run_gpu(plan: Plan, x, W: int, thr: float, capacity: int = 1 << 16, want_snr
     return out, snr, got, total, nsamp
 
 
-def oracle_candidates(oracle, rows_y, W, thr, dm_offset, rng, windows=None):
+def oracle_candidates(oracle, rows_y, W, thr, dm_offset, rng, windows=None, clip=None):
     """Oracle candidate dict {(dm, t): Candidate} and fragile key set for the
-    given rows {row_index: int64 series}; windows {row: (t_lo, t_hi)}."""
+    given rows {row_index: int64 series}; windows {row: (t_lo, t_hi)};
+    clip = (c16, max_iters) for k-sigma clipped statistics."""
     solid, fragile, B = {}, set(), {}
     for i, y in rows_y.items():
         lo, hi = windows[i] if windows else (0, y.size)
-        c, b, wb, mu, sg = oracle.search_row(y, W, thr, dm_offset + i, rng, lo, hi)
+        c, b, wb, mu, sg = oracle.search_row(y, W, thr, dm_offset + i, rng, lo, hi, clip=clip)
         B[i] = (lo, b, wb, mu, sg)
         for cc in c:
             key = (cc.dm_index, cc.t)
