@@ -52,38 +52,80 @@ constexpr int kStatsThreads = 512;
 // Exact integer sums N, S1 = sum y, S2 = sum y^2 (128-bit) over the kept
 // samples; pass 0 keeps every sample.  With k-sigma clipping (k = c16/16),
 // each further pass keeps the samples with |y - mu| <= k sigma of the previous
-// set, i.e. (times 16N, squared) 256 (N y - S1)^2 <= c16^2 (N S2 - S1^2),
-// decided exactly in 128-bit integers; it stops after clip_iters passes, at a
-// pass keeping nothing (dropped) or at a fixed point (same N, S1, S2).
+// set, i.e. (times 16N, squared) 256 (N y - S1)^2 <= c16^2 (N S2 - S1^2).
+// That set is an interval of integers; thread 0 finds its ends exactly (an
+// FP64 estimate corrected by the 128-bit test), so each sample needs two
+// compares.  Stops after clip_iters passes, at a pass keeping nothing
+// (dropped) or at a fixed point (same N, S1, S2).
+
+// 256 (N v - S1)^2 <= R, exactly (|N v - S1| < 2^57 for |v| <= 2^25, N < 2^31)
+__device__ __forceinline__ bool clip_keeps(long long N, long long S1, unsigned __int128 R, long long v) {
+    const long long d = N * v - S1;
+    const unsigned long long ad = (unsigned long long)(d < 0 ? -d : d);
+    return (((unsigned __int128)ad * ad) << 8) <= R;
+}
+
+// Ends [lo, hi] of the kept interval, clamped to +-2^25 (every sample lies
+// within +-2^24); lo > hi when no integer is kept.
+__device__ void clip_interval(long long N, long long S1, unsigned __int128 R, long long& lo, long long& hi) {
+    constexpr long long kLim = 1ll << 25;
+    const double half = sqrt((double)R) / 16.0;  // |N v - S1| <= half
+    const double c = (double)S1 / (double)N, h = half / (double)N;
+    lo = (long long)fmax(fmin(ceil(c - h), (double)kLim), (double)-kLim);
+    hi = (long long)fmax(fmin(floor(c + h), (double)kLim), (double)-kLim);
+    // the estimate is within a few units; move each end onto the exact boundary
+    for (int k = 0; k < 64 && lo <= hi && !clip_keeps(N, S1, R, lo); ++k) ++lo;
+    for (int k = 0; k < 64 && lo > -kLim && clip_keeps(N, S1, R, lo - 1); ++k) --lo;
+    for (int k = 0; k < 64 && hi >= lo && !clip_keeps(N, S1, R, hi); ++k) --hi;
+    for (int k = 0; k < 64 && hi < kLim && clip_keeps(N, S1, R, hi + 1); ++k) ++hi;
+}
+
+__device__ __forceinline__ void stats_accumulate(float yf, bool clip, float lo, float hi, long long& cnt,
+                                                 long long& s1, long long& s2) {
+    if (clip && !(yf >= lo && yf <= hi)) return;
+    const int v = (int)yf;  // exact: |y| < 2^24
+    ++cnt;
+    s1 += v;
+    s2 += (long long)v * v;
+}
+
 __device__ __forceinline__ void stats_row(const SpsArgs& a, const double* rsw, int row) {
     constexpr int NW = kStatsThreads / 32;
+    constexpr int64_t kFlush = 4096;  // float4 steps per 128-bit flush: 2^14 samples, s2 < 2^14 * 2^48
     __shared__ long long s1w[NW], cw[NW];
     __shared__ unsigned long long hiw[NW], low[NW];
     __shared__ long long sh_N, sh_S1;           // sums of the accepted set
     __shared__ unsigned long long sh_H, sh_L;   // its S2 (high, low words)
-    __shared__ unsigned long long sh_Rh, sh_Rl; // clipping bound c16^2 (N S2 - S1^2)
+    __shared__ float sh_lo, sh_hi;              // kept interval of the next pass
     __shared__ int sh_go;
     __shared__ double sh_f, sh_inv;
-    const float* y = a.dd + (int64_t)row * a.pitch;
+    const float* y = a.dd + (int64_t)row * a.pitch;  // 16-byte aligned rows
     const int64_t n = a.length;
+    const int64_t n4 = n >> 2;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int iters = a.clip_iters;
     for (int pass = 0; pass <= iters; ++pass) {
         const bool clip = pass > 0;
-        const long long N = clip ? sh_N : 0, S1p = clip ? sh_S1 : 0;
-        const unsigned __int128 R = clip ? (((unsigned __int128)sh_Rh << 64) | sh_Rl) : 0;
+        const float lo_f = clip ? sh_lo : 0.f, hi_f = clip ? sh_hi : 0.f;
         long long cnt = 0, s1 = 0;
         unsigned long long hi = 0, lo = 0;
-        for (int64_t i = threadIdx.x; i < n; i += kStatsThreads) {
-            const long long v = (long long)y[i];
-            if (clip) {
-                const long long d = N * v - S1p;  // |d| < 2^56 (N < 2^31, |v| < 2^24)
-                const unsigned long long ad = (unsigned long long)(d < 0 ? -d : d);
-                if ((((unsigned __int128)ad * ad) << 8) > R) continue;
+        const float4* y4 = reinterpret_cast<const float4*>(y);
+        for (int64_t b = threadIdx.x; b < n4; b += (int64_t)kStatsThreads * kFlush) {
+            const int64_t e = min(n4, b + (int64_t)kStatsThreads * kFlush);
+            long long s2 = 0;
+            for (int64_t j = b; j < e; j += kStatsThreads) {
+                const float4 q = y4[j];
+                stats_accumulate(q.x, clip, lo_f, hi_f, cnt, s1, s2);
+                stats_accumulate(q.y, clip, lo_f, hi_f, cnt, s1, s2);
+                stats_accumulate(q.z, clip, lo_f, hi_f, cnt, s1, s2);
+                stats_accumulate(q.w, clip, lo_f, hi_f, cnt, s1, s2);
             }
-            ++cnt;
-            s1 += v;
-            add128(hi, lo, 0ull, (unsigned long long)(v * v));
+            add128(hi, lo, 0ull, (unsigned long long)s2);
+        }
+        if (threadIdx.x < (int)(n - 4 * n4)) {
+            long long s2 = 0;
+            stats_accumulate(y[4 * n4 + threadIdx.x], clip, lo_f, hi_f, cnt, s1, s2);
+            add128(hi, lo, 0ull, (unsigned long long)s2);
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -122,10 +164,12 @@ __device__ __forceinline__ void stats_row(const SpsArgs& a, const double* rsw, i
             if (go) {
                 const unsigned __int128 S2 = ((unsigned __int128)sh_H << 64) | sh_L;
                 const __int128 V = (__int128)sh_N * (__int128)S2 - (__int128)sh_S1 * (__int128)sh_S1;
-                const unsigned __int128 Rn =
+                const unsigned __int128 R =
                     (unsigned __int128)(a.clip_c16 * a.clip_c16) * (V > 0 ? (unsigned __int128)V : 0);
-                sh_Rh = (unsigned long long)(Rn >> 64);
-                sh_Rl = (unsigned long long)Rn;
+                long long vlo, vhi;
+                clip_interval(sh_N, sh_S1, R, vlo, vhi);
+                sh_lo = (float)vlo;  // exact: |v| <= 2^25
+                sh_hi = (float)vhi;
             }
             sh_go = go;
         }
