@@ -64,10 +64,12 @@ static void build_groups(RangePlan& r, int C) {
     const int lane_max = 65535 / (255 * dec);          // channels per 16-bit lane
     if (r.span_max > 4096) return;
     const int gzw = (int)round_up((kGroupTau + r.span_max + 3) / 2 + 2, 4);
-    // chunks of up to 64 channels (fewer when 16-bit lanes would overflow);
-    // as many group sums per batch as two CTAs per SM leave room for (<= 32,
-    // one per lane of the warps' group-field registers)
-    const int gcc = std::min(64, lane_max) / 8 * 8;
+    // chunks of up to kGroupChunkMax channels (fewer when 16-bit lanes would
+    // overflow): larger chunks put more channels with one delay pattern into
+    // one group; as many group sums per batch as two CTAs per SM leave room
+    // for (<= 32, one per lane of the warps' group-field registers)
+    constexpr int kGroupChunkMax = 256;
+    const int gcc = std::min(kGroupChunkMax, lane_max) / 8 * 8;
     int gz = 0;
     while (grouped_smem(gz + 1, gzw) <= kPairSmem && gz < std::min(gcc, 32)) ++gz;
     if (gcc < 8 || gz < 1) return;

@@ -1,5 +1,6 @@
 """Host-side strategy selection (no GPU): which ranges get the grouped
 dedispersion, the work it saves, and the checks of aa_plan_set_strategy."""
+import numpy as np
 import pytest
 
 from paper_1912_07704_gb300 import abi, synth
@@ -12,11 +13,42 @@ def test_ska_plan_selects_grouped():
     for r in range(len(w.ranges)):
         info = abi.aa_plan_range(p.handle, w.nsamp, r)
         assert info.grouped_available == 1
-        # fine DM steps: about a third to a half of the direct adds
-        assert 0.25 < info.grouped_work < 0.5, (r, info.grouped_work)
+        # fine DM steps: a quarter to a half of the direct adds
+        assert 0.2 < info.grouped_work < 0.5, (r, info.grouped_work)
         assert info.strategy == abi.AA_DEDISP_GROUPED
         assert info.tile_dms == 16 and info.tile_samples == 512
         assert info.smem_bytes <= 113 * 1024  # two CTAs per SM
+
+
+def _pattern_work(shifts, ndm, C, cc, B=16):
+    """Adds of the grouped form over those of the direct form, counting the
+    distinct delay patterns of every (B-trial block, cc-channel chunk) by brute
+    force (a partial block repeats its last trial)."""
+    sh = np.asarray(shifts).reshape(ndm, C)
+    direct = grouped = 0
+    for d0 in range(0, ndm, B):
+        nb = min(B, ndm - d0)
+        rows = sh[[d0 + min(d, nb - 1) for d in range(B)]]
+        rel = (rows - rows[0]).T
+        for c0 in range(0, C, cc):
+            nch = min(cc, C - c0)
+            G = len({tuple(x) for x in rel[c0:c0 + nch]})
+            direct += nch * nb
+            grouped += nch + G * nb
+    return grouped / direct
+
+
+@pytest.mark.parametrize("ranges,C", [(synth.SKA_4096.ranges[:2], 4096),
+                                      ([(0.0, 0.25, 45, 1), (11.0, 0.5, 21, 4)], 1024)])
+def test_grouped_work_counts_delay_patterns(ranges, C):
+    p = Plan(C, 1508.0, -300.0 / C, 64e-6, list(ranges))
+    for r, rg in enumerate(ranges):
+        p.set_strategy(r, abi.AA_DEDISP_GROUPED)  # stage_channels of the grouped tiles
+        info = abi.aa_plan_range(p.handle, 1 << 17, r)
+        want = _pattern_work(p.shifts(r), rg[2], C, info.stage_channels)
+        assert info.grouped_work == pytest.approx(want, rel=1e-12)
+        # chunks as wide as 16-bit lanes allow, up to 256 channels
+        assert info.stage_channels == min(256, 65535 // (255 * rg[3]) // 8 * 8)
 
 
 def test_coarse_plan_keeps_direct():
@@ -38,7 +70,7 @@ def test_grouped_wide_spans_then_unavailable():
     p = Plan(203, 1400.0, -1.5, 64e-6, [(0.0, 3.0, 35, 1)])  # span ~940 samples
     p.set_strategy(0, abi.AA_DEDISP_GROUPED)
     info = abi.aa_plan_range(p.handle, 9001, 0)
-    assert info.grouped_available == 1 and info.stage_channels == 64
+    assert info.grouped_available == 1 and info.stage_channels == 256
     assert info.smem_bytes <= 113 * 1024
     p = Plan(203, 1400.0, -1.5, 64e-6, [(0.0, 15.0, 35, 1)])  # span ~4700 samples
     info = abi.aa_plan_range(p.handle, 9001, 0)
