@@ -69,6 +69,7 @@ static void build_groups(RangePlan& r, int C) {
     // one group; as many group sums per batch as two CTAs per SM leave room
     // for (<= 32, one per lane of the warps' group-field registers)
     constexpr int kGroupChunkMax = 256;
+    constexpr int kGroupSplit = 16;  // members per group sum at most
     const int gcc = std::min(kGroupChunkMax, lane_max) / 8 * 8;
     int gz = 0;
     while (grouped_smem(gz + 1, gzw) <= kPairSmem && gz < std::min(gcc, 32)) ++gz;
@@ -104,24 +105,63 @@ static void build_groups(RangePlan& r, int C) {
                 }
                 members[gi].push_back((uint8_t)cl);
             }
+            // Phase 1 of the kernel gives the two 256-sample units of the
+            // group at batch position j to warp pair j % 8, and a unit costs
+            // one pass over the group's members.  Groups larger than
+            // kGroupSplit members are split into near-equal parts (same delay
+            // pattern, separate sums), the parts sorted by size and, batch by
+            // batch, dealt to the warp pairs least loaded so far, so that no
+            // warp pair waits on one large group.
+            struct Part { int gi, b, e; };
+            std::vector<Part> parts;
+            for (size_t gi = 0; gi < local.size(); ++gi) {
+                const int n = (int)members[gi].size();
+                const int np = (n + kGroupSplit - 1) / kGroupSplit, base = n / np, rem = n % np;
+                for (int j = 0, pos = 0; j < np; ++j) {
+                    const int sz = base + (j < rem ? 1 : 0);
+                    parts.push_back(Part{(int)gi, pos, pos + sz});
+                    pos += sz;
+                }
+            }
+            std::stable_sort(parts.begin(), parts.end(),
+                             [](const Part& x, const Part& y) { return x.e - x.b > y.e - y.b; });
+            std::vector<Part> laid(parts.size());
+            constexpr int kPairs = kDedispWarps / 2;
+            for (size_t b0 = 0; b0 < parts.size(); b0 += (size_t)gz) {
+                const int n = (int)std::min(parts.size() - b0, (size_t)gz);
+                int load[kPairs] = {}, cnt[kPairs] = {};
+                for (int i = 0; i < n; ++i) {
+                    int best = -1;
+                    for (int q = 0; q < kPairs; ++q) {
+                        const int cap = n / kPairs + (q < n % kPairs ? 1 : 0);
+                        if (cnt[q] < cap && (best < 0 || load[q] < load[best])) best = q;
+                    }
+                    const Part& pt = parts[b0 + i];
+                    laid[b0 + (size_t)(kPairs * cnt[best] + best)] = pt;
+                    ++cnt[best];
+                    load[best] += pt.e - pt.b;
+                }
+            }
             GroupRec& rec = r.grec[(size_t)b * nchk + k];
             rec.first = (uint32_t)r.gdesc.size();
-            rec.ngroups = (uint16_t)local.size();
+            rec.ngroups = (uint16_t)laid.size();
             rec.nch = (uint16_t)nch;
             GroupMember* mem = &r.gmem[((size_t)b * nchk + k) * gcc];
             int m = 0;
-            for (size_t gi = 0; gi < local.size(); ++gi) {
-                local[gi].mstart = (uint16_t)m;
-                local[gi].mcount = (uint16_t)members[gi].size();
-                for (uint8_t cl : members[gi]) {
+            for (const Part& pt : laid) {
+                GroupDesc g = local[(size_t)pt.gi];
+                g.mstart = (uint16_t)m;
+                g.mcount = (uint16_t)(pt.e - pt.b);
+                for (int j = pt.b; j < pt.e; ++j) {
+                    const uint8_t cl = members[(size_t)pt.gi][(size_t)j];
                     const int32_t s0 = r.shifts[(size_t)d0 * C + c0 + cl];
                     const int32_t s1 = r.shifts[(size_t)(d0 + nb - 1) * C + c0 + cl];
                     mem[m++] = GroupMember{s0, (uint16_t)cl, (uint16_t)(s1 - s0)};
                 }
-                r.gdesc.push_back(local[gi]);
+                r.gdesc.push_back(g);
             }
             direct += (double)nch * nb;
-            grouped += (double)nch + (double)local.size() * nb;
+            grouped += (double)nch + (double)laid.size() * nb;
         }
     }
     r.gcc = gcc;

@@ -20,10 +20,11 @@ def test_ska_plan_selects_grouped():
         assert info.smem_bytes <= 113 * 1024  # two CTAs per SM
 
 
-def _pattern_work(shifts, ndm, C, cc, B=16):
+def _pattern_work(shifts, ndm, C, cc, B=16, split=16):
     """Adds of the grouped form over those of the direct form, counting the
     distinct delay patterns of every (B-trial block, cc-channel chunk) by brute
-    force (a partial block repeats its last trial)."""
+    force (a partial block repeats its last trial); a pattern shared by n
+    channels makes ceil(n / split) group sums."""
     sh = np.asarray(shifts).reshape(ndm, C)
     direct = grouped = 0
     for d0 in range(0, ndm, B):
@@ -32,7 +33,10 @@ def _pattern_work(shifts, ndm, C, cc, B=16):
         rel = (rows - rows[0]).T
         for c0 in range(0, C, cc):
             nch = min(cc, C - c0)
-            G = len({tuple(x) for x in rel[c0:c0 + nch]})
+            pats = {}
+            for x in rel[c0:c0 + nch]:
+                pats[tuple(x)] = pats.get(tuple(x), 0) + 1
+            G = sum(-(-n // split) for n in pats.values())
             direct += nch * nb
             grouped += nch + G * nb
     return grouped / direct
