@@ -131,7 +131,7 @@ def test_autograd_functions(small):
     loss_b = DedispersionMSE.apply(xb, wb, tmpl, plan)
     loss_b.backward()
     torch.cuda.synchronize()
-    assert abs(float(loss_a) - float(loss_b)) <= 1e-5 * abs(float(loss_b))
+    assert abs(float(loss_a.detach()) - float(loss_b.detach())) <= 1e-5 * abs(float(loss_b.detach()))
     assert torch.allclose(xr.grad, xb.grad, rtol=1e-3, atol=1e-6 * float(xb.grad.abs().max()))
     assert torch.allclose(wr.grad, wb.grad, rtol=1e-3, atol=1e-6 * float(wb.grad.abs().max()))
 
