@@ -418,14 +418,25 @@ __device__ __forceinline__ void dedisperse_grouped_block(const DedispArgs& a, in
             // otherwise gnj full units per group.
             {
                 const int ng = ge - gb;
-                const int nmain = gtl ? 2 * ng : ng * nj;
+                // 8-bit input with tail units: one unit per group covers samples
+                // 0..511 at 16 per lane; otherwise two units of 8 per lane
+                constexpr bool kWide = EB == 1;
+                const int nmain = gtl ? (kWide ? ng : 2 * ng) : ng * nj;
                 const int nunits = gtl ? nmain + (ng + gpt - 1) / gpt : nmain;
                 for (int u = warp; u < nunits; u += kDedispWarps) {
-                    int gi, idx;  // this lane's group and sample block (samples 8 idx .. 8 idx + 7)
+                    int gi, idx;  // this lane's group and sample block (samples 8 idx .. 8 idx + 7,
+                                  // or 16 idx .. 16 idx + 15 when wide)
+                    bool wide = false;
                     if (gtl) {
                         if (u < nmain) {
-                            gi = u >> 1;
-                            idx = 32 * (u & 1) + lane;
+                            if (kWide) {
+                                gi = u;
+                                idx = lane;
+                                wide = true;
+                            } else {
+                                gi = u >> 1;
+                                idx = 32 * (u & 1) + lane;
+                            }
                         } else {
                             gi = (u - nmain) * gpt + (lane >> gtl_log);
                             idx = 64 + (lane & (gtl - 1));
@@ -441,6 +452,49 @@ __device__ __forceinline__ void dedisperse_grouped_block(const DedispArgs& a, in
                     const int mstart = (int)(ms & 0xffffu), mend = mstart + (int)(ms >> 16);
                     uint32_t* zA = zs + gs * 2 * gzw;
                     uint32_t* zB = zA + gzw;
+                    const int wl = (int)(pitch_b >> 2) - 1;
+                    if constexpr (kWide) {
+                        if (wide) {
+                            // 16 samples: five words per member (bytes b .. b + 16)
+                            uint32_t A0 = 0, A1 = 0, A2 = 0, A3 = 0, A4 = 0, A5 = 0, A6 = 0, A7 = 0, E = 0;
+                            if (gvalid) {
+#pragma unroll 2
+                                for (int m = mstart; m < mend; ++m) {
+                                    const int2 rm = __ldg(reinterpret_cast<const int2*>(mk + m));
+                                    const int64_t bo = t0 + rm.x + 16 * idx;
+                                    const int wi = (int)(bo >> 2);
+                                    const uint32_t* w = reinterpret_cast<const uint32_t*>(
+                                        chunk_in + (int64_t)(rm.y & 0xffff) * pitch_b);
+                                    const uint32_t sh = (uint32_t)(bo & 3) * 8u;
+                                    const uint32_t w0 = __ldg(w + min(wi, wl)), w1 = __ldg(w + min(wi + 1, wl)),
+                                                   w2 = __ldg(w + min(wi + 2, wl)), w3 = __ldg(w + min(wi + 3, wl)),
+                                                   w4 = __ldg(w + min(wi + 4, wl));
+                                    const uint32_t v0 = __funnelshift_r(w0, w1, sh);
+                                    const uint32_t v1 = __funnelshift_r(w1, w2, sh);
+                                    const uint32_t v2 = __funnelshift_r(w2, w3, sh);
+                                    const uint32_t v3 = __funnelshift_r(w3, w4, sh);
+                                    A0 += __byte_perm(v0, 0u, 0x4140);
+                                    A1 += __byte_perm(v0, 0u, 0x4342);
+                                    A2 += __byte_perm(v1, 0u, 0x4140);
+                                    A3 += __byte_perm(v1, 0u, 0x4342);
+                                    A4 += __byte_perm(v2, 0u, 0x4140);
+                                    A5 += __byte_perm(v2, 0u, 0x4342);
+                                    A6 += __byte_perm(v3, 0u, 0x4140);
+                                    A7 += __byte_perm(v3, 0u, 0x4342);
+                                    E += (w4 >> sh) & 0xffu;
+                                }
+                                uint4* a4 = reinterpret_cast<uint4*>(zA + 8 * idx);
+                                uint4* b4 = reinterpret_cast<uint4*>(zB + 8 * idx);
+                                a4[0] = make_uint4(A0, A1, A2, A3);
+                                a4[1] = make_uint4(A4, A5, A6, A7);
+                                b4[0] = make_uint4(__byte_perm(A0, A1, 0x5432), __byte_perm(A1, A2, 0x5432),
+                                                   __byte_perm(A2, A3, 0x5432), __byte_perm(A3, A4, 0x5432));
+                                b4[1] = make_uint4(__byte_perm(A4, A5, 0x5432), __byte_perm(A5, A6, 0x5432),
+                                                   __byte_perm(A6, A7, 0x5432), __byte_perm(A7, E, 0x5432));
+                            }
+                            continue;
+                        }
+                    }
                     uint32_t A0 = 0, A1 = 0, A2 = 0, A3 = 0, E = 0;  // (z0,z1) .. (z6,z7), z8
                     if (gvalid && 8 * idx < zlen) {
 #pragma unroll 2
@@ -451,7 +505,7 @@ __device__ __forceinline__ void dedisperse_grouped_block(const DedispArgs& a, in
                             // output sample; their words are clamped to the row's
                             // last word so no read leaves the buffer.
                             const int64_t bo = (int64_t)EB * (t0 + rm.x + 8 * idx);
-                            const int wi = (int)(bo >> 2), wl = (int)(pitch_b >> 2) - 1;
+                            const int wi = (int)(bo >> 2);
                             const uint32_t* w = reinterpret_cast<const uint32_t*>(
                                 chunk_in + (int64_t)(rm.y & 0xffff) * pitch_b);
                             const uint32_t sh = (uint32_t)(bo & 3) * 8u;

@@ -74,6 +74,16 @@ static void build_groups(RangePlan& r, int C) {
     int gz = 0;
     while (grouped_smem(gz + 1, gzw) <= kPairSmem && gz < std::min(gcc, 32)) ++gz;
     if (gcc < 8 || gz < 1) return;
+    {   // samples past kGroupTau (the span and the one sample after it) in lanes of 8
+        const int need = (r.span_max + 1 + 7) / 8;
+        int tl = 1;
+        while (tl < need) tl *= 2;
+        r.gtl = (kGroupTau % 256 == 0 && tl <= 32) ? tl : 0;
+    }
+    // phase 1's static unit assignment: with tail units, an 8-bit range gives
+    // a group one unit (warp j mod 16 for batch position j), a 16-bit range
+    // two (warp pair j mod 8)
+    const int kSlots = (r.gtl > 0 && r.elem == 1) ? kDedispWarps : kDedispWarps / 2;
     const int ndm = r.desc.ndm;
     const int nblk = (ndm + B - 1) / B, nchk = (C + gcc - 1) / gcc;
     r.grec.assign((size_t)nblk * nchk, GroupRec{});
@@ -105,13 +115,13 @@ static void build_groups(RangePlan& r, int C) {
                 }
                 members[gi].push_back((uint8_t)cl);
             }
-            // Phase 1 of the kernel gives the two 256-sample units of the
-            // group at batch position j to warp pair j % 8, and a unit costs
-            // one pass over the group's members.  Groups larger than
+            // Phase 1 of the kernel gives the unit(s) of the group at batch
+            // position j to slot j % kSlots (a warp or a warp pair), and a unit
+            // costs one pass over the group's members.  Groups larger than
             // kGroupSplit members are split into near-equal parts (same delay
             // pattern, separate sums), the parts sorted by size and, batch by
-            // batch, dealt to the warp pairs least loaded so far, so that no
-            // warp pair waits on one large group.
+            // batch, dealt to the slots least loaded so far, so that no warp
+            // waits on one large group.
             struct Part { int gi, b, e; };
             std::vector<Part> parts;
             for (size_t gi = 0; gi < local.size(); ++gi) {
@@ -126,18 +136,17 @@ static void build_groups(RangePlan& r, int C) {
             std::stable_sort(parts.begin(), parts.end(),
                              [](const Part& x, const Part& y) { return x.e - x.b > y.e - y.b; });
             std::vector<Part> laid(parts.size());
-            constexpr int kPairs = kDedispWarps / 2;
             for (size_t b0 = 0; b0 < parts.size(); b0 += (size_t)gz) {
                 const int n = (int)std::min(parts.size() - b0, (size_t)gz);
-                int load[kPairs] = {}, cnt[kPairs] = {};
+                int load[kDedispWarps] = {}, cnt[kDedispWarps] = {};
                 for (int i = 0; i < n; ++i) {
                     int best = -1;
-                    for (int q = 0; q < kPairs; ++q) {
-                        const int cap = n / kPairs + (q < n % kPairs ? 1 : 0);
+                    for (int q = 0; q < kSlots; ++q) {
+                        const int cap = n / kSlots + (q < n % kSlots ? 1 : 0);
                         if (cnt[q] < cap && (best < 0 || load[q] < load[best])) best = q;
                     }
                     const Part& pt = parts[b0 + i];
-                    laid[b0 + (size_t)(kPairs * cnt[best] + best)] = pt;
+                    laid[b0 + (size_t)(kSlots * cnt[best] + best)] = pt;
                     ++cnt[best];
                     load[best] += pt.e - pt.b;
                 }
@@ -169,12 +178,6 @@ static void build_groups(RangePlan& r, int C) {
     r.gzw = gzw;
     r.gflush = std::max(1, lane_max / gcc);
     r.gnj = (kGroupTau + r.span_max + 255) / 256;
-    {   // samples past kGroupTau (the span and the one sample after it) in lanes of 8
-        const int need = (r.span_max + 1 + 7) / 8;
-        int tl = 1;
-        while (tl < need) tl *= 2;
-        r.gtl = (kGroupTau % 256 == 0 && tl <= 32) ? tl : 0;
-    }
     r.gsmem = grouped_smem(gz, gzw);
     r.gwork = direct > 0 ? grouped / direct : 1.0;
     r.grouped_ok = true;
