@@ -128,7 +128,8 @@ typedef struct aa_range_info {
     double dm_lo;
     double dm_step;
     int64_t nsamp_dec;   /* floor(nsamp/dec) */
-    int64_t length;      /* L = max(0, nsamp_dec - maxshift): output samples per trial */
+    int64_t length;      /* L = max(0, nsamp_dec - maxshift): output samples per trial
+                            (maxshift: largest effective delay of the strategy in use) */
     int64_t pitch;       /* floats between consecutive output rows (multiple of 64) */
     int64_t row_offset;  /* float offset of this range's row 0 in the output buffer */
     /* strategy (fixed at aa_plan_create) */
@@ -141,6 +142,9 @@ typedef struct aa_range_info {
     int32_t strategy;        /* aa_dedisp_strategy in use for this range */
     int32_t grouped_available;  /* 1 if AA_DEDISP_GROUPED can be selected */
     double grouped_work;     /* adds of the grouped strategy / adds of the direct one */
+    int32_t subband_channels;       /* AA_DEDISP_SUBBAND: channels per band (else 0) */
+    int32_t subband_coarse_trials;  /* AA_DEDISP_SUBBAND: fine trials per coarse trial */
+    double subband_work;     /* adds of the sub-band strategy / adds of the direct one */
 } aa_range_info;
 
 /* Strategy and memory requests for `nsamp` samples and boxcar widths up to
@@ -245,7 +249,32 @@ aa_status aa_workspace_status(void* d_ws, aa_stream_t stream);
  *     channels whose delays differ from the block's first trial by the same
  *     amounts at every trial are first summed once; each trial then adds the
  *     group sums.  Available when the plan could build the group tables. */
-typedef enum { AA_DEDISP_DIRECT = 0, AA_DEDISP_GROUPED = 1 } aa_dedisp_strategy;
+typedef enum { AA_DEDISP_DIRECT = 0, AA_DEDISP_GROUPED = 1, AA_DEDISP_SUBBAND = 2 } aa_dedisp_strategy;
+
+/* Sub-band dedispersion of range r (AA_DEDISP_SUBBAND): an approximation of
+ * the brute-force sum with fewer adds, the cheaper-than-brute-force family
+ * the dedispersion module's cited work belongs to (Sec. 1).  Channels form
+ * bands of band_channels consecutive channels (the last may be shorter), each
+ * with a reference channel: its highest-frequency channel c_b.  Fine trials
+ * form coarse trials of coarse_trials consecutive trials (the last may be
+ * shorter) whose DM D_j is that of their middle trial i_j = j*m + (n_j-1)/2.
+ *   stage 1: z[b][j][t] = sum_{c in band b} x[c][t + r(c, j)],
+ *            r(c, j) = round_half_away(((k_DM*D_j)*(delta_c - delta_cb))/(tsamp*dec)),
+ *            delta_c = f_c^-2 - f_top^-2 (the plan's delay arithmetic);
+ *   stage 2: y[i][t] = sum_b z[b][j(i)][t + s(c_b, i)], s the plan's delays,
+ * i.e. channel c of trial i is taken at the effective delay
+ * s(c_b, i) + r(c, j(i)) instead of s(c, i).  Sums stay exact integers.  The
+ * range's maxshift becomes max r + max s(c_b, .) and its length
+ * nsamp_dec - maxshift.  Adds per trial-sample: nchans/coarse_trials + nbands.
+ * AA_ERR_ARG for a bad range, band_channels outside [1, nchans] or
+ * coarse_trials outside [1, 16]; AA_ERR_CONFIG when band_channels * 255 * dec
+ * > 32767 (the 16-bit partial sums) or the stages do not fit the dedispersion
+ * tile.  aa_plan_set_strategy returns the range to an exact strategy.  Not
+ * available in batched runs (aa_batch_create returns AA_ERR_CONFIG) nor in
+ * the differentiable form; the autotuner leaves such ranges alone.  Like
+ * aa_plan_set_strategy, call it while no work of the plan is in flight. */
+aa_status aa_plan_set_subband(aa_plan* plan, int32_t r, int32_t band_channels,
+                              int32_t coarse_trials);
 
 /* Select the strategy of range r (aa_plan_create picks one from the number
  * of adds each needs).  AA_ERR_ARG for a bad range or strategy value,

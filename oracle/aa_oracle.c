@@ -79,6 +79,28 @@ int32_t oracle_shifts(int32_t nchans, double fch1, double foff, double tsamp,
     return near_half;
 }
 
+/* Sub-band dedispersion (an approximation of the brute-force sum): channels
+ * in bands of `band` consecutive channels, each with a reference channel, its
+ * highest frequency (the band's first channel when foff < 0, else its last).
+ * Delay of every channel relative to its band's reference at one DM, in
+ * decimated samples: round half away of ((K*dm)*(delta_c - delta_ref)) /
+ * (tsamp*dec), delta as in oracle_shifts. */
+void oracle_subband_rel(int32_t nchans, double fch1, double foff, double tsamp, double dm,
+                        int32_t dec, int32_t band, int32_t* out)
+{
+    double ft = oracle_f_top(fch1, foff, nchans);
+    for (int32_t c = 0; c < nchans; ++c) {
+        int32_t b0 = (c / band) * band;
+        int32_t b1 = b0 + band - 1 < nchans - 1 ? b0 + band - 1 : nchans - 1;
+        int32_t cr = foff < 0 ? b0 : b1;
+        double fc = fch1 + (double)c * foff;
+        double fr = fch1 + (double)cr * foff;
+        double dc = 1.0 / (fc * fc) - 1.0 / (ft * ft);
+        double dr = 1.0 / (fr * fr) - 1.0 / (ft * ft);
+        out[c] = (int32_t)llround(ORACLE_K_DM * dm * (dc - dr) / (tsamp * (double)dec));
+    }
+}
+
 /* Time decimation by summation; the trailing partial bin is dropped. */
 void oracle_decimate(const uint8_t* x, int32_t nchans, int64_t nsamp, int64_t pitch,
                      int32_t dec, uint16_t* out, int64_t out_pitch)

@@ -68,6 +68,8 @@ def lib():
         L.oracle_dedisperse.restype = None
         L.oracle_moments.argtypes = [vp, i64, ctypes.POINTER(f64), ctypes.POINTER(f64)]
         L.oracle_moments.restype = None
+        L.oracle_subband_rel.argtypes = [i32, f64, f64, f64, f64, i32, i32, vp]
+        L.oracle_subband_rel.restype = None
         L.oracle_moments_clipped.argtypes = [vp, i64, i32, i32, ctypes.POINTER(f64),
                                              ctypes.POINTER(f64), ctypes.POINTER(i64)]
         L.oracle_moments_clipped.restype = None
@@ -278,6 +280,56 @@ def search_row(y: np.ndarray, W: int, thr: float, dm_index: int, rng: int,
             fragile = near or mg[k] < FRAGILE_CMP
             cands.append(Candidate(dm_index, t, int(wb[k]), rng, float(v), bool(fragile)))
     return cands, B[t_lo - a:t_hi - a], wb[t_lo - a:t_hi - a], mu, sigma
+
+
+# ----------------------------------------------------------------------------
+# Sub-band dedispersion (approximate; exact integer sums of approximated delays)
+# ----------------------------------------------------------------------------
+
+def subband_rel(nchans, fch1, foff, tsamp, dm, dec, band) -> np.ndarray:
+    """Delay of every channel relative to its band's reference channel."""
+    out = np.empty(nchans, dtype=np.int32)
+    lib().oracle_subband_rel(int(nchans), float(fch1), float(foff), float(tsamp), float(dm),
+                             int(dec), int(band), _ptr(out))
+    return out
+
+
+def subband_delays(nchans, fch1, foff, tsamp, rng: OracleRange, band, coarse):
+    """Effective delay table [ndm][nchans] of the sub-band form and the
+    largest stage delays (rmax, s2max).
+
+    Channel c of trial i (coarse trial j = i // coarse, middle trial
+    i_j = j*coarse + (n_j - 1)//2) is taken at s(c_b, i) + r(c, D_j): the
+    reference channel's own delay at the fine DM plus the channel's delay
+    relative to the reference at the coarse DM D_j = DM_{i_j}.
+    """
+    ndm = rng.ndm
+    cref = np.array([min((c // band) * band + band - 1, nchans - 1) if foff > 0 else (c // band) * band
+                     for c in range(nchans)], dtype=np.int64)
+    eff = np.zeros((ndm, nchans), dtype=np.int64)
+    rmax = 0
+    for j in range((ndm + coarse - 1) // coarse):
+        i0 = j * coarse
+        nj = min(coarse, ndm - i0)
+        ij = i0 + (nj - 1) // 2
+        rel = subband_rel(nchans, fch1, foff, tsamp, rng.dms[ij], rng.dec, band).astype(np.int64)
+        rmax = max(rmax, int(rel.max()))
+        for i in range(i0, i0 + nj):
+            eff[i] = rng.shifts[i][cref] + rel
+    s2max = int(rng.shifts[:, np.unique(cref)].max()) if ndm else 0
+    return eff, rmax, s2max
+
+
+def dedisperse_subband(x, nchans, fch1, foff, tsamp, rng: OracleRange, band, coarse):
+    """y[i][t] = sum_c xr[c][t + eff(i, c)], t < nsamp_dec - (rmax + s2max)."""
+    eff, rmax, s2max = subband_delays(nchans, fch1, foff, tsamp, rng, band, coarse)
+    xr = range_input(x, rng.dec)
+    L = max(0, rng.nsamp_dec - (rmax + s2max))
+    out = np.zeros((rng.ndm, L), dtype=np.int64)
+    for i in range(rng.ndm):
+        if L:
+            out[i] = dedisperse_row(xr, eff[i].astype(np.int32), 0, L)
+    return out, eff, rmax, s2max
 
 
 # ----------------------------------------------------------------------------

@@ -46,7 +46,9 @@ class aa_range_info(ctypes.Structure):
                 ("tile_samples", ctypes.c_int32), ("stage_channels", ctypes.c_int32),
                 ("stages", ctypes.c_int32), ("span_max", ctypes.c_int32),
                 ("smem_bytes", ctypes.c_int32), ("strategy", ctypes.c_int32),
-                ("grouped_available", ctypes.c_int32), ("grouped_work", ctypes.c_double)]
+                ("grouped_available", ctypes.c_int32), ("grouped_work", ctypes.c_double),
+                ("subband_channels", ctypes.c_int32), ("subband_coarse_trials", ctypes.c_int32),
+                ("subband_work", ctypes.c_double)]
 
 
 class aa_plan_info(ctypes.Structure):
@@ -122,6 +124,7 @@ _SIG = {
     "aa_fil_read_block": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(aa_fil_header), _I64, _I64, _P]),
     "aa_corner_turn_device": (ctypes.c_int, [_P, _I64, _I32, _I64, _P, _I64, _P]),
     "aa_plan_set_sps_clip": (ctypes.c_int, [_P, _I32, _I32]),
+    "aa_plan_set_subband": (ctypes.c_int, [_P, _I32, _I32, _I32]),
     "aa_postprocess_ws_bytes": (ctypes.c_int, [_P, _I64, _I32, _I64,
                                                ctypes.POINTER(ctypes.c_size_t)]),
     "aa_sps_order_device": (ctypes.c_int, [_P, _I64, _I32, _P, _P, _P, _I64, _P, _P,
@@ -312,6 +315,11 @@ def aa_corner_turn_device(d_tm: int, nsamp: int, nchans: int, tm_stride: int, d_
                                       int(cm_pitch), stream), "aa_corner_turn_device")
 
 
+def aa_plan_set_subband(plan, r: int, band_channels: int, coarse_trials: int) -> None:
+    check(lib().aa_plan_set_subband(plan, int(r), int(band_channels), int(coarse_trials)),
+          "aa_plan_set_subband")
+
+
 def aa_plan_set_sps_clip(plan, c16: int, max_iters: int) -> None:
     check(lib().aa_plan_set_sps_clip(plan, int(c16), int(max_iters)), "aa_plan_set_sps_clip")
 
@@ -394,6 +402,7 @@ def aa_dedisperse_f32_mse_device(plan, d_x, nsamp, x_pitch, d_w, d_tmpl, d_loss,
 
 AA_DEDISP_DIRECT = 0
 AA_DEDISP_GROUPED = 1
+AA_DEDISP_SUBBAND = 2
 
 
 def aa_plan_set_strategy(plan, r: int, strategy: int) -> None:

@@ -100,6 +100,10 @@ class Plan:
         max_iters passes; 0 = plain mean and sigma)."""
         abi.aa_plan_set_sps_clip(self.handle, c16, max_iters)
 
+    def set_subband(self, r: int, band_channels: int, coarse_trials: int) -> None:
+        """Sub-band dedispersion (an approximation) for range r."""
+        abi.aa_plan_set_subband(self.handle, r, band_channels, coarse_trials)
+
     def set_strategy(self, r: int, strategy: int) -> None:
         """Dedispersion strategy of range r: abi.AA_DEDISP_DIRECT or
         abi.AA_DEDISP_GROUPED (same result, different grouping of the sums)."""

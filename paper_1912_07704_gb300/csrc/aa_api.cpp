@@ -179,6 +179,70 @@ aa_status order_candidates(const aa_candidate* d_cands, int64_t stored, std::vec
 
 }  // namespace aa
 
+// Sub-band strategy of range r: stage 1 per band into the 16-bit partial
+// series, stage 2 per coarse trial into the range's output rows.
+static aa_status launch_subband(const aa_plan* p, size_t r, const Layout& L, const void* in, int64_t in_pitch,
+                                float* d_out, char* ws, unsigned* err, cudaStream_t s) {
+    const RangePlan& g = p->ranges[r];
+    const SubbandPlan& sb = g.sb;
+    if (L.length[r] <= 0) return AA_OK;
+    if (!sb.d_rel || !sb.d_s2) {
+        set_error("range %zu: sub-band tables are not on the device", r);
+        return AA_ERR_STATE;
+    }
+    auto shape = [](DedispArgs& a, const DirectShape& d) {
+        a.elem = d.elem;
+        a.rw = d.rw;
+        a.cc = d.cc;
+        a.nstage = d.nstage;
+        a.flush = d.flush;
+        a.smem = d.smem;
+        a.grouped = 0;
+    };
+    const int C = p->nchans;
+    const int64_t pitch1 = L.sub_pitch[r];
+    uint16_t* z = reinterpret_cast<uint16_t*>(ws + L.sub_offset[r]);
+    {
+        ProfScope prof(kKSubband1, s);
+        size_t off = 0;
+        for (int b = 0; b < sb.nsub; ++b) {
+            const int c0 = b * sb.k, kb = std::min(C, c0 + sb.k) - c0;
+            DedispArgs a{};
+            a.in = static_cast<const char*>(in) + (int64_t)c0 * in_pitch * g.elem;
+            a.in_pitch = in_pitch;
+            a.nchans = kb;
+            a.nsamp = L.nsamp_dec[r];
+            a.length = L.sub_len[r];
+            a.ndm = sb.ncoarse;
+            a.shifts = sb.d_rel + off;
+            a.out16 = z + (int64_t)b * sb.ncoarse * pitch1;
+            a.out_pitch = pitch1;
+            shape(a, sb.shape1);
+            a.err = err;
+            AA_CUDA(launch_dedisperse(a, s), "sub-band stage 1 launch");
+            off += (size_t)sb.ncoarse * kb;
+        }
+    }
+    ProfScope prof(kKSubband2, s);
+    for (int j = 0; j < sb.ncoarse; ++j) {
+        const int i0 = j * sb.m, nj = std::min(sb.m, g.desc.ndm - i0);
+        DedispArgs a{};
+        a.in = z + (int64_t)j * pitch1;
+        a.in_pitch = (int64_t)sb.ncoarse * pitch1;  // band b's row of coarse trial j
+        a.nchans = sb.nsub;
+        a.nsamp = L.sub_len[r];
+        a.length = L.length[r];
+        a.ndm = nj;
+        a.shifts = sb.d_s2 + (size_t)i0 * sb.nsub;
+        a.out = d_out + L.row_offset[r] + (int64_t)i0 * L.pitch[r];
+        a.out_pitch = L.pitch[r];
+        shape(a, sb.shape2);
+        a.err = err;
+        AA_CUDA(launch_dedisperse(a, s), "sub-band stage 2 launch");
+    }
+    return AA_OK;
+}
+
 extern "C" {
 
 aa_status aa_dedisperse_device(const aa_plan* p, const uint8_t* d_in, int64_t nsamp,
@@ -235,6 +299,11 @@ aa_status aa_dedisperse_device(const aa_plan* p, const uint8_t* d_in, int64_t ns
             const size_t k = std::find(p->decs.begin(), p->decs.end(), g.desc.dec) - p->decs.begin();
             a.in = ws + L.dec_offset[k];
             a.in_pitch = L.dec_pitch[k];
+        }
+        if (g.strategy == 2) {
+            st = launch_subband(p, r, L, a.in, a.in_pitch, d_out, ws, err, s);
+            if (st != AA_OK) return st;
+            continue;
         }
         a.nchans = p->nchans;
         a.nsamp = L.nsamp_dec[r];

@@ -25,7 +25,10 @@ aa_status check(const aa_plan* p, const float* x, int64_t nsamp, int64_t x_pitch
     AA_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
     if (dev != p->device) { set_error("current device differs from the plan's device"); return AA_ERR_STATE; }
     for (const auto& r : p->ranges)
-        if (r.desc.dec != 1) { set_error("the differentiable form supports dec == 1 ranges only"); return AA_ERR_CONFIG; }
+        if (r.desc.dec != 1 || r.strategy == 2) {
+            set_error("the differentiable form supports exact dec == 1 ranges only");
+            return AA_ERR_CONFIG;
+        }
     if (nsamp < 0 || x_pitch < nsamp) { set_error("bad nsamp/x_pitch"); return AA_ERR_ARG; }
     if (nsamp > 0 && (!x || !w)) { set_error("d_x and d_w must be non-NULL"); return AA_ERR_ARG; }
     return AA_OK;

@@ -94,7 +94,7 @@ extern "C" aa_status aa_plan_autotune(aa_plan* p, int64_t nsamp_probe, const cha
     }
     for (size_t r = 0; status == AA_OK && r < p->ranges.size(); ++r) {
         RangePlan& g = p->ranges[r];
-        if (L.length[r] <= 0) continue;
+        if (L.length[r] <= 0 || g.strategy == 2) continue;  // sub-band ranges keep their shape
         const std::string key = cache_key(prop, *p, g);
         int best_cc = g.cc, best_ns = g.nstage, best_strategy = g.strategy;
         auto hit = cache.find(key);

@@ -317,11 +317,32 @@ __device__ __forceinline__ void dedisperse_block(const DedispArgs& a, int ndm_bl
     }
     flush();
 
-    // epilogue: exact integer totals -> FP32 rows
+    // epilogue: exact integer totals -> FP32 rows (or 16-bit rows: the
+    // sub-band partial sums, which the caller keeps below 2^16)
 #pragma unroll
     for (int kk = 0; kk < kDmPerWarp; ++kk) {
         const int d = d0 + warp * kDmPerWarp + kk;
         if (d >= a.ndm) continue;
+        if (a.out16) {
+            uint16_t* row = a.out16 + (int64_t)d * a.out_pitch;
+#pragma unroll
+            for (int j = 0; j < QW; ++j) {
+                const int64_t t = t0 + (int64_t)SPW * (lane + 32 * j);
+                if (t + SPW <= a.length) {
+                    if constexpr (SPW == 4) {
+                        *reinterpret_cast<uint2*>(row + t) =
+                            make_uint2(tot[kk][j][0] | (tot[kk][j][1] << 16), tot[kk][j][2] | (tot[kk][j][3] << 16));
+                    } else {
+                        *reinterpret_cast<uint32_t*>(row + t) = tot[kk][j][0] | (tot[kk][j][1] << 16);
+                    }
+                } else {
+#pragma unroll
+                    for (int q = 0; q < SPW; ++q)
+                        if (t + q < a.length) row[t + q] = (uint16_t)tot[kk][j][q];
+                }
+            }
+            continue;
+        }
         float* row = a.out + (int64_t)d * a.out_pitch;
 #pragma unroll
         for (int j = 0; j < QW; ++j) {

@@ -58,6 +58,36 @@ static_assert(sizeof(GroupRec) == 8 && sizeof(GroupDesc) == 40 && sizeof(GroupMe
               "group table layout");
 static_assert(kGroupTau == kTau, "both strategies tile time alike (launch and queue sizing)");
 
+// Tile shape of the direct (shift-and-sum) kernel for one kind of launch.
+struct DirectShape {
+    int elem = 1, spw = 4;   // bytes per input sample, samples per 32-bit word
+    int rw = 0;              // words per shared-memory row copy
+    int cc = 2, nstage = 2;  // channels per stage, pipeline depth
+    int flush = 2;           // channels between SWAR flushes (multiple of cc)
+    size_t smem = 0;
+};
+// Shape for input samples of `elem` bytes, each at most per_lane_max, and a
+// delay spread of `span` samples across a block of trials; false if no
+// stage of at least two channels fits.
+bool direct_shape(int elem, int32_t span, int per_lane_max, DirectShape& out);
+
+// Sub-band strategy of a range (AA_DEDISP_SUBBAND): channel bands of k
+// channels and coarse trials of m fine trials.  Stage 1 sums each band at
+// the coarse trial's relative delays into 16-bit partial series
+// z[b][j][t]; stage 2 sums the bands at each fine trial's delay of the band's
+// reference (highest-frequency) channel.
+struct SubbandPlan {
+    int k = 0, m = 0, nsub = 0, ncoarse = 0;
+    int32_t rmax = 0;       // largest stage-1 (within-band) delay
+    int32_t s2max = 0;      // largest stage-2 (reference channel) delay
+    DirectShape shape1, shape2;
+    std::vector<int32_t> rel;  // stage 1: per band b, [ncoarse][k_b] (band slices concatenated)
+    std::vector<int32_t> s2;   // stage 2: [ndm][nsub]
+    double work = 1.0;         // (stage-1 + stage-2 adds) / direct adds
+    int32_t* d_rel = nullptr;
+    int32_t* d_s2 = nullptr;
+};
+
 // Per-range strategy, derived once at plan creation (immutable afterwards).
 struct RangePlan {
     aa_dm_range desc{};
@@ -93,6 +123,7 @@ struct RangePlan {
     GroupRec* d_grec = nullptr;
     GroupDesc* d_gdesc = nullptr;
     GroupMember* d_gmem = nullptr;
+    SubbandPlan sb;        // valid once aa_plan_set_subband chose it (strategy 2)
 };
 
 }  // namespace aa
@@ -111,6 +142,7 @@ struct aa_plan {
     bool ready = false;
     void* d_tables = nullptr;
     size_t table_bytes = 0;
+    void* d_sub = nullptr;  // sub-band delay tables of every range using them
 };
 
 namespace aa {
@@ -125,6 +157,9 @@ struct Layout {
     // dedispersion workspace: [error word block][one uint16 buffer per decimation]
     std::vector<int64_t> dec_pitch;   // elements, per entry of plan.decs
     std::vector<int64_t> dec_offset;  // bytes into the workspace
+    // sub-band ranges: 16-bit partial series [nsub][ncoarse][sub_pitch] (bytes
+    // into the workspace; -1 for other ranges) and their length
+    std::vector<int64_t> sub_offset, sub_pitch, sub_len;
     int64_t dedisp_ws = 0;
     // single-pulse workspace: [error word + chunk counter][1/sqrt(w)][row stats]
     //                         [width tables][candidate chunk headers]
@@ -171,7 +206,7 @@ constexpr int64_t kEvaluatedOffset = 16;     // evaluated width-samples counter
 // ------------------------------------------------------------- profiling --
 enum KernelId {
     kKDecimate = 0, kKDedispU8, kKDedispU16, kKRsqrt, kKStats, kKBoxcar, kKF32Fwd, kKF32Adj,
-    kKCornerTurn, kKOrder, kKPeaks2d, kNumKernels
+    kKCornerTurn, kKOrder, kKPeaks2d, kKSubband1, kKSubband2, kNumKernels
 };
 
 // RAII: records CUDA events around a launch on `s` while profiling is on.
@@ -199,7 +234,8 @@ struct DedispArgs {
     int32_t ndm;
     const int32_t* shifts;   // [ndm][nchans]
     float* out;              // row 0 of this range
-    int64_t out_pitch;       // floats
+    uint16_t* out16;         // direct strategy only: 16-bit rows instead of `out` (non-NULL)
+    int64_t out_pitch;       // elements
     int rw, cc, nstage, flush, elem;
     size_t smem;
     unsigned* err;

@@ -41,6 +41,19 @@ static int32_t delay_samples(double fch1, double foff, double f_top, int32_t c, 
     return (int32_t)std::llround(v);
 }
 
+// Delay of channel c relative to channel cref at dispersion measure dm, in
+// samples of a series decimated by dec: round half away from zero of
+// ((kDM*dm)*(delta_c - delta_ref))/(tsamp*dec), delta as in delay_samples.
+static int32_t rel_delay_samples(double fch1, double foff, double f_top, int32_t c, int32_t cref,
+                                 double tsamp, double dm, int32_t dec) {
+    double fc = fch1 + (double)c * foff;
+    double fr = fch1 + (double)cref * foff;
+    double dc = 1.0 / (fc * fc) - 1.0 / (f_top * f_top);
+    double dr = 1.0 / (fr * fr) - 1.0 / (f_top * f_top);
+    double v = kDM * dm * (dc - dr) / (tsamp * (double)dec);
+    return (int32_t)std::llround(v);
+}
+
 // Shared-memory footprint of one dedispersion CTA for a given channel chunk.
 static size_t dedisp_smem(const RangePlan& r, int cc, int nstage) {
     size_t stage = (size_t)cc * r.spw * r.rw * 4;  // spw shifted copies per channel row
@@ -49,6 +62,32 @@ static size_t dedisp_smem(const RangePlan& r, int cc, int nstage) {
 }
 
 size_t dedisp_smem_bytes(const RangePlan& r, int cc, int nstage) { return dedisp_smem(r, cc, nstage); }
+
+static size_t shape_smem(int spw, int rw, int cc, int nstage) {
+    size_t stage = (size_t)cc * spw * rw * 4;
+    size_t tables = (size_t)kDmPerBlock * cc * 4 + (size_t)cc * 4;
+    return (size_t)nstage * (stage + tables) + 64;
+}
+
+bool direct_shape(int elem, int32_t span, int per_lane_max, DirectShape& out) {
+    DirectShape d;
+    d.elem = elem;
+    d.spw = 4 / elem;
+    const int a16 = 16 / elem;  // samples per 16-byte alignment unit
+    const int64_t window = (int64_t)kTau + span + (a16 - 1) + d.spw;
+    d.rw = (int)round_up((window + d.spw - 1) / d.spw, 4);
+    // SWAR flush period: 16-bit lanes hold at most 65535
+    const int max_flush = 65535 / std::max(per_lane_max, 1);
+    const size_t budget = 120 * 1024;
+    d.nstage = 2;
+    d.cc = std::min(24, (max_flush / 2) * 2);
+    while (d.cc > 2 && shape_smem(d.spw, d.rw, d.cc, d.nstage) > budget) d.cc -= 2;
+    if (d.cc < 2 || shape_smem(d.spw, d.rw, d.cc, d.nstage) > 200 * 1024) return false;
+    d.flush = (std::min(max_flush, 256) / d.cc) * d.cc;
+    d.smem = shape_smem(d.spw, d.rw, d.cc, d.nstage);
+    out = d;
+    return true;
+}
 
 // Shared memory of the grouped strategy: the group sums of one batch (two
 // copies each; the input rows are read from global memory).
@@ -281,7 +320,9 @@ Layout make_layout(const aa_plan& p, int64_t nsamp, int32_t max_width) {
     int64_t off = 0;
     for (auto& r : p.ranges) {
         int64_t nd = nsamp / r.desc.dec;
-        int64_t len = std::max<int64_t>(0, nd - r.maxshift);
+        // sub-band ranges: the effective delay is at most rmax + s2max
+        const int64_t ms = r.strategy == 2 ? (int64_t)r.sb.rmax + r.sb.s2max : r.maxshift;
+        int64_t len = std::max<int64_t>(0, nd - ms);
         int64_t pitch = round_up(std::max<int64_t>(len, 1), 64);
         L.nsamp_dec.push_back(nd);
         L.length.push_back(len);
@@ -297,6 +338,22 @@ Layout make_layout(const aa_plan& p, int64_t nsamp, int32_t max_width) {
         L.dec_pitch.push_back(pitch);
         L.dec_offset.push_back(ws);
         ws += round_up((int64_t)p.nchans * pitch * 2, 256);
+    }
+    for (size_t q = 0; q < p.ranges.size(); ++q) {
+        const RangePlan& r = p.ranges[q];
+        if (r.strategy != 2) {
+            L.sub_offset.push_back(-1);
+            L.sub_pitch.push_back(0);
+            L.sub_len.push_back(0);
+            continue;
+        }
+        const int64_t len1 = std::max<int64_t>(0, nsamp / r.desc.dec - r.sb.rmax);
+        const int64_t pitch = round_up(std::max<int64_t>(len1, 1), 64);
+        L.sub_offset.push_back(ws);
+        L.sub_pitch.push_back(pitch);
+        L.sub_len.push_back(len1);
+        // + one staged row window: stage 2 may read that far past the last row
+        ws += round_up((int64_t)r.sb.nsub * r.sb.ncoarse * pitch * 2 + (int64_t)r.sb.shape2.rw * 4 + 256, 256);
     }
     L.dedisp_ws = ws;  // always holds at least the error word
     L.max_width = max_width;
@@ -332,6 +389,54 @@ Layout make_layout(const aa_plan& p, int64_t nsamp, int32_t max_width) {
 }  // namespace aa
 
 using namespace aa;
+
+// Upload every sub-band range's tables into one device block (the plan must
+// be bound; the previous block is released).
+static aa_status upload_subband(aa_plan* p) {
+    // the same per-table rounding as the placement below
+    auto table_bytes = [](size_t n) { return (size_t)round_up((int64_t)n * 4 + 256, 256); };
+    size_t bytes = 0;
+    for (const auto& r : p->ranges)
+        if (r.strategy == 2) bytes += table_bytes(r.sb.rel.size()) + table_bytes(r.sb.s2.size());
+    int prev = -1;
+    cudaGetDevice(&prev);
+    cudaSetDevice(p->device);
+    if (p->d_sub) {
+        cudaFree(p->d_sub);
+        p->d_sub = nullptr;
+    }
+    for (auto& r : p->ranges) r.sb.d_rel = r.sb.d_s2 = nullptr;
+    aa_status st = AA_OK;
+    if (bytes) {
+        void* mem = nullptr;
+        cudaError_t e = cudaMalloc(&mem, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            set_error("cudaMalloc(%zu) for sub-band tables: %s", bytes, cudaGetErrorString(e));
+            st = AA_ERR_NOMEM;
+        } else {
+            p->d_sub = mem;
+            size_t off = 0;
+            for (auto& r : p->ranges) {
+                if (r.strategy != 2) continue;
+                r.sb.d_rel = reinterpret_cast<int32_t*>((char*)mem + off);
+                off += table_bytes(r.sb.rel.size());
+                r.sb.d_s2 = reinterpret_cast<int32_t*>((char*)mem + off);
+                off += table_bytes(r.sb.s2.size());
+                if (e == cudaSuccess)
+                    e = cudaMemcpy(r.sb.d_rel, r.sb.rel.data(), r.sb.rel.size() * 4, cudaMemcpyHostToDevice);
+                if (e == cudaSuccess)
+                    e = cudaMemcpy(r.sb.d_s2, r.sb.s2.data(), r.sb.s2.size() * 4, cudaMemcpyHostToDevice);
+            }
+            if (e != cudaSuccess) {
+                set_error("upload of sub-band tables: %s", cudaGetErrorString(e));
+                st = AA_ERR_CUDA;
+            }
+        }
+    }
+    if (prev >= 0) cudaSetDevice(prev);
+    return st;
+}
 
 extern "C" {
 
@@ -432,11 +537,12 @@ aa_status aa_plan_create(const aa_plan_desc* d, aa_plan** out) {
 
 void aa_plan_destroy(aa_plan* p) {
     if (!p) return;
-    if (p->d_tables) {
+    if (p->d_tables || p->d_sub) {
         int prev = -1;
         cudaGetDevice(&prev);
         cudaSetDevice(p->device);
-        cudaFree(p->d_tables);
+        if (p->d_tables) cudaFree(p->d_tables);
+        if (p->d_sub) cudaFree(p->d_sub);
         if (prev >= 0) cudaSetDevice(prev);
     }
     delete p;
@@ -492,6 +598,8 @@ aa_status aa_plan_bind(aa_plan* p, int device) {
     p->device = device;
     p->ready = true;
     if (prev >= 0 && prev != device) cudaSetDevice(prev);
+    for (const auto& r : p->ranges)
+        if (r.strategy == 2) return upload_subband(p);
     return AA_OK;
 }
 
@@ -550,9 +658,18 @@ aa_status aa_plan_range(const aa_plan* p, int64_t nsamp, int32_t r, aa_range_inf
         info->stages = 2;
         info->tile_samples = kGroupTau;
     }
+    if (g.strategy == 2) {
+        info->stage_channels = g.sb.shape1.cc;
+        info->stages = g.sb.shape1.nstage;
+        info->smem_bytes = (int32_t)std::max(g.sb.shape1.smem, g.sb.shape2.smem);
+        info->maxshift = g.sb.rmax + g.sb.s2max;
+    }
     info->strategy = g.strategy;
     info->grouped_available = g.grouped_ok ? 1 : 0;
     info->grouped_work = g.gwork;
+    info->subband_channels = g.strategy == 2 ? g.sb.k : 0;
+    info->subband_coarse_trials = g.strategy == 2 ? g.sb.m : 0;
+    info->subband_work = g.strategy == 2 ? g.sb.work : 0.0;
     return AA_OK;
 }
 
@@ -580,6 +697,95 @@ aa_status aa_plan_set_sps_clip(aa_plan* p, int32_t c16, int32_t max_iters) {
     if (max_iters > 0 && (c16 < 1 || c16 > 255)) { set_error("c16 %d outside [1, 255]", c16); return AA_ERR_ARG; }
     p->clip_c16 = max_iters > 0 ? c16 : 0;
     p->clip_iters = max_iters;
+    return AA_OK;
+}
+
+aa_status aa_plan_set_subband(aa_plan* p, int32_t r, int32_t band_channels, int32_t coarse_trials) {
+    clear_error();
+    if (!p) { set_error("plan is NULL"); return AA_ERR_ARG; }
+    if (r < 0 || r >= (int32_t)p->ranges.size()) { set_error("range %d out of bounds", r); return AA_ERR_ARG; }
+    RangePlan& g = p->ranges[r];
+    const int C = p->nchans, dec = g.desc.dec, ndm = g.desc.ndm;
+    if (band_channels < 1 || band_channels > C) {
+        set_error("band_channels %d outside [1, %d]", band_channels, C);
+        return AA_ERR_ARG;
+    }
+    if (coarse_trials < 1 || coarse_trials > kDmPerBlock) {
+        set_error("coarse_trials %d outside [1, %d]", coarse_trials, kDmPerBlock);
+        return AA_ERR_ARG;
+    }
+    if ((int64_t)band_channels * 255 * dec > 32767) {
+        set_error("band of %d channels at decimation %d: partial sums exceed the 16-bit stage "
+                  "(band_channels * 255 * dec must be <= 32767)", band_channels, dec);
+        return AA_ERR_CONFIG;
+    }
+    SubbandPlan sb;
+    sb.k = band_channels;
+    sb.m = coarse_trials;
+    sb.nsub = (C + sb.k - 1) / sb.k;
+    sb.ncoarse = (ndm + sb.m - 1) / sb.m;
+    std::vector<int32_t> cref(sb.nsub);
+    for (int b = 0; b < sb.nsub; ++b) {
+        const int c0 = b * sb.k, c1 = std::min(C, c0 + sb.k) - 1;
+        cref[b] = p->foff < 0 ? c0 : c1;  // the band's highest frequency
+    }
+    // stage 1: delay of every channel relative to its band's reference, at
+    // the middle fine trial of each coarse trial
+    sb.rel.assign((size_t)sb.ncoarse * C, 0);
+    int32_t span1 = 0;
+    size_t off = 0;
+    for (int b = 0; b < sb.nsub; ++b) {
+        const int c0 = b * sb.k, kb = std::min(C, c0 + sb.k) - c0;
+        for (int j = 0; j < sb.ncoarse; ++j) {
+            const int nj = std::min(sb.m, ndm - j * sb.m);
+            const int ij = j * sb.m + (nj - 1) / 2;
+            const double dm = g.desc.dm_lo + (double)ij * g.desc.dm_step;
+            for (int cl = 0; cl < kb; ++cl) {
+                const int32_t v = rel_delay_samples(p->fch1, p->foff, p->f_top, c0 + cl, cref[b], p->tsamp, dm, dec);
+                sb.rel[off + (size_t)j * kb + cl] = v;
+                sb.rmax = std::max(sb.rmax, v);
+            }
+        }
+        for (int j0 = 0; j0 < sb.ncoarse; j0 += kDmPerBlock) {
+            const int j1 = std::min(sb.ncoarse, j0 + kDmPerBlock) - 1;
+            for (int cl = 0; cl < kb; ++cl)
+                span1 = std::max(span1, sb.rel[off + (size_t)j1 * kb + cl] - sb.rel[off + (size_t)j0 * kb + cl]);
+        }
+        off += (size_t)sb.ncoarse * kb;
+    }
+    // stage 2: the reference channels' own delays at every fine trial
+    sb.s2.assign((size_t)ndm * sb.nsub, 0);
+    int32_t span2 = 0;
+    for (int i = 0; i < ndm; ++i)
+        for (int b = 0; b < sb.nsub; ++b) {
+            const int32_t v = g.shifts[(size_t)i * C + cref[b]];
+            sb.s2[(size_t)i * sb.nsub + b] = v;
+            sb.s2max = std::max(sb.s2max, v);
+        }
+    for (int j = 0; j < sb.ncoarse; ++j) {
+        const int i0 = j * sb.m, i1 = std::min(ndm, i0 + sb.m) - 1;
+        for (int b = 0; b < sb.nsub; ++b)
+            span2 = std::max(span2, sb.s2[(size_t)i1 * sb.nsub + b] - sb.s2[(size_t)i0 * sb.nsub + b]);
+    }
+    if (!direct_shape(g.elem, span1, 255 * dec, sb.shape1) ||
+        !direct_shape(2, span2, sb.k * 255 * dec, sb.shape2)) {
+        set_error("range %d: sub-band stages do not fit the dedispersion tile (spans %d, %d)", r, span1, span2);
+        return AA_ERR_CONFIG;
+    }
+    sb.work = ((double)sb.ncoarse * C + (double)ndm * sb.nsub) / ((double)ndm * C);
+    const SubbandPlan old = g.sb;
+    const int old_strategy = g.strategy;
+    g.sb = std::move(sb);
+    g.strategy = 2;
+    if (p->ready) {
+        const aa_status st = upload_subband(p);
+        if (st != AA_OK) {
+            g.sb = old;
+            g.strategy = old_strategy;
+            upload_subband(p);
+            return st;
+        }
+    }
     return AA_OK;
 }
 
