@@ -203,9 +203,9 @@ static aa_status launch_subband(const aa_plan* p, size_t r, const Layout& L, con
     const int64_t pitch1 = L.sub_pitch[r];
     uint16_t* z = reinterpret_cast<uint16_t*>(ws + L.sub_offset[r]);
     {
-        ProfScope prof(kKSubband1, s);
         size_t off = 0;
         for (int b = 0; b < sb.nsub; ++b) {
+            ProfScope prof(kKSubband1, s);  // one record per launch
             const int c0 = b * sb.k, kb = std::min(C, c0 + sb.k) - c0;
             DedispArgs a{};
             a.in = static_cast<const char*>(in) + (int64_t)c0 * in_pitch * g.elem;
@@ -223,8 +223,8 @@ static aa_status launch_subband(const aa_plan* p, size_t r, const Layout& L, con
             off += (size_t)sb.ncoarse * kb;
         }
     }
-    ProfScope prof(kKSubband2, s);
     for (int j = 0; j < sb.ncoarse; ++j) {
+        ProfScope prof(kKSubband2, s);
         const int i0 = j * sb.m, nj = std::min(sb.m, g.desc.ndm - i0);
         DedispArgs a{};
         a.in = z + (int64_t)j * pitch1;
