@@ -270,7 +270,7 @@ def bench_ours(args):
         # bands as wide as the 16-bit partial sums allow (at most 64 channels),
         # coarse trials of 16 fine trials
         for r, rg in enumerate(w.ranges):
-            plan.set_subband(r, min(64, 32767 // (255 * rg[3]) // 8 * 8), 16)
+            plan.set_subband(r, min(64, 65535 // (255 * rg[3]) // 8 * 8), 16)
     elif args.strategy != "auto":
         for r in range(len(w.ranges)):
             plan.set_strategy(r, abi.AA_DEDISP_GROUPED if args.strategy == "grouped"

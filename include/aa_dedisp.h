@@ -266,9 +266,10 @@ typedef enum { AA_DEDISP_DIRECT = 0, AA_DEDISP_GROUPED = 1, AA_DEDISP_SUBBAND = 
  * s(c_b, i) + r(c, j(i)) instead of s(c, i).  Sums stay exact integers.  The
  * range's maxshift becomes max r + max s(c_b, .) and its length
  * nsamp_dec - maxshift.  Adds per trial-sample: nchans/coarse_trials + nbands.
+ * Stage 1 stores 16-bit partial sums; stage 2 adds them in 32 bits.
  * AA_ERR_ARG for a bad range, band_channels outside [1, nchans] or
  * coarse_trials outside [1, 16]; AA_ERR_CONFIG when band_channels * 255 * dec
- * > 32767 (the 16-bit partial sums) or the stages do not fit the dedispersion
+ * > 65535 (the 16-bit partial sums) or stage 1 does not fit the dedispersion
  * tile.  aa_plan_set_strategy returns the range to an exact strategy.  Not
  * available in batched runs (aa_batch_create returns AA_ERR_CONFIG) nor in
  * the differentiable form; the autotuner leaves such ranges alone.  Like

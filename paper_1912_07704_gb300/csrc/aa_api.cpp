@@ -180,7 +180,8 @@ aa_status order_candidates(const aa_candidate* d_cands, int64_t stored, std::vec
 }  // namespace aa
 
 // Sub-band strategy of range r: stage 1 per band into the 16-bit partial
-// series, stage 2 per coarse trial into the range's output rows.
+// series (direct kernel), stage 2 over all coarse trials into the range's
+// output rows (32-bit sums).
 static aa_status launch_subband(const aa_plan* p, size_t r, const Layout& L, const void* in, int64_t in_pitch,
                                 float* d_out, char* ws, unsigned* err, cudaStream_t s) {
     const RangePlan& g = p->ranges[r];
@@ -223,23 +224,11 @@ static aa_status launch_subband(const aa_plan* p, size_t r, const Layout& L, con
             off += (size_t)sb.ncoarse * kb;
         }
     }
-    for (int j = 0; j < sb.ncoarse; ++j) {
-        ProfScope prof(kKSubband2, s);
-        const int i0 = j * sb.m, nj = std::min(sb.m, g.desc.ndm - i0);
-        DedispArgs a{};
-        a.in = z + (int64_t)j * pitch1;
-        a.in_pitch = (int64_t)sb.ncoarse * pitch1;  // band b's row of coarse trial j
-        a.nchans = sb.nsub;
-        a.nsamp = L.sub_len[r];
-        a.length = L.length[r];
-        a.ndm = nj;
-        a.shifts = sb.d_s2 + (size_t)i0 * sb.nsub;
-        a.out = d_out + L.row_offset[r] + (int64_t)i0 * L.pitch[r];
-        a.out_pitch = L.pitch[r];
-        shape(a, sb.shape2);
-        a.err = err;
-        AA_CUDA(launch_dedisperse(a, s), "sub-band stage 2 launch");
-    }
+    ProfScope prof(kKSubband2, s);
+    AA_CUDA(launch_subband_stage2(z, (int64_t)sb.ncoarse * pitch1, pitch1, L.sub_len[r], sb.nsub, sb.ncoarse, sb.m,
+                                  g.desc.ndm, sb.d_s2, sb.span2, d_out + L.row_offset[r], L.pitch[r],
+                                  L.length[r], s),
+            "sub-band stage 2 launch");
     return AA_OK;
 }
 

@@ -72,21 +72,30 @@ struct DirectShape {
 bool direct_shape(int elem, int32_t span, int per_lane_max, DirectShape& out);
 
 // Sub-band strategy of a range (AA_DEDISP_SUBBAND): channel bands of k
-// channels and coarse trials of m fine trials.  Stage 1 sums each band at
-// the coarse trial's relative delays into 16-bit partial series
-// z[b][j][t]; stage 2 sums the bands at each fine trial's delay of the band's
-// reference (highest-frequency) channel.
+// channels and coarse trials of m fine trials.  Stage 1 (direct kernel) sums
+// each band at the coarse trial's relative delays into 16-bit partial series
+// z[b][j][t]; stage 2 (its own kernel, 32-bit sums) adds the bands at each
+// fine trial's delay of the band's reference (highest-frequency) channel.
 struct SubbandPlan {
     int k = 0, m = 0, nsub = 0, ncoarse = 0;
     int32_t rmax = 0;       // largest stage-1 (within-band) delay
     int32_t s2max = 0;      // largest stage-2 (reference channel) delay
-    DirectShape shape1, shape2;
+    int32_t span2 = 0;      // largest stage-2 delay spread within a coarse trial
+    DirectShape shape1;     // stage 1 runs on the direct kernel
     std::vector<int32_t> rel;  // stage 1: per band b, [ncoarse][k_b] (band slices concatenated)
     std::vector<int32_t> s2;   // stage 2: [ndm][nsub]
     double work = 1.0;         // (stage-1 + stage-2 adds) / direct adds
     int32_t* d_rel = nullptr;
     int32_t* d_s2 = nullptr;
 };
+
+// Sub-band stage 2 (32-bit accumulation): shared memory for nsub bands and a
+// delay span across the coarse trial's fine trials; also the staged window
+// length and the bands staged at once.
+size_t subband_stage2_smem(int nsub, int span, int& swin, int& nb_chunk);
+cudaError_t launch_subband_stage2(const uint16_t* z, int64_t band_stride, int64_t pitch1, int64_t len1, int nsub,
+                                  int ncoarse, int m, int ndm, const int32_t* s2, int span, float* out,
+                                  int64_t out_pitch, int64_t length, cudaStream_t s);
 
 // Per-range strategy, derived once at plan creation (immutable afterwards).
 struct RangePlan {

@@ -352,8 +352,7 @@ Layout make_layout(const aa_plan& p, int64_t nsamp, int32_t max_width) {
         L.sub_offset.push_back(ws);
         L.sub_pitch.push_back(pitch);
         L.sub_len.push_back(len1);
-        // + one staged row window: stage 2 may read that far past the last row
-        ws += round_up((int64_t)r.sb.nsub * r.sb.ncoarse * pitch * 2 + (int64_t)r.sb.shape2.rw * 4 + 256, 256);
+        ws += round_up((int64_t)r.sb.nsub * r.sb.ncoarse * pitch * 2, 256);
     }
     L.dedisp_ws = ws;  // always holds at least the error word
     L.max_width = max_width;
@@ -661,7 +660,8 @@ aa_status aa_plan_range(const aa_plan* p, int64_t nsamp, int32_t r, aa_range_inf
     if (g.strategy == 2) {
         info->stage_channels = g.sb.shape1.cc;
         info->stages = g.sb.shape1.nstage;
-        info->smem_bytes = (int32_t)std::max(g.sb.shape1.smem, g.sb.shape2.smem);
+        int swin = 0, nbc = 0;
+        info->smem_bytes = (int32_t)std::max(g.sb.shape1.smem, subband_stage2_smem(g.sb.nsub, g.sb.span2, swin, nbc));
         info->maxshift = g.sb.rmax + g.sb.s2max;
     }
     info->strategy = g.strategy;
@@ -714,9 +714,9 @@ aa_status aa_plan_set_subband(aa_plan* p, int32_t r, int32_t band_channels, int3
         set_error("coarse_trials %d outside [1, %d]", coarse_trials, kDmPerBlock);
         return AA_ERR_ARG;
     }
-    if ((int64_t)band_channels * 255 * dec > 32767) {
-        set_error("band of %d channels at decimation %d: partial sums exceed the 16-bit stage "
-                  "(band_channels * 255 * dec must be <= 32767)", band_channels, dec);
+    if ((int64_t)band_channels * 255 * dec > 65535) {
+        set_error("band of %d channels at decimation %d: partial sums exceed 16 bits "
+                  "(band_channels * 255 * dec must be <= 65535)", band_channels, dec);
         return AA_ERR_CONFIG;
     }
     SubbandPlan sb;
@@ -767,11 +767,11 @@ aa_status aa_plan_set_subband(aa_plan* p, int32_t r, int32_t band_channels, int3
         for (int b = 0; b < sb.nsub; ++b)
             span2 = std::max(span2, sb.s2[(size_t)i1 * sb.nsub + b] - sb.s2[(size_t)i0 * sb.nsub + b]);
     }
-    if (!direct_shape(g.elem, span1, 255 * dec, sb.shape1) ||
-        !direct_shape(2, span2, sb.k * 255 * dec, sb.shape2)) {
-        set_error("range %d: sub-band stages do not fit the dedispersion tile (spans %d, %d)", r, span1, span2);
+    if (!direct_shape(g.elem, span1, 255 * dec, sb.shape1)) {
+        set_error("range %d: sub-band stage 1 does not fit the dedispersion tile (span %d)", r, span1);
         return AA_ERR_CONFIG;
     }
+    sb.span2 = span2;
     sb.work = ((double)sb.ncoarse * C + (double)ndm * sb.nsub) / ((double)ndm * C);
     const SubbandPlan old = g.sb;
     const int old_strategy = g.strategy;

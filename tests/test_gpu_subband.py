@@ -92,3 +92,11 @@ def test_batch_refuses_subband():
     from paper_1912_07704_gb300.api import Batch
     with pytest.raises(abi.AAError, match="AA_ERR_CONFIG"):
         Batch([p], [8000], 16, 6.0, capacity=1024)
+
+
+def test_many_bands_staged_in_chunks(oracle):
+    """512 bands: stage 2 stages its band windows in several chunks."""
+    C, fch1, foff, ts, T = 1024, 1500.0, -0.29296875, 64e-6, 6000
+    ranges = [(0.0, 0.5, 40, 1), (20.0, 1.0, 9, 2)]
+    x = np.random.default_rng(44).integers(0, 256, size=(C, T), dtype=np.uint8)
+    _check(oracle, C, fch1, foff, ts, ranges, x, [(2, 16), (3, 7)])

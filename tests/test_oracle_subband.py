@@ -124,7 +124,7 @@ def test_set_subband_argument_checks():
     for args, code in [((2, 16, 8), "AA_ERR_ARG"), ((0, 0, 8), "AA_ERR_ARG"),
                        ((0, 101, 8), "AA_ERR_ARG"), ((0, 16, 0), "AA_ERR_ARG"),
                        ((0, 16, 17), "AA_ERR_ARG"), ((0, 129, 8), "AA_ERR_ARG"),
-                       ((1, 17, 8), "AA_ERR_CONFIG")]:
+                       ((1, 33, 8), "AA_ERR_CONFIG")]:
         with pytest.raises(abi.AAError, match=code):
             p.set_subband(*args)
-    p.set_subband(1, 16, 8)  # 16 * 255 * 8 = 32640 fits
+    p.set_subband(1, 32, 8)  # 32 * 255 * 8 = 65280 fits 16 bits
