@@ -186,13 +186,29 @@ def workload_algorithmics(plan, w):
                 in_bytes=in_bytes, dd_bytes=dd_bytes, lay=lay)
 
 
-def run_oracle_sample(w, x_host, rows_per_range: int, threads: int):
+def subband_bands(dec: int) -> int:
+    """Bench sub-band width: as wide as 16-bit partial sums allow, at most 64."""
+    return min(64, 65535 // (255 * dec) // 8 * 8)
+
+
+SUBBAND_COARSE = 16
+
+
+def run_oracle_sample(w, x_host, rows_per_range: int, threads: int, subband: bool = False):
     """Oracle (CPU) on a bounded sample: `rows_per_range` full-length DM trials
     of every range (decimated inputs prepared outside the timed part and
-    amortised over all trials).  Returns (DM-trial samples, seconds, cores, desc)."""
+    amortised over all trials); with `subband`, the oracle's sub-band form
+    (the same sum at the effective delays).  Returns (DM-trial samples,
+    seconds, cores, desc)."""
     from oracle import oracle as o
     cores = o.set_threads(threads)
     pl = o.plan(w.nchans, w.fch1, w.foff, w.tsamp, w.ranges, w.nsamp)
+    if subband:  # effective delays and lengths of the sub-band form
+        for g in pl:
+            eff, rmax, s2max = o.subband_delays(w.nchans, w.fch1, w.foff, w.tsamp, g,
+                                                subband_bands(g.dec), SUBBAND_COARSE)
+            g.shifts = eff.astype(np.int32)
+            g.length = max(0, g.nsamp_dec - (rmax + s2max))
     t_dec = 0.0
     inputs = []
     for g in pl:
@@ -212,7 +228,7 @@ def run_oracle_sample(w, x_host, rows_per_range: int, threads: int):
             nrows += 1
     secs = t_rows + t_dec * nrows / ntrials
     desc = (f"{rows_per_range} full-length DM trials per range ({nrows} of {ntrials}), "
-            f"decimation time amortised over all trials")
+            f"decimation time amortised over all trials" + (", sub-band form" if subband else ""))
     return samples, secs, cores, desc
 
 
@@ -270,7 +286,7 @@ def bench_ours(args):
         # bands as wide as the 16-bit partial sums allow (at most 64 channels),
         # coarse trials of 16 fine trials
         for r, rg in enumerate(w.ranges):
-            plan.set_subband(r, min(64, 65535 // (255 * rg[3]) // 8 * 8), 16)
+            plan.set_subband(r, subband_bands(rg[3]), SUBBAND_COARSE)
     elif args.strategy != "auto":
         for r in range(len(w.ranges)):
             plan.set_strategy(r, abi.AA_DEDISP_GROUPED if args.strategy == "grouped"
@@ -424,7 +440,8 @@ def bench_ours(args):
     cpu = None
     if not args.no_cpu_baseline and rank == 0 and ws == 1:
         xh = x[:, :nsamp].cpu().numpy()
-        s, secs, cores, desc = run_oracle_sample(w, xh, 1, os.cpu_count() or 1)
+        s, secs, cores, desc = run_oracle_sample(w, xh, 1, os.cpu_count() or 1,
+                                                 subband=args.strategy == "subband")
         cpu = {"value": s / secs, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
 
     if rank == 0:
