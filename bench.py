@@ -151,7 +151,7 @@ def build_input(plan, w, device):
 # when the kernel changes until it is captured again.
 NCU_TRAFFIC = {
     ("dedisperse_u8", "grouped"): {
-        "small_read_bytes": 542_319_872, "small_write_bytes": 739_636_480,
+        "small_read_bytes": 545_137_920, "small_write_bytes": 744_004_352,
         "small_output_samples": 1500 * 128687,
         "capture": "profiles/dedisperse_grouped_u8_ska-4096ch-2^17.md"},
     ("sps_boxcar", "pruned"): {
