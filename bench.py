@@ -294,6 +294,8 @@ def bench_ours(args):
     if args.sps_clip:
         c16, iters = (int(v) for v in args.sps_clip.split(","))
         plan.set_sps_clip(c16, iters)
+    if args.sps_ladder:
+        plan.set_sps_ladder(args.sps_ladder)
     plan.bind(local)
     info = plan.query(w.nsamp, w.max_width)
     x = build_input(plan, w, "cuda")
@@ -458,6 +460,8 @@ def bench_ours(args):
                        "statistics": (f"k-sigma clipped, k = {args.sps_clip.split(',')[0]}/16, "
                                       f"<= {args.sps_clip.split(',')[1]} passes"
                                       if args.sps_clip else "plain mean and sigma"),
+                       "widths": (f"sparse ladder, growth {args.sps_ladder}/16 (approximate)"
+                                  if args.sps_ladder else "every width 1..W"),
                        "dedispersion": [_strategy_name(abi.aa_plan_range(plan.handle, nsamp, r))
                                         for r in range(len(w.ranges))],
                        "l2": (f"inputs larger than L2 ({alg['in_bytes'] / 1e9:.2f} GB filterbank, "
@@ -778,6 +782,8 @@ def main():
                          "subband: the approximate two-stage sum, a different metric)")
     ap.add_argument("--sps-clip", default="",
                     help="C16,ITERS: k-sigma clipped statistics (k = C16/16), e.g. 48,4")
+    ap.add_argument("--sps-ladder", type=int, default=0,
+                    help="G16: sparse boxcar width ladder of growth G16/16 (approximate), e.g. 24")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

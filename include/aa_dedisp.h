@@ -283,6 +283,19 @@ aa_status aa_plan_set_subband(aa_plan* plan, int32_t r, int32_t band_channels,
  * Like aa_plan_autotune, call it while no work of the plan is in flight. */
 aa_status aa_plan_set_strategy(aa_plan* plan, int32_t r, int32_t strategy);
 
+/* Sparse width ladder for the single-pulse search: an approximation that
+ * evaluates only some boxcar widths when W is large (the cited search method
+ * covers large widths sparsely; Sec. 1 names boxcar filters with peak
+ * finding).  Widths form chunks of 16 (chunk c = widths 16c+1 .. 16c+16);
+ * chunks 0-3 (widths 1..64) always take part, then chunk c_0 = 4 and
+ * c_{n+1} = max(c_n + 1, ceil(c_n * growth_x16 / 16)), i.e. chunk starts
+ * growing geometrically by growth_x16/16.  B(t) is then the largest SNR over
+ * the widths taking part and a candidate's width the smallest of them
+ * reaching it.  growth_x16 = 0 restores every width 1..W (the default);
+ * otherwise it must lie in [17, 64].  Applies to the searches started (and
+ * batches created) after the call.  AA_ERR_ARG for other values. */
+aa_status aa_plan_set_sps_ladder(aa_plan* plan, int32_t growth_x16);
+
 /* Robust statistics for the single-pulse search (outlier rejection).  The
  * mean and standard deviation that normalise each dedispersed series' SNR
  * (Sec. 1: boxcar filters with peak finding) are by default those of all its

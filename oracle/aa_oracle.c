@@ -256,6 +256,44 @@ void oracle_boxcar(const int64_t* y, int64_t n, double mu, double sigma, int32_t
     }
 }
 
+/* oracle_boxcar over a subset of widths: width w (1 <= w <= W) takes part
+ * iff wset[w - 1] != 0; B, the smallest maximising width and the margin are
+ * those of the widths taking part. */
+void oracle_boxcar_widths(const int64_t* y, int64_t n, double mu, double sigma, int32_t W,
+                          const uint8_t* wset, int64_t t0, int64_t t1, double* B, int32_t* wbest,
+                          double* margin)
+{
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t t = t0; t < t1; ++t) {
+        int64_t k = t - t0;
+        if (sigma == 0.0) {
+            B[k] = 0.0;
+            wbest[k] = 1;
+            margin[k] = INFINITY;
+            continue;
+        }
+        int64_t wmax = n - t < (int64_t)W ? n - t : (int64_t)W;
+        int64_t S = 0;
+        double best = -INFINITY, second = -INFINITY;
+        int32_t bw = 0;
+        for (int64_t w = 1; w <= wmax; ++w) {
+            S += y[t + w - 1];
+            if (!wset[w - 1]) continue;
+            double snr = ((double)S - (double)w * mu) / (sigma * sqrt((double)w));
+            if (snr > best) {
+                second = best;
+                best = snr;
+                bw = (int32_t)w;
+            } else if (snr > second) {
+                second = snr;
+            }
+        }
+        B[k] = best;
+        wbest[k] = bw;
+        margin[k] = best - second;
+    }
+}
+
 /* Thresholded local maxima of B over [0, n): returns the number found and
  * writes up to cap indices. */
 int64_t oracle_peaks(const double* B, int64_t n, double thr, int64_t* out_t, int64_t cap)

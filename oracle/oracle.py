@@ -74,6 +74,8 @@ def lib():
                                              ctypes.POINTER(f64), ctypes.POINTER(i64)]
         L.oracle_moments_clipped.restype = None
         L.oracle_boxcar.argtypes = [vp, i64, f64, f64, i32, i64, i64, vp, vp, vp]
+        L.oracle_boxcar_widths.argtypes = [vp, i64, f64, f64, i32, vp, i64, i64, vp, vp, vp]
+        L.oracle_boxcar_widths.restype = None
         L.oracle_boxcar.restype = None
         L.oracle_peaks.argtypes = [vp, i64, f64, vp, i64]
         L.oracle_peaks.restype = i64
@@ -214,8 +216,24 @@ def row_moments(y: np.ndarray, clip=None):
     return moments(y)
 
 
-def boxcar(y: np.ndarray, mu: float, sigma: float, W: int, t0: int = 0, t1: int | None = None):
-    """(B, wbest, margin) for t in [t0, t1)."""
+def ladder_widths(W: int, g16: int) -> np.ndarray:
+    """Widths 1..W taking part in the sparse width ladder with growth g16/16:
+    width chunks of 16 (chunk c = widths 16c+1 .. 16c+16); chunks 0-3 always,
+    then c_0 = 4 and c_{n+1} = max(c_n + 1, ceil(c_n * g16 / 16))."""
+    nch = -(-W // 16)
+    on = np.zeros(nch, bool)
+    on[:min(4, nch)] = True
+    c = 4
+    while c < nch:
+        on[c] = True
+        c = max(c + 1, -(-(c * g16) // 16))
+    return np.repeat(on, 16)[:W]
+
+
+def boxcar(y: np.ndarray, mu: float, sigma: float, W: int, t0: int = 0, t1: int | None = None,
+           wset: np.ndarray | None = None):
+    """(B, wbest, margin) for t in [t0, t1); wset: optional bool mask of the
+    widths 1..W taking part."""
     y = np.ascontiguousarray(y, dtype=np.int64)
     n = y.size
     t1 = n if t1 is None else t1
@@ -223,9 +241,14 @@ def boxcar(y: np.ndarray, mu: float, sigma: float, W: int, t0: int = 0, t1: int 
     B = np.empty(m, np.float64)
     wb = np.empty(m, np.int32)
     mg = np.empty(m, np.float64)
-    if m:
+    if m and wset is None:
         lib().oracle_boxcar(_ptr(y), n, float(mu), float(sigma), int(W), int(t0), int(t1),
                             _ptr(B), _ptr(wb), _ptr(mg))
+    elif m:
+        ws = np.ascontiguousarray(wset, dtype=np.uint8)
+        assert ws.size == W
+        lib().oracle_boxcar_widths(_ptr(y), n, float(mu), float(sigma), int(W), _ptr(ws), int(t0),
+                                   int(t1), _ptr(B), _ptr(wb), _ptr(mg))
     return B, wb, mg
 
 
@@ -247,11 +270,12 @@ class Candidate:
 
 
 def search_row(y: np.ndarray, W: int, thr: float, dm_index: int, rng: int,
-               t_lo: int = 0, t_hi: int | None = None, clip=None):
+               t_lo: int = 0, t_hi: int | None = None, clip=None, wset=None):
     """Candidates of one DM series with t in [t_lo, t_hi).
 
     Returns (candidates, B, wbest, mu, sigma) with B/wbest over [t_lo, t_hi).
-    clip = (c16, max_iters) takes mu, sigma from iterative k-sigma clipping.
+    clip = (c16, max_iters) takes mu, sigma from iterative k-sigma clipping;
+    wset restricts the widths (bool mask over 1..W, e.g. ladder_widths).
     Rows with sigma == 0 have B = 0 and no candidates.  Near-decision entries
     (|B - thr| < FRAGILE_THR, neighbour or width-argmax margin < FRAGILE_CMP)
     are flagged fragile; entries just below the threshold that could flip
@@ -262,7 +286,7 @@ def search_row(y: np.ndarray, W: int, thr: float, dm_index: int, rng: int,
     t_hi = n if t_hi is None else min(t_hi, n)
     mu, sigma = row_moments(y, clip)
     a, b = max(0, t_lo - 1), min(n, t_hi + 1)
-    B, wb, mg = boxcar(y, mu, sigma, W, a, b)
+    B, wb, mg = boxcar(y, mu, sigma, W, a, b, wset)
     cands = []
     if sigma == 0.0 or t_hi <= t_lo:
         return cands, B[t_lo - a:t_hi - a], wb[t_lo - a:t_hi - a], mu, sigma

@@ -125,6 +125,7 @@ _SIG = {
     "aa_corner_turn_device": (ctypes.c_int, [_P, _I64, _I32, _I64, _P, _I64, _P]),
     "aa_plan_set_sps_clip": (ctypes.c_int, [_P, _I32, _I32]),
     "aa_plan_set_subband": (ctypes.c_int, [_P, _I32, _I32, _I32]),
+    "aa_plan_set_sps_ladder": (ctypes.c_int, [_P, _I32]),
     "aa_postprocess_ws_bytes": (ctypes.c_int, [_P, _I64, _I32, _I64,
                                                ctypes.POINTER(ctypes.c_size_t)]),
     "aa_sps_order_device": (ctypes.c_int, [_P, _I64, _I32, _P, _P, _P, _I64, _P, _P,
@@ -313,6 +314,10 @@ def aa_corner_turn_device(d_tm: int, nsamp: int, nchans: int, tm_stride: int, d_
                           cm_pitch: int, stream: int = 0) -> None:
     check(lib().aa_corner_turn_device(d_tm, int(nsamp), int(nchans), int(tm_stride), d_cm,
                                       int(cm_pitch), stream), "aa_corner_turn_device")
+
+
+def aa_plan_set_sps_ladder(plan, growth_x16: int) -> None:
+    check(lib().aa_plan_set_sps_ladder(plan, int(growth_x16)), "aa_plan_set_sps_ladder")
 
 
 def aa_plan_set_subband(plan, r: int, band_channels: int, coarse_trials: int) -> None:

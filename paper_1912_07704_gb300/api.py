@@ -100,6 +100,10 @@ class Plan:
         max_iters passes; 0 = plain mean and sigma)."""
         abi.aa_plan_set_sps_clip(self.handle, c16, max_iters)
 
+    def set_sps_ladder(self, growth_x16: int) -> None:
+        """Sparse boxcar width ladder for later searches (0: every width)."""
+        abi.aa_plan_set_sps_ladder(self.handle, growth_x16)
+
     def set_subband(self, r: int, band_channels: int, coarse_trials: int) -> None:
         """Sub-band dedispersion (an approximation) for range r."""
         abi.aa_plan_set_subband(self.handle, r, band_channels, coarse_trials)

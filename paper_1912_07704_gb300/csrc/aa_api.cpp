@@ -376,6 +376,7 @@ aa_status aa_sps_search_device(const aa_plan* p, int64_t nsamp, const float* d_d
         a.prune = d_snr_out ? 0 : 1;  // B(t) everywhere requested: exhaustive
         a.clip_c16 = p->clip_c16;
         a.clip_iters = p->clip_iters;
+        a.ladder_g16 = p->ladder_g16;
         a.err = err;
         a.chunks = chunks;
         a.nchunks = nchunks;

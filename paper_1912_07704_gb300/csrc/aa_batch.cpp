@@ -318,6 +318,7 @@ aa_status aa_batch_create(aa_plan* const* plans, const int64_t* nsamps, int32_t 
                 s.prune = 1;
                 s.clip_c16 = pl.clip_c16;
                 s.clip_iters = pl.clip_iters;
+                s.ladder_g16 = pl.ladder_g16;
                 s.beam = bi;
                 s.chunks = b->d_chunks;
                 s.nchunks = &b->d_counts[1];

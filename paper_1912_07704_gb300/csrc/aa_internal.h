@@ -147,6 +147,8 @@ struct aa_plan {
     // single-pulse statistics: iterative k-sigma clipping, k = clip_c16 / 16,
     // at most clip_iters clipping passes (0: plain mean and sigma)
     int32_t clip_c16 = 0, clip_iters = 0;
+    // boxcar widths: 0 every width 1..W, else the sparse ladder of growth ladder_g16 / 16
+    int32_t ladder_g16 = 0;
     int device = -1;
     bool ready = false;
     void* d_tables = nullptr;
@@ -304,6 +306,7 @@ struct SpsArgs {
     int32_t prune;          // skip width blocks bounded below the threshold
     int32_t clip_c16;       // k-sigma clipping of the statistics, k = clip_c16 / 16
     int32_t clip_iters;     // clipping passes (0: plain statistics)
+    int32_t ladder_g16;     // sparse width ladder growth x16 (0: every width)
     int32_t beam;           // beam id stored in candidate records (batched mode)
     unsigned long long* evaluated;  // width-samples actually evaluated (instrumentation)
     CandChunk* chunks;      // chunk headers (all ranges)

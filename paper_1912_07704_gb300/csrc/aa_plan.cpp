@@ -700,6 +700,17 @@ aa_status aa_plan_set_sps_clip(aa_plan* p, int32_t c16, int32_t max_iters) {
     return AA_OK;
 }
 
+aa_status aa_plan_set_sps_ladder(aa_plan* p, int32_t growth_x16) {
+    clear_error();
+    if (!p) { set_error("plan is NULL"); return AA_ERR_ARG; }
+    if (growth_x16 != 0 && (growth_x16 < 17 || growth_x16 > 64)) {
+        set_error("growth_x16 %d: 0 or within [17, 64]", growth_x16);
+        return AA_ERR_ARG;
+    }
+    p->ladder_g16 = growth_x16;
+    return AA_OK;
+}
+
 aa_status aa_plan_set_subband(aa_plan* p, int32_t r, int32_t band_channels, int32_t coarse_trials) {
     clear_error();
     if (!p) { set_error("plan is NULL"); return AA_ERR_ARG; }

@@ -47,6 +47,24 @@ __device__ __forceinline__ void add128(unsigned long long& hi, unsigned long lon
 
 constexpr int kStatsThreads = 512;
 
+// Sparse width ladder: width chunk c (widths 16c+1 .. 16c+16) takes part iff
+// its bit is set.  Chunks 0-3 always; then c_0 = 4 and
+// c_{n+1} = max(c_n + 1, ceil(c_n * g16 / 16)).  Whole CTA; words past
+// nchunks are cleared.
+constexpr int kLadderWords = 65536 / kSpsSlots / 32;  // chunks of the widest search
+__device__ __forceinline__ void fill_ladder(uint32_t* mask, int nchunks, int g16) {
+    for (int i = threadIdx.x; i < kLadderWords; i += blockDim.x) mask[i] = 0;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int c = 0; c < min(4, nchunks); ++c) mask[c >> 5] |= 1u << (c & 31);
+        for (int c = 4; c < nchunks; c = max(c + 1, (c * g16 + 15) / 16)) mask[c >> 5] |= 1u << (c & 31);
+    }
+}
+__device__ __forceinline__ bool ladder_has(const uint32_t* mask, int w) {  // width w >= 1
+    const int c = (w - 1) / kSpsSlots;
+    return (mask[c >> 5] >> (c & 31)) & 1u;
+}
+
 // Statistics of one series (row) and its width table; whole CTA.
 //
 // Exact integer sums N, S1 = sum y, S2 = sum y^2 (128-bit) over the kept
@@ -338,7 +356,7 @@ __device__ __forceinline__ float warp_segment_bound(const float* __restrict__ P,
 __device__ __forceinline__ int boxcar_prefix(const float* __restrict__ P,
                                              const float2* __restrict__ tab, int wpad,
                                              const float (&base)[M], const WarpBound& bnd,
-                                             float (&B)[M], int (&C)[M]) {
+                                             const uint32_t* lmask, float (&B)[M], int (&C)[M]) {
     const float* pb = P + M * threadIdx.x;
     int evaluated = 0;
 #pragma unroll
@@ -370,6 +388,7 @@ __device__ __forceinline__ int boxcar_prefix(const float* __restrict__ P,
                 continue;
             }
         }
+        if (lmask && !ladder_has(lmask, w0 + 1)) continue;  // chunk not on the width ladder
         ++evaluated;
         float win[2 * M];  // win[k] = P[p_thread + w0 + k]
 #pragma unroll
@@ -412,7 +431,8 @@ __device__ __forceinline__ int boxcar_prefix(const float* __restrict__ P,
 // exceed 2^24.  Same SNR arithmetic as boxcar_fast (fmaf of the correctly
 // rounded sum).
 __device__ __noinline__ float boxcar_exact_slot(const float* __restrict__ ys,
-                                                const float2* __restrict__ tab, int wpad, int i) {
+                                                const float2* __restrict__ tab, int wpad, int i,
+                                                const uint32_t* lmask) {
     const float* yb = ys + M * threadIdx.x + i;
     long long S = 0;
     float best = -FLT_MAX;
@@ -420,6 +440,7 @@ __device__ __noinline__ float boxcar_exact_slot(const float* __restrict__ ys,
         const float v = yb[w - 1];
         if (v < kSentinelTest) break;  // window left [0, L): later widths invalid too
         S += (long long)v;
+        if (lmask && !ladder_has(lmask, w)) continue;
         const float2 rc = tab[w - 1];
         best = fmaxf(best, fmaf(__ll2float_rn(S), rc.x, rc.y));
     }
@@ -438,6 +459,9 @@ __host__ __device__ constexpr int sps_region_bytes(int wpad) {
 __device__ __forceinline__ void boxcar_block(const SpsArgs& a, int ntiles, int64_t bid, float* sm) {
     __shared__ long long scratch[2 * NT / 32];
     __shared__ unsigned long long s_base;
+    __shared__ uint32_t s_ladder[kLadderWords];
+    const uint32_t* lmask = a.ladder_g16 > 0 ? s_ladder : nullptr;
+    if (lmask) fill_ladder(s_ladder, a.wpad / M, a.ladder_g16);  // visible after the staging barrier
     const int wpad = a.wpad;
     const int ylen = kSpsTile + wpad + M;
     float* ys = sm;
@@ -540,13 +564,13 @@ __device__ __forceinline__ void boxcar_block(const SpsArgs& a, int ntiles, int64
         bnd.ylen = ylen;
         bnd.p_first = M * 32 * warp;
         bnd.active = a.prune != 0;
-        const int chunks = boxcar_prefix(P, tab, wpad, base, bnd, B, C);
+        const int chunks = boxcar_prefix(P, tab, wpad, base, bnd, lmask, B, C);
         if (a.evaluated && (threadIdx.x & 31) == 0)
             atomicAdd(a.evaluated, (unsigned long long)chunks * 32ull * M * M);
     } else {
 #pragma unroll
         for (int i = 0; i < M; ++i) {
-            B[i] = boxcar_exact_slot(ys, tab, wpad, i);
+            B[i] = boxcar_exact_slot(ys, tab, wpad, i, lmask);
             C[i] = 0;
         }
         if (a.evaluated && threadIdx.x == 0)
@@ -612,7 +636,7 @@ __device__ __forceinline__ void boxcar_block(const SpsArgs& a, int ntiles, int64
             const float b0 = P[p];
             for (int w0 = cw0; w0 < wmax; w0 += 32) {
                 const int w = w0 + lane + 1;
-                if (w <= wmax) {
+                if (w <= wmax && (!lmask || ladder_has(lmask, w))) {
                     const float2 rc = __ldg(gtab + w - 1);
                     const float snr = fmaf(P[p + w] - b0, rc.x, rc.y);
                     if (snr > best) { best = snr; bw = w; }
@@ -633,7 +657,7 @@ __device__ __forceinline__ void boxcar_block(const SpsArgs& a, int ntiles, int64
                 }
                 const long long S = base + v;
                 base += __shfl_sync(0xffffffffu, v, 31);
-                if (w <= wmax) {
+                if (w <= wmax && (!lmask || ladder_has(lmask, w))) {
                     const float2 rc = __ldg(gtab + w - 1);
                     const float snr = fmaf(__ll2float_rn(S), rc.x, rc.y);
                     if (snr > best) { best = snr; bw = w; }
