@@ -364,10 +364,11 @@ __device__ __forceinline__ int boxcar_prefix(const float* __restrict__ P,
         B[i] = -FLT_MAX;
         C[i] = 0;
     }
+    constexpr int kSeg = 128;  // widths per segment inside the wide power-of-two blocks
     for (int w0 = 0; w0 < wpad; w0 += M) {
         const bool blk = (w0 & (w0 - 1)) == 0;  // first chunk of a power-of-two block
-        if (bnd.active && w0 >= 16 && (blk || (w0 >= 256 && (w0 & 127) == 0))) {
-            int w_end = blk ? 2 * w0 : w0 + 128;
+        if (bnd.active && w0 >= 16 && (blk || (w0 >= 2 * kSeg && (w0 & (kSeg - 1)) == 0))) {
+            int w_end = blk ? 2 * w0 : w0 + kSeg;
             bool skip = bnd.pmin == FLT_MAX;
             if (!skip) {
                 float bmin = B[0];
@@ -378,8 +379,8 @@ __device__ __forceinline__ int boxcar_prefix(const float* __restrict__ P,
                     bmin = fminf(bmin, __shfl_xor_sync(0xffffffffu, bmin, o));
                 const float floor_b = fmaxf(bnd.cut, bmin);
                 skip = warp_segment_bound(P, bnd, w0 + 1, min(w_end, bnd.max_width)) < floor_b;
-                if (!skip && blk && w0 >= 256) {
-                    w_end = w0 + 128;
+                if (!skip && blk && w0 >= 2 * kSeg) {
+                    w_end = w0 + kSeg;
                     skip = warp_segment_bound(P, bnd, w0 + 1, min(w_end, bnd.max_width)) < floor_b;
                 }
             }
