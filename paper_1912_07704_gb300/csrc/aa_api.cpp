@@ -2,6 +2,7 @@
 // the host-buffer path with library-owned results (arXiv:1912.07704 Sec. 2.3
 // memory requests, Sec. 2.4 ownership, Sec. 3.1 usage steps 4-8).
 #include <algorithm>
+#include <mutex>
 #include <cstring>
 #include <memory>
 #include <new>
@@ -25,11 +26,61 @@ struct aa_dd_result {
     int device = -1;
 };
 
+namespace aa {
+namespace {
+// Page-locked host blocks for ordered candidate lists, kept for reuse: a list
+// of tens of millions of records is then copied at the link's speed into
+// memory that is already mapped (a fresh pageable allocation is staged and
+// faults in page by page).  Blocks are never returned to the system.
+class PinnedPool {
+  public:
+    void* acquire(size_t bytes, size_t& got) {
+        {
+            std::lock_guard<std::mutex> g(mu_);
+            size_t best = free_.size();
+            for (size_t i = 0; i < free_.size(); ++i)
+                if (free_[i].first >= bytes && (best == free_.size() || free_[i].first < free_[best].first))
+                    best = i;
+            if (best < free_.size()) {
+                got = free_[best].first;
+                void* p = free_[best].second;
+                free_.erase(free_.begin() + (long)best);
+                return p;
+            }
+        }
+        const size_t want = (bytes + (64u << 20) - 1) / (64u << 20) * (64u << 20);  // 64 MiB steps
+        void* p = nullptr;
+        if (cudaHostAlloc(&p, want, cudaHostAllocDefault) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        got = want;
+        return p;
+    }
+    void release(void* p, size_t bytes) {
+        if (!p) return;
+        std::lock_guard<std::mutex> g(mu_);
+        free_.emplace_back(bytes, p);
+    }
+
+  private:
+    std::mutex mu_;
+    std::vector<std::pair<size_t, void*>> free_;
+};
+PinnedPool& pinned_pool() {
+    static PinnedPool* pool = new PinnedPool();  // outlives every result
+    return *pool;
+}
+}  // namespace
+}  // namespace aa
+
 struct aa_candidates {
-    std::vector<aa_candidate> list;            // filled by the batch and server paths
-    std::unique_ptr<aa_candidate[]> ordered;   // filled by order_candidates
+    std::vector<aa_candidate> list;  // filled by the batch and server paths
+    aa_candidate* ordered = nullptr; // filled by order_candidates (pinned pool block)
+    size_t ordered_bytes = 0;
     int64_t nordered = 0;
     int64_t total = 0;
+    ~aa_candidates() { aa::pinned_pool().release(ordered, ordered_bytes); }
 };
 
 namespace aa {
@@ -156,10 +207,12 @@ aa_status order_candidates(const aa_candidate* d_cands, int64_t stored, std::vec
     }
     res->nordered = 0;
     if (dst == 0) return AA_OK;
-    try {
-        res->ordered.reset(new aa_candidate[(size_t)dst]);
-    } catch (const std::bad_alloc&) {
-        set_error("host allocation of %lld candidates failed", (long long)dst);
+    pinned_pool().release(res->ordered, res->ordered_bytes);
+    res->ordered = static_cast<aa_candidate*>(
+        pinned_pool().acquire((size_t)dst * sizeof(aa_candidate), res->ordered_bytes));
+    if (!res->ordered) {
+        res->ordered_bytes = 0;
+        set_error("page-locked host allocation of %lld candidates failed", (long long)dst);
         return AA_ERR_NOMEM;
     }
     AsyncAllocs mem(s);
@@ -169,7 +222,7 @@ aa_status order_candidates(const aa_candidate* d_cands, int64_t stored, std::vec
     AA_CUDA(cudaMemcpyAsync(d_runs, runs.data(), runs.size() * sizeof(RunCopy), cudaMemcpyHostToDevice, s),
             "upload run order");
     AA_CUDA(launch_gather_runs(d_cands, d_out, d_runs, (int64_t)runs.size(), s), "gather candidates");
-    AA_CUDA(cudaMemcpyAsync(res->ordered.get(), d_out, (size_t)dst * sizeof(aa_candidate),
+    AA_CUDA(cudaMemcpyAsync(res->ordered, d_out, (size_t)dst * sizeof(aa_candidate),
                             cudaMemcpyDeviceToHost, s),
             "read candidates");
     AA_CUDA(cudaStreamSynchronize(s), "synchronize");
@@ -455,8 +508,12 @@ aa_status aa_dedisperse(aa_plan* p, const uint8_t* host_in, int64_t nsamp, int64
         return AA_ERR_NOMEM;
     }
     if (nsamp > 0) {
-        cudaError_t e = cudaMemcpy2DAsync(d_in, L.in_pitch_min, host_in, host_pitch, nsamp,
-                                          p->nchans, cudaMemcpyHostToDevice, s);
+        // one contiguous copy when the rows are packed alike on both sides
+        cudaError_t e = host_pitch == L.in_pitch_min
+                            ? cudaMemcpyAsync(d_in, host_in, (size_t)p->nchans * (size_t)host_pitch,
+                                              cudaMemcpyHostToDevice, s)
+                            : cudaMemcpy2DAsync(d_in, L.in_pitch_min, host_in, host_pitch, nsamp, p->nchans,
+                                                cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess) {
             cudaEvent_t ev;
             e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
@@ -557,7 +614,7 @@ aa_status aa_candidates_view(const aa_candidates* c, const aa_candidate** host, 
     if (!c) { set_error("candidates is NULL"); return AA_ERR_ARG; }
     const bool ord = c->nordered > 0;
     const int64_t n = ord ? c->nordered : (int64_t)c->list.size();
-    if (host) *host = n == 0 ? nullptr : (ord ? c->ordered.get() : c->list.data());
+    if (host) *host = n == 0 ? nullptr : (ord ? c->ordered : c->list.data());
     if (stored) *stored = n;
     if (total) *total = c->total;
     return AA_OK;
