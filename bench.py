@@ -156,7 +156,7 @@ NCU_TRAFFIC = {
         "small_output_samples": 1500 * 128687,
         "capture": "profiles/dedisperse_grouped_u8_ska-4096ch-2^17.md"},
     ("sps_boxcar", "pruned"): {
-        "small_read_bytes": 871_785_216, "small_write_bytes": 43_952_640,
+        "small_read_bytes": 875_240_960, "small_write_bytes": 44_166_400,
         "small_output_samples": 1500 * 128687,
         "capture": "profiles/sps_boxcar_ska-4096ch-2^17.md"},
 }
