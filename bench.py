@@ -29,7 +29,6 @@ sys.path.insert(0, ROOT)
 
 METRIC = "DM-trial samples/s (4096-ch SKA-like plan, dedispersion + single-pulse search)"
 UNIT = "DM-trial samples/s"
-SM_COUNT = 152
 SM_MAX_MHZ_DEFAULT = 2070.0
 # Minimal lane instructions per boxcar width-sample on sm_103a: running-sum
 # add, normalising FMA, and half of a three-input max.
@@ -195,11 +194,26 @@ def subband_bands(dec: int) -> int:
 SUBBAND_COARSE = 16
 
 
-def run_oracle_sample(w, x_host, rows_per_range: int, threads: int, subband: bool = False):
+def strided_rows(ndm: int, count: int, k: int = 0) -> list:
+    """Trial indices of one range for an oracle sample: `count` trials
+    evenly spaced over [0, ndm) including both ends; with count = 1, the
+    k-th of a sequence that strides over the range (successive k land on
+    trials far apart, so K steps of one trial cover the range evenly)."""
+    if ndm <= 0:
+        return []
+    if count > 1:
+        return sorted(set(np.linspace(0, ndm - 1, count).round().astype(int).tolist()))
+    # golden-ratio stride: k -> frac(k * 0.618...) * ndm
+    return [int((k * 0.6180339887498949) % 1.0 * ndm)]
+
+
+def run_oracle_sample(w, x_host, rows_per_range: int, threads: int, subband: bool = False,
+                      k: int = 0):
     """Oracle (CPU) on a bounded sample: `rows_per_range` full-length DM trials
-    of every range (decimated inputs prepared outside the timed part and
-    amortised over all trials); with `subband`, the oracle's sub-band form
-    (the same sum at the effective delays).  Returns (DM-trial samples,
+    of every range, strided over the range (see strided_rows; k selects the
+    trial of a one-trial sample), decimated inputs prepared outside the timed
+    part and amortised over all trials; with `subband`, the oracle's sub-band
+    form (the same sum at the effective delays).  Returns (DM-trial samples,
     seconds, cores, desc)."""
     from oracle import oracle as o
     cores = o.set_threads(threads)
@@ -219,8 +233,7 @@ def run_oracle_sample(w, x_host, rows_per_range: int, threads: int, subband: boo
     ntrials = sum(g.ndm for g in pl)
     samples, t_rows, nrows = 0, 0.0, 0
     for g, xr in zip(pl, inputs):
-        idx = np.linspace(0, g.ndm - 1, rows_per_range).round().astype(int)
-        for i in idx:
+        for i in strided_rows(g.ndm, rows_per_range, k):
             t = time.perf_counter()
             y = o.dedisperse_row(xr, g.shifts[i], 0, g.length)
             o.search_row(y, w.max_width, w.threshold, g.dm_offset + int(i), 0)
@@ -228,8 +241,11 @@ def run_oracle_sample(w, x_host, rows_per_range: int, threads: int, subband: boo
             samples += g.length
             nrows += 1
     secs = t_rows + t_dec * nrows / ntrials
-    desc = (f"{rows_per_range} full-length DM trials per range ({nrows} of {ntrials}), "
-            f"decimation time amortised over all trials" + (", sub-band form" if subband else ""))
+    how = ("evenly spaced over each range incl. both ends" if rows_per_range > 1 else
+           "a different trial per step, striding over each range")
+    desc = (f"{rows_per_range} full-length DM trial(s) per range ({nrows} of {ntrials}; {how}), "
+            f"time extrapolated to all trials by output samples, decimation time amortised "
+            f"over all trials" + (", sub-band form" if subband else ""))
     return samples, secs, cores, desc
 
 
@@ -245,11 +261,11 @@ def bench_reference(args):
     pulses = synth.pulses_ska(w, lambda dm: int(d1(dm).max()))
     x = synth.make_filterbank(w, pulses, d1, device="cpu").numpy()
     threads = os.cpu_count() or 1
-    for _ in range(args.warmup):
-        run_oracle_sample(w, x, 1, threads)
+    for j in range(args.warmup):
+        run_oracle_sample(w, x, 1, threads, k=args.steps + j)
     tot_s, tot_t, cores, desc = 0, 0.0, 1, ""
-    for _ in range(args.steps):
-        s, t, cores, desc = run_oracle_sample(w, x, 1, threads)
+    for j in range(args.steps):
+        s, t, cores, desc = run_oracle_sample(w, x, 1, threads, k=j)
         tot_s += s
         tot_t += t
     v = tot_s / tot_t
@@ -375,7 +391,10 @@ def bench_ours(args):
     # roofline of the dominant kernel, from the live event timings
     peaks = load_peaks()
     sm_max = float(peaks.get("sm_max_mhz", SM_MAX_MHZ_DEFAULT))
-    lane_peak = SM_COUNT * 128 * sm_max * 1e6  # lane instructions / s
+    # lane peak from the device the bench ran on: its SM count x 128 integer /
+    # FP32 lanes per SM x the measured maximum SM clock
+    sm_count = int(torch.cuda.get_device_properties(local).multi_processor_count)
+    lane_peak = sm_count * 128 * sm_max * 1e6  # lane instructions / s
     kern = {}
     for name, (n, ms) in prof.items():
         if n:
@@ -419,12 +438,12 @@ def bench_ours(args):
     if dominant == "sps_boxcar":
         achieved = BOXCAR_OPS_PER_WS * evaluated / box_s
         tb, tnote = traffic("sps_boxcar")
-        roof = {"kernel": "sps_boxcar", "bound": "alu", "achieved": achieved / 1e9,
+        roof = {"kernel": "sps_boxcar", "bound": "alu", "sm_count": sm_count, "achieved": achieved / 1e9,
                 "peak": lane_peak / 1e9, "unit": "Gop/s", "frac": achieved / lane_peak,
                 "traffic": tb, "traffic_source": tnote,
                 "ops": f"{BOXCAR_OPS_PER_WS} lane instructions per evaluated width-sample "
                        f"(device-counted; blocks bounded below threshold skipped); peak = "
-                       f"{SM_COUNT} SMs x 128 lanes x {sm_max:.0f} MHz"}
+                       f"{sm_count} SMs (device query) x 128 lanes x {sm_max:.0f} MHz"}
     else:
         key = dominant
         s = kern[key]["ms_per_step"] / 1e3
@@ -434,21 +453,21 @@ def bench_ours(args):
         nl = kern[key]["launches"] / max(args.steps, 1)
         alg_bytes = sum((w.nchans * g.nsamp_dec * (1 if g.dec == 1 else 2) + 4 * g.ndm * g.length)
                         for g in alg["lay"] if (g.dec == 1) == (key == "dedisperse_u8")) / max(nl, 1)
-        roof = {"kernel": key, "bound": "alu", "achieved": achieved / 1e9,
+        roof = {"kernel": key, "bound": "alu", "sm_count": sm_count, "achieved": achieved / 1e9,
                 "peak": lane_peak / 1e9, "unit": "Gop/s", "frac": achieved / lane_peak,
                 "traffic": tb, "traffic_source": tnote, "algorithmic_bytes_per_launch": alg_bytes,
                 "executed_gops": executed / 1e9, "executed_frac": executed / lane_peak,
                 "ops": "algorithmic channel-adds (sum over trials of nchans x L) per second; "
                        "executed_* counts the adds the chosen strategy performs (grouped: "
                        "pre-sum adds + group adds); peak = 1 add per lane per clock "
-                       f"({SM_COUNT} SMs x 128 lanes x {sm_max:.0f} MHz)"}
+                       f"({sm_count} SMs (device query) x 128 lanes x {sm_max:.0f} MHz)"}
     hbm = float(peaks.get("hbm_gbs", 6678.2))
     eff_in_gbs = alg["dm_samples"] * w.nchans / step_s / 1e9
 
     cpu = None
     if not args.no_cpu_baseline and rank == 0 and ws == 1:
         xh = x[:, :nsamp].cpu().numpy()
-        s, secs, cores, desc = run_oracle_sample(w, xh, 1, os.cpu_count() or 1,
+        s, secs, cores, desc = run_oracle_sample(w, xh, 3, os.cpu_count() or 1,
                                                  subband=args.strategy == "subband")
         cpu = {"value": s / secs, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
 

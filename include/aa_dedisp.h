@@ -405,7 +405,9 @@ void aa_server_destroy(aa_server* server);
 /* Queue the next chunk of `beam`: uint8 [nchans][host_pitch] host memory
  * (first chunk_nsamp bytes of each row), read-only, owned by the caller and
  * kept valid until the chunk completes.  arrival_time: the caller's clock
- * (use aa_server_clock).  Returns AA_PENDING and the chunk's ticket. */
+ * (use aa_server_clock).  Returns AA_PENDING and the chunk's ticket;
+ * AA_ERR_CONFIG (nothing queued) for a chunk whose samples would pass global
+ * sample index 2^32 of its beam (reported start times are 32-bit). */
 aa_status aa_server_submit(aa_server* server, int32_t beam, const uint8_t* host_chunk,
                            int64_t host_pitch, double arrival_time, int64_t* ticket);
 
@@ -509,9 +511,11 @@ void aa_candidates_destroy(aa_candidates* c);
  * every GPU loading the library holds until the process exits.  The caller
  * still passes the dedispersed input, the candidate array, the count and the
  * optional B(t) output.  The first call on a device looks up the array's
- * device address (with that device current); make that first call before
- * any stream capture.  All calls share the one array: calls whose GPU work
- * overlaps race.  Returns AA_ERR_ARG if the search needs more scratch than
+ * device address (with that device current) and keeps it for the life of
+ * the process; make that first call before any stream capture, and do not
+ * use this entry point on a device after a cudaDeviceReset of it (the kept
+ * address no longer names the array).  All calls share the one array: calls
+ * whose GPU work overlaps race.  Returns AA_ERR_ARG if the search needs more scratch than
  * the array holds (aa_plan_query(...).sps_ws_bytes > AA_NOALLOC_SCRATCH_BYTES),
  * otherwise what aa_sps_search_device returns.  Calls no allocation
  * routine. */

@@ -290,6 +290,10 @@ def search_row(y: np.ndarray, W: int, thr: float, dm_index: int, rng: int,
     cands = []
     if sigma == 0.0 or t_hi <= t_lo:
         return cands, B[t_lo - a:t_hi - a], wb[t_lo - a:t_hi - a], mu, sigma
+    # The peak decision is oracle_peaks on B over [a, b): a window end is the
+    # series end (a missing neighbour, -inf) or lies outside [t_lo, t_hi),
+    # so every t in [t_lo, t_hi) is decided with its true neighbours.
+    peak_set = set((peaks_thr(B, thr) + a).tolist())
     # only samples within FRAGILE_THR of the threshold or above can matter
     near_idx = np.nonzero(B[t_lo - a:t_hi - a] >= thr - FRAGILE_THR)[0] + t_lo
     for t in near_idx.tolist():
@@ -297,7 +301,7 @@ def search_row(y: np.ndarray, W: int, thr: float, dm_index: int, rng: int,
         v = B[k]
         left = B[k - 1] if t > 0 else -np.inf
         right = B[k + 1] if t + 1 < n else -np.inf
-        is_peak = v >= thr and v > left and v >= right
+        is_peak = t in peak_set
         near = (abs(v - thr) < FRAGILE_THR or abs(v - left) < FRAGILE_CMP
                 or abs(v - right) < FRAGILE_CMP)
         if is_peak or near:

@@ -8,9 +8,12 @@
 // runs the same search as aa_sps_search_device with its scratch taken from a
 // fixed-size array that is part of the library's device image.
 //
-// The array below is a host-side stand-in in host code: its device address
-// is obtained with cudaGetSymbolAddress, once per device, with that device
-// current, on the first call made on that device.  It occupies
+// In host code the name of the array below is only its host-side shadow,
+// not a device address: the kernels get the address that
+// cudaGetSymbolAddress returns, looked up once per device, with that device
+// current, on the first call made on that device (and cached: a
+// cudaDeviceReset of that device invalidates it, so this entry point must not
+// be used on a device after it was reset).  The array occupies
 // AA_NOALLOC_SCRATCH_BYTES on every GPU that loads the library, until the
 // process exits.  Every call shares it: calls whose work overlaps on the GPU
 // (other streams, other host threads) race on it.

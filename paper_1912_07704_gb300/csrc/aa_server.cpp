@@ -283,6 +283,15 @@ aa_status aa_server_submit(aa_server* s, int32_t beam, const uint8_t* host_chunk
     if (!s || !host_chunk || !ticket) { set_error("server/host_chunk/ticket is NULL"); return AA_ERR_ARG; }
     if (beam < 0 || beam >= s->nbeams) { set_error("beam %d out of range", beam); return AA_ERR_ARG; }
     if (host_pitch < s->N) { set_error("host_pitch must be >= chunk_nsamp"); return AA_ERR_ARG; }
+    // Reported start times are global sample indices of the beam, stored in
+    // 32 bits: every index this chunk can report is below (chunk + 1) * N
+    // (decimation only lowers it), so refuse chunks past 2^32 samples.
+    const int64_t chunk = s->beams[beam].next_chunk;
+    if ((chunk + 1) * s->N > (int64_t)UINT32_MAX) {
+        set_error("beam %d chunk %lld: global sample index would pass 2^32 (start a new beam)", beam,
+                  (long long)chunk);
+        return AA_ERR_CONFIG;
+    }
     Request r;
     r.ticket = (int64_t)s->reqs.size();
     r.beam = beam;

@@ -4,7 +4,8 @@ aa_sps_search_device_noalloc serves callers that may not allocate device
 memory while they run (a real-time loop with memory fixed at start-up, a
 plug-in whose host framework owns all allocations): its scratch is a fixed
 array inside the library.  Two calls in a row must each reproduce the
-regular entry point's candidates and B(t).  This file is collected last so
+regular entry point's candidates and B(t) exactly (same kernels, same
+input).  This file is collected last so
 that a run stopping at the first failure has run every other test first.
 """
 import numpy as np
@@ -16,14 +17,13 @@ from paper_1912_07704_gb300.api import Plan, candidates_from_device
 
 pytestmark = pytest.mark.gpu
 
-TOL = 1e-4
 
 
 def _compare(a, b):
+    """Both entry points run the same kernels on the same input; only where
+    their scratch lives differs, so every record is identical."""
     assert len(a) == len(b)
-    assert np.array_equal(a["dm_index"], b["dm_index"]) and np.array_equal(a["t"], b["t"])
-    assert np.array_equal(a["width"], b["width"]) and np.array_equal(a["range"], b["range"])
-    assert np.abs(a["snr"].astype(np.float64) - b["snr"]).max(initial=0.0) <= TOL
+    assert np.array_equal(a, b)
 
 
 def test_noalloc_search_matches_workspace_search():
@@ -56,7 +56,7 @@ def test_noalloc_search_matches_workspace_search():
         _compare(candidates_from_device(c2, n2, cap), ref)
         for a, b in zip(plan.range_views(snr2, w.nsamp), views_ref):
             assert torch.isfinite(a).all()
-            assert (a.double() - b.double()).abs().max().item() <= TOL
+            assert torch.equal(a, b)
     plan.close()
 
 
