@@ -345,6 +345,15 @@ void aa_batch_destroy(aa_batch* batch);
  * bytes of each row are read).  The caller fills it before aa_batch_run. */
 aa_status aa_batch_input(aa_batch* batch, int32_t beam, uint8_t** d_in, int64_t* pitch);
 
+/* The dedispersed series of a beam after aa_batch_run has completed (until
+ * the next run), in the layout aa_dedisperse_device writes for that beam's
+ * plan and nsamp (aa_plan_query), library-owned, read-only.  Only beams of
+ * the batch's last wave keep their series (earlier waves share the region):
+ * AA_ERR_STATE for the others, AA_ERR_ARG for a bad beam or NULL d_dd.
+ * (Inspection only, e.g. to check the batched sums against the plain
+ * definition; the paper's pipeline searches them in place, Sec. 2.3.) */
+aa_status aa_batch_dd_view(const aa_batch* batch, int32_t beam, const float** d_dd);
+
 /* Number of waves and total device bytes held by the batch. */
 aa_status aa_batch_info(const aa_batch* batch, int32_t* nwaves, int64_t* device_bytes);
 

@@ -122,18 +122,23 @@ static inline int64_t sample_at(const void* x, int32_t elem_bytes, int64_t idx)
 }
 
 /* One dedispersed series y[t] = sum_c x[c][t + shifts[c]] for t in [t0, t1).
- * x is [nchans][pitch] with 1- or 2-byte unsigned samples. */
+ * x is [nchans][pitch] with 1- or 2-byte unsigned samples.  The sum over c is
+ * an exact integer sum, so it is taken channel by channel over blocks of
+ * consecutive t (each channel's samples read in order); OpenMP splits the
+ * blocks. */
 void oracle_dedisperse(const void* x, int32_t elem_bytes, int32_t nchans, int64_t pitch,
                        const int32_t* shifts, int64_t t0, int64_t t1, int64_t* out)
 {
-    int64_t n = t1 - t0;
-    if (n <= 0) return;
+    const int64_t block = 4096;
+    if (t1 - t0 <= 0) return;
 #pragma omp parallel for schedule(static)
-    for (int64_t t = t0; t < t1; ++t) {
-        int64_t acc = 0;
-        for (int32_t c = 0; c < nchans; ++c)
-            acc += sample_at(x, elem_bytes, (int64_t)c * pitch + t + shifts[c]);
-        out[t - t0] = acc;
+    for (int64_t b = t0; b < t1; b += block) {
+        const int64_t e = b + block < t1 ? b + block : t1;
+        for (int64_t t = b; t < e; ++t) out[t - t0] = 0;
+        for (int32_t c = 0; c < nchans; ++c) {
+            const int64_t row = (int64_t)c * pitch + shifts[c];
+            for (int64_t t = b; t < e; ++t) out[t - t0] += sample_at(x, elem_bytes, row + t);
+        }
     }
 }
 

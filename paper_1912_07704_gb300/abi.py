@@ -145,6 +145,7 @@ _SIG = {
     "aa_batch_destroy": (None, [_P]),
     "aa_batch_input": (ctypes.c_int, [_P, _I32, ctypes.POINTER(_P), ctypes.POINTER(_I64)]),
     "aa_batch_info": (ctypes.c_int, [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I64)]),
+    "aa_batch_dd_view": (ctypes.c_int, [_P, _I32, ctypes.POINTER(_P)]),
     "aa_batch_run": (ctypes.c_int, [_P, _P]),
     "aa_batch_candidates": (ctypes.c_int, [_P, _P, ctypes.POINTER(_P)]),
     "aa_server_create": (ctypes.c_int, [_P, _I32, _I64, _I32, _F32, _I64, _I64, _I32,
@@ -439,6 +440,12 @@ def aa_batch_input(batch, beam: int) -> tuple:
     check(lib().aa_batch_input(batch, int(beam), ctypes.byref(p), ctypes.byref(pitch)),
           "aa_batch_input")
     return p.value, pitch.value
+
+
+def aa_batch_dd_view(batch, beam: int) -> int:
+    p = ctypes.c_void_p()
+    check(lib().aa_batch_dd_view(batch, int(beam), ctypes.byref(p)), "aa_batch_dd_view")
+    return p.value
 
 
 def aa_batch_info(batch) -> tuple:

@@ -364,6 +364,18 @@ class Batch:
                                         "data": (ptr, False), "version": 3, "strides": None}
         return torch.as_tensor(_U8(), device="cuda")
 
+    def dd_view(self, beam: int) -> torch.Tensor:
+        """The beam's dedispersed series after a completed run (beams of the
+        last wave only), as a float32 tensor of the plan's dd_elems (zero-copy,
+        layout of Plan.dedisperse_device; split it with Plan.range_views)."""
+        ptr = abi.aa_batch_dd_view(self.handle, beam)
+        n = self.plans[beam].query(self.nsamps[beam]).dd_elems
+
+        class _F32:
+            __cuda_array_interface__ = {"shape": (n,), "typestr": "<f4",
+                                        "data": (ptr, True), "version": 3, "strides": None}
+        return torch.as_tensor(_F32(), device="cuda")
+
     def info(self) -> tuple:
         return abi.aa_batch_info(self.handle)
 

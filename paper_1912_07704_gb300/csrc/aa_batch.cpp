@@ -76,6 +76,8 @@ struct aa_batch {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     int grid_dd = 0, grid_st = 0, grid_bx = 0, grid_dec = 0;
+    std::vector<float*> dd_of;    // each beam's dedispersed series (inside its wave's region)
+    std::vector<int> wave_of;     // each beam's wave
 };
 
 namespace {
@@ -221,6 +223,8 @@ aa_status aa_batch_create(aa_plan* const* plans, const int64_t* nsamps, int32_t 
 
     // per-wave descriptors
     b->tables.resize(b->waves.size());
+    b->dd_of.assign(nbeams, nullptr);
+    b->wave_of.assign(nbeams, -1);
     for (size_t wi = 0; wi < b->waves.size(); ++wi) {
         WaveTables& T = b->tables[wi];
         char* q = wave_area;
@@ -237,6 +241,8 @@ aa_status aa_batch_create(aa_plan* const* plans, const int64_t* nsamps, int32_t 
             q += needs[bi].dec_bytes;
             float* dd = reinterpret_cast<float*>(q);
             q += needs[bi].dd_bytes;
+            b->dd_of[bi] = dd;
+            b->wave_of[bi] = (int)wi;
             RowStats* stats = reinterpret_cast<RowStats*>(q);
             q += round_up((int64_t)pl.ndm_total * (int64_t)sizeof(RowStats), 256);
             float2* tab = reinterpret_cast<float2*>(q);
@@ -418,6 +424,19 @@ aa_status aa_batch_input(aa_batch* b, int32_t beam, uint8_t** d_in, int64_t* pit
     if (!b || beam < 0 || beam >= b->nbeams) { set_error("bad batch/beam"); return AA_ERR_ARG; }
     if (d_in) *d_in = reinterpret_cast<uint8_t*>(b->arena + b->in_offset[beam]);
     if (pitch) *pitch = b->in_pitch[beam];
+    return AA_OK;
+}
+
+aa_status aa_batch_dd_view(const aa_batch* b, int32_t beam, const float** d_dd) {
+    clear_error();
+    if (!b || !d_dd || beam < 0 || beam >= b->nbeams) { set_error("bad batch/beam/d_dd"); return AA_ERR_ARG; }
+    *d_dd = nullptr;
+    if (b->wave_of[beam] != (int)b->waves.size() - 1) {
+        set_error("beam %d ran in wave %d of %zu: its series were overwritten by later waves", beam,
+                  b->wave_of[beam], b->waves.size());
+        return AA_ERR_STATE;
+    }
+    *d_dd = b->dd_of[beam];
     return AA_OK;
 }
 

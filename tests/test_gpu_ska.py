@@ -1,7 +1,12 @@
 """Full-size 4096-channel, 2^20-sample, four-range plan with W = 8192, run
-exactly as bench.py runs it; the oracle checks sampled DM rows in full
-(dedispersion) and sampled time windows (boxcar SNR and candidates), and
-every strong injected pulse must be detected near its DM and arrival time.
+exactly as bench.py runs it.  The oracle checks dedispersion bit-exactly on
+a strided subset of trials (every 25th trial of each range, both ends of each
+range and the trials at the injected pulses' DMs: about 180 full rows), the
+boxcar SNR B(t) and the candidate list over one full-length row per range
+(the row at the range's strongest pulse, else its middle row) and over
+2048-sample windows (around each pulse where one falls in the row) of every
+other sampled row; every strong injected pulse must be detected near its DM
+and arrival time.
 The bench's post-processing runs on the same output: the device ordering must
 equal a numpy sort of the records, and the 2-D peak filter must agree with the
 oracle on sampled candidates."""
@@ -70,14 +75,34 @@ def test_bench_and_snr_runs_agree(ska_run):
     assert np.array_equal(bc, sc)
 
 
+STRIDE = 25
+
+
+def _pulse_row(g, p):
+    i = int(round((p.dm - g.dm_lo) / g.dm_step)) if g.dm_step > 0 else 0
+    return i if 0 <= i < g.ndm else None
+
+
 def _sample_rows(lay, pulses, r):
     g = lay[r]
-    rows = {0, g.ndm // 2, g.ndm - 1}
+    rows = set(range(0, g.ndm, STRIDE)) | {g.ndm - 1}
     for p in pulses:
-        i = int(round((p.dm - g.dm_lo) / g.dm_step)) if g.dm_step > 0 else 0
-        if 0 <= i < g.ndm:
+        i = _pulse_row(g, p)
+        if i is not None:
             rows.add(i)
     return sorted(rows)
+
+
+def _full_row(lay, pulses, r):
+    """The row searched over its whole length: the strongest pulse's trial
+    in this range, else the middle trial."""
+    g = lay[r]
+    best = None
+    for p in pulses:
+        i = _pulse_row(g, p)
+        if i is not None and (best is None or p.amplitude * np.sqrt(p.n_w) > best[0]):
+            best = (p.amplitude * np.sqrt(p.n_w), i)
+    return best[1] if best else g.ndm // 2
 
 
 def test_sampled_rows_parity(oracle, ska_run):
@@ -86,7 +111,7 @@ def test_sampled_rows_parity(oracle, ska_run):
     dd = plan.range_views(out, W.nsamp)
     sv = plan.range_views(snr, W.nsamp)
     opl = oracle.plan(W.nchans, W.fch1, W.foff, W.tsamp, W.ranges, W.nsamp)
-    compared = 0
+    compared = checked_rows = 0
     for r, g in enumerate(lay):
         xr = oracle.range_input(xh, g.dec)
         rows = _sample_rows(lay, pulses, r)
@@ -96,6 +121,7 @@ def test_sampled_rows_parity(oracle, ska_run):
             assert np.array_equal(dd[r][i].double().cpu().numpy(), y.astype(np.float64)), (r, i)
             ys[i] = y
         windows = {}
+        full = _full_row(lay, pulses, r)
         for i in rows:
             lo, hi = 0, 2048
             for p in pulses:
@@ -103,13 +129,16 @@ def test_sampled_rows_parity(oracle, ska_run):
                 if abs(p.dm - (g.dm_lo + i * g.dm_step)) < 3 * max(g.dm_step, 1e-9) and t < g.length:
                     lo, hi = max(0, t - 1024), min(g.length, t + 1024)
             windows[i] = (lo, hi)
+        windows[full] = (0, g.length)  # the whole series
         solid, fragile, B = oracle_candidates(oracle, ys, W.max_width, W.threshold,
                                               g.dm_offset, r, windows)
         check_snr_rows(sv[r], ys, B)
         glob = {g.dm_offset + i: windows[i] for i in rows}
         keep = lambda dm, t: dm in glob and glob[dm][0] <= t < glob[dm][1]
         compared += compare_candidate_lists(bc[bc["range"] == r], solid, fragile, keep)
+        checked_rows += len(rows)
     assert compared > 0
+    assert checked_rows >= 170
 
 
 def test_strong_pulses_detected(ska_run):
