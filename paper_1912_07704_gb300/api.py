@@ -373,7 +373,7 @@ class Batch:
 
         class _F32:
             __cuda_array_interface__ = {"shape": (n,), "typestr": "<f4",
-                                        "data": (ptr, True), "version": 3, "strides": None}
+                                        "data": (ptr, False), "version": 3, "strides": None}
         return torch.as_tensor(_F32(), device="cuda")
 
     def info(self) -> tuple:
