@@ -505,6 +505,51 @@ aa_status aa_candidates_view(const aa_candidates* c, const aa_candidate** host,
 /* Free a candidate list.  NULL is a no-op. */
 void aa_candidates_destroy(aa_candidates* c);
 
+/* --------------------------------------- host-buffer pipeline (Sec. 2.3-3.3) */
+
+/* A pipeline searches a sequence of same-sized blocks of caller-owned host
+ * data (uint8 [nchans][host_pitch], first nsamp bytes of each row) through
+ * the whole path -- decimation, dedispersion, single-pulse search, candidate
+ * ordering -- with every device buffer requested once, at creation (Sec. 2.3)
+ * and the copies overlapped with the compute: block k+1 is uploaded while
+ * block k is searched, and block k's candidates are read back while block
+ * k+1 is searched.  The results are those of aa_dedisperse + aa_sps_search
+ * on each block.
+ *
+ * aa_pipeline_create: plan (bound to the current device if needed; it must
+ * outlive the pipeline), block length nsamp >= 1, search parameters as in
+ * aa_sps_search, depth in [1, 8] = blocks in flight (input slots; 2 overlaps
+ * one upload with one search).  Allocates depth x (nchans x in_pitch +
+ * cand_capacity x 16) bytes plus one set of working buffers (aa_plan_query
+ * with max_width: dd_elems x 4 + dedisp_ws_bytes + sps_ws_bytes, the
+ * candidate array and the ordering scratch of aa_postprocess_ws_bytes).
+ * AA_ERR_ARG on bad arguments, AA_ERR_NOMEM if memory runs out (nothing is
+ * left allocated). */
+typedef struct aa_pipeline aa_pipeline;
+aa_status aa_pipeline_create(aa_plan* plan, int64_t nsamp, int32_t max_width, float threshold,
+                             int64_t cand_capacity, int32_t depth, aa_pipeline** out);
+
+/* Queue the next block.  The host memory is read asynchronously: keep it
+ * valid and unchanged until aa_pipeline_wait returns for this ticket
+ * (page-locked memory lets the upload overlap the compute; pageable memory
+ * works but is copied synchronously by the driver).  Never written.  Returns
+ * AA_PENDING and the block's ticket (0, 1, 2, ... in submission order);
+ * AA_ERR_STATE if `depth` blocks are already in flight (wait for the oldest
+ * first) or another device is current; AA_ERR_ARG on bad arguments. */
+aa_status aa_pipeline_submit(aa_pipeline* pipeline, const uint8_t* host_in, int64_t host_pitch,
+                             int64_t* ticket);
+
+/* Block until the ticket's search is done and return its candidates
+ * (library-owned host memory, sorted by (dm_index, t); free with
+ * aa_candidates_destroy).  Tickets may be collected in any order, each once
+ * (AA_ERR_STATE for a ticket already collected).  Returns AA_OK,
+ * AA_WARN_CAND_OVERFLOW, AA_ERR_TIMEOUT (a bounded device-side wait gave up)
+ * or AA_ERR_CUDA; the block's slot is free again in every case. */
+aa_status aa_pipeline_wait(aa_pipeline* pipeline, int64_t ticket, aa_candidates** out);
+
+/* Synchronise and free everything the pipeline holds.  NULL is a no-op. */
+void aa_pipeline_destroy(aa_pipeline* pipeline);
+
 /* ---------------------------------------------- no-allocation search -- */
 
 /* Size of the fixed scratch area behind aa_sps_search_device_noalloc. */

@@ -119,6 +119,10 @@ _SIG = {
     "aa_candidates_view": (ctypes.c_int, [_P, ctypes.POINTER(_P), ctypes.POINTER(_I64),
                                           ctypes.POINTER(_I64)]),
     "aa_candidates_destroy": (None, [_P]),
+    "aa_pipeline_create": (ctypes.c_int, [_P, _I64, _I32, _F32, _I64, _I32, ctypes.POINTER(_P)]),
+    "aa_pipeline_submit": (ctypes.c_int, [_P, _P, _I64, ctypes.POINTER(_I64)]),
+    "aa_pipeline_wait": (ctypes.c_int, [_P, _I64, ctypes.POINTER(_P)]),
+    "aa_pipeline_destroy": (None, [_P]),
     "aa_debug_inject": (ctypes.c_int, [_I32, _I64]),
     "aa_fil_read_header": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(aa_fil_header)]),
     "aa_fil_read_block": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(aa_fil_header), _I64, _I64, _P]),
@@ -294,6 +298,32 @@ def aa_candidates_view(c) -> tuple:
 
 def aa_candidates_destroy(c) -> None:
     lib().aa_candidates_destroy(c)
+
+
+def aa_pipeline_create(plan, nsamp, max_width, threshold, capacity, depth) -> int:
+    h = ctypes.c_void_p()
+    check(lib().aa_pipeline_create(plan, int(nsamp), int(max_width), float(threshold),
+                                   int(capacity), int(depth), ctypes.byref(h)),
+          "aa_pipeline_create")
+    return h.value
+
+
+def aa_pipeline_submit(pipeline, host_ptr: int, host_pitch: int) -> int:
+    t = ctypes.c_int64()
+    check(lib().aa_pipeline_submit(pipeline, host_ptr, int(host_pitch), ctypes.byref(t)),
+          "aa_pipeline_submit", ok=(AA_PENDING,))
+    return t.value
+
+
+def aa_pipeline_wait(pipeline, ticket: int) -> tuple:
+    h = ctypes.c_void_p()
+    st = check(lib().aa_pipeline_wait(pipeline, int(ticket), ctypes.byref(h)), "aa_pipeline_wait",
+               ok=(AA_OK, AA_WARN_CAND_OVERFLOW))
+    return h.value, st
+
+
+def aa_pipeline_destroy(pipeline) -> None:
+    lib().aa_pipeline_destroy(pipeline)
 
 
 def aa_debug_inject(what: int, value: int = 0) -> None:

@@ -341,6 +341,56 @@ def _candidates_array(h) -> tuple:
     return np.frombuffer(buf, dtype=abi.CANDIDATE_DTYPE, count=stored), total
 
 
+class Pipeline:
+    """Host-buffer pipeline over same-sized blocks (see aa_pipeline_create):
+    submit() queues a block of uint8 [nchans][>= nsamp] host memory (keep it
+    unchanged until its wait() returns), wait() returns its sorted candidate
+    records and the total found.  Uploads and read-backs overlap the search
+    of the neighbouring blocks."""
+
+    def __init__(self, plan: Plan, nsamp: int, max_width: int, threshold: float,
+                 capacity: int = 1 << 20, depth: int = 2):
+        plan.bind()
+        self.plan = plan
+        self.nsamp = int(nsamp)
+        self.handle = abi.aa_pipeline_create(plan.handle, nsamp, max_width, threshold, capacity,
+                                             depth)
+        self._held = {}
+
+    def submit(self, host) -> int:
+        h = host if isinstance(host, np.ndarray) else host.numpy()
+        assert h.dtype == np.uint8 and h.ndim == 2 and h.shape[0] == self.plan.nchans
+        assert h.strides[1] == 1 and h.shape[1] >= self.nsamp
+        t = abi.aa_pipeline_submit(self.handle, h.ctypes.data, h.strides[0])
+        self._held[t] = h  # the library reads it until wait(t)
+        return t
+
+    def wait(self, ticket: int):
+        try:
+            h, st = abi.aa_pipeline_wait(self.handle, ticket)
+        finally:
+            self._held.pop(ticket, None)
+        return _candidates_array(h)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            abi.aa_pipeline_destroy(self.handle)
+            self.handle = None
+            self._held.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class Batch:
     """Several beams searched by one CUDA graph of persistent work-queue
     kernels (see aa_batch_create).  The plans must outlive the batch."""

@@ -230,6 +230,34 @@ aa_status order_candidates(const aa_candidate* d_cands, int64_t stored, std::vec
     return AA_OK;
 }
 
+aa_status candidates_copy_ordered(const aa_candidate* d_sorted, int64_t n, int64_t total, cudaStream_t s,
+                                  aa_candidates** out) {
+    *out = nullptr;
+    aa_candidates* res = candidates_new();
+    if (!res) { set_error("host allocation failed"); return AA_ERR_NOMEM; }
+    res->total = total;
+    if (n > 0) {
+        res->ordered = static_cast<aa_candidate*>(
+            pinned_pool().acquire((size_t)n * sizeof(aa_candidate), res->ordered_bytes));
+        if (!res->ordered) {
+            res->ordered_bytes = 0;
+            delete res;
+            set_error("page-locked host allocation of %lld candidates failed", (long long)n);
+            return AA_ERR_NOMEM;
+        }
+        cudaError_t e = cudaMemcpyAsync(res->ordered, d_sorted, (size_t)n * sizeof(aa_candidate),
+                                        cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) {
+            delete res;
+            return cuda_fail(e, "read candidates");
+        }
+        res->nordered = n;
+    }
+    *out = res;
+    return AA_OK;
+}
+
 }  // namespace aa
 
 // Sub-band strategy of range r: stage 1 per band into the 16-bit partial

@@ -383,6 +383,12 @@ cudaError_t launch_f32_forward(int mode, const F32FwdArgs& p, cudaStream_t s);
 cudaError_t launch_f32_adjoint(const F32AdjArgs& p, cudaStream_t s);
 cudaError_t launch_finish_loss(const double* sum, double n, double* loss, cudaStream_t s);
 
+// Host list of n records already in (dm_index, t) order on the device:
+// copied on stream s into a page-locked block of the library's pool (the
+// call synchronises s); total = candidates found (may exceed n).
+aa_status candidates_copy_ordered(const aa_candidate* d_sorted, int64_t n, int64_t total, cudaStream_t s,
+                                  aa_candidates** out);
+
 // candidate-list objects shared by the single-beam and batched paths
 aa_candidates* candidates_new();
 std::vector<aa_candidate>& candidates_list(aa_candidates* c);
