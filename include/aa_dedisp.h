@@ -700,12 +700,8 @@ aa_status aa_corner_turn_device(const uint8_t* d_tm, int64_t nsamp, int32_t ncha
  * direct-strategy dedispersion producer never issues the staging copy of
  * channel chunk `value` (that stage's barrier never completes, so every CTA
  * gives up after the wait limit, sets the workspace error word and exits
- * without writing output); what = 3: the grouped strategy's producer warps
- * never mark batch `value` of group sums complete (its consumers give up
- * after the wait limit, set the error word and exit; the producers then give
- * up waiting for the consumers); what = 2: set the wait limit to `value`
- * nanoseconds (default 2 s).  Single-beam launches only (the batched
- * persistent kernels ignore hooks 1 and 3).
+ * without writing output; the grouped strategy has no staging waits); what =
+ * 2: set the wait limit to `value` nanoseconds (default 2 s).
  * Returns AA_ERR_ARG for an unknown `what` or a non-positive limit. */
 aa_status aa_debug_inject(int32_t what, int64_t value);
 

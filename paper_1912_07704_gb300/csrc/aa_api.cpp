@@ -12,7 +12,6 @@
 
 namespace aa {
 extern int g_fault_skip_chunk;
-extern int g_fault_skip_batch;
 extern uint64_t g_wait_limit_ns;
 }  // namespace aa
 
@@ -656,14 +655,10 @@ aa_status aa_debug_inject(int32_t what, int64_t value) {
     switch (what) {
         case 0:  // reset
             g_fault_skip_chunk = -1;
-            g_fault_skip_batch = -1;
             g_wait_limit_ns = 2000000000ull;
             return AA_OK;
         case 1:  // never issue the staging copy of this channel chunk
             g_fault_skip_chunk = (int)value;
-            return AA_OK;
-        case 3:  // grouped strategy: producers never complete this batch of group sums
-            g_fault_skip_batch = (int)value;
             return AA_OK;
         case 2:  // bounded-wait limit in nanoseconds
             if (value <= 0) { set_error("limit must be > 0"); return AA_ERR_ARG; }

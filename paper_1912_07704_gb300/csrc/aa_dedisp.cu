@@ -86,10 +86,6 @@ __device__ __forceinline__ uint32_t mad_add(uint32_t x, uint32_t one, uint32_t a
     return d;
 }
 
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
-}
-
 __device__ __forceinline__ void mbar_inval(uint64_t* bar) {
     asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
@@ -369,43 +365,59 @@ __device__ __forceinline__ void dedisperse_block(const DedispArgs& a, int ndm_bl
     }
 }
 
-// Grouped strategy (see GroupRec / GroupBatch in aa_internal.h).  CTA = 16
-// DM trials x kGroupTau output samples, 24 warps.  The channels stream through
-// in chunks of a.cc; the groups of a chunk are processed in batches of at most
-// a.gz (the DM block's batch table lists them chunk after chunk):
-//   phase 1 (producer warps 16..23): z_g[u] = sum over the group's members of
-//            x[c][t0 + s0_c + u], u < kGroupTau + span_g, read straight from
-//            global memory (each member row is read by one warp, coalesced
-//            32-bit words; the rows of a chunk are shared by the CTAs of all
-//            DM blocks through L2), as packed 16-bit pairs stored twice:
-//            copy A word j = (z[2j], z[2j+1]) and copy B word j =
-//            (z[2j+1], z[2j+2]); work unit = (group, 256 or 512 consecutive
-//            u) or (several groups' samples past 511: tail units), units
-//            round-robin over the producer warps;
-//   phase 2 (consumer warp w < 16 = trial d0 + w): adds z_g[t + delta_g(w)]
-//            for its 16 samples t: copy (delta & 1), word offset delta >> 1,
-//            aligned.
-// The two phases run concurrently on a ring of a.gnbuf batch buffers: batch j
-// lives in buffer j % gnbuf; full[b] completes when every producer thread has
-// written its part of the batch, empty[b] when every consumer thread has read
-// it.  Every wait is bounded (wait_limit_ns of wall clock); on expiry the
-// thread sets the error word and leaves, and the others then run out of time
-// too (nothing waits forever).  Returns false in every thread that gave up.
+// Five consecutive 32-bit words of a row, starting at the word holding byte
+// bo.  vec: as two aligned 16-byte loads, the five words picked by the word
+// offset of bo within its 16-byte block (the same for every lane of the warp,
+// so the branch does not diverge); the caller guarantees that the 32 bytes
+// from bo rounded down to 16 lie inside the buffer.  Otherwise five word
+// loads clamped to the row's last word wl (measured faster than unclamped
+// word loads, and than 16-byte loads for 16-bit rows).
+__device__ __forceinline__ void load_words5(const unsigned char* row, int64_t bo, bool vec, int wl,
+                                            uint32_t& w0, uint32_t& w1, uint32_t& w2, uint32_t& w3,
+                                            uint32_t& w4) {
+    if (vec) {
+        const uint4* q = reinterpret_cast<const uint4*>(row + (bo & ~(int64_t)15));
+        const uint4 q0 = __ldg(q), q1 = __ldg(q + 1);
+        switch ((int)(bo >> 2) & 3) {
+            case 0: w0 = q0.x; w1 = q0.y; w2 = q0.z; w3 = q0.w; w4 = q1.x; break;
+            case 1: w0 = q0.y; w1 = q0.z; w2 = q0.w; w3 = q1.x; w4 = q1.y; break;
+            case 2: w0 = q0.z; w1 = q0.w; w2 = q1.x; w3 = q1.y; w4 = q1.z; break;
+            default: w0 = q0.w; w1 = q1.x; w2 = q1.y; w3 = q1.z; w4 = q1.w; break;
+        }
+    } else {
+        const uint32_t* w = reinterpret_cast<const uint32_t*>(row);
+        const int wi = (int)(bo >> 2);
+        w0 = __ldg(w + min(wi, wl));
+        w1 = __ldg(w + min(wi + 1, wl));
+        w2 = __ldg(w + min(wi + 2, wl));
+        w3 = __ldg(w + min(wi + 3, wl));
+        w4 = __ldg(w + min(wi + 4, wl));
+    }
+}
+
+// Grouped strategy (see GroupRec in aa_internal.h).  CTA = 16 DM trials x
+// kGroupTau output samples.  The channels stream through in chunks of a.cc;
+// the groups of a chunk are processed in batches of at most a.gz:
+//   phase 1: z_g[u] = sum over the group's members of x[c][t0 + s0_c + u],
+//            u < kGroupTau + span_g, read straight from global memory (each
+//            member row is read by one warp, coalesced 32-bit words; the rows
+//            of a chunk are shared by the CTAs of all DM blocks through L2),
+//            as packed 16-bit pairs stored twice: copy A word j =
+//            (z[2j], z[2j+1]) and copy B word j = (z[2j+1], z[2j+2]);
+//            work unit = (group, 256 consecutive u), units round-robin over
+//            the warps;
+//   phase 2: warp w (trial d0 + w) adds z_g[t + delta_g(w)] for its 16
+//            samples t: copy (delta & 1), word offset delta >> 1, aligned.
 // 16-bit lanes never overflow: a chunk holds at most 65535 / (255 dec)
 // channels, and trial accumulators are flushed every a.gflush chunks.
+// `wait_limit_ns` and `fault_skip_chunk` are unused (no device-side waits).
 template <int EB>
-__device__ __forceinline__ bool dedisperse_grouped_block(const DedispArgs& a, int ndm_blocks,
-                                                         int64_t bid, unsigned char* smem,
-                                                         uint64_t* bars, bool reinit,
-                                                         uint64_t wait_limit_ns, int fault_skip_batch) {
+__device__ __forceinline__ void dedisperse_grouped_block(const DedispArgs& a, int ndm_blocks,
+                                                         int64_t bid, unsigned char* smem) {
     constexpr int T = kGroupTau;
     constexpr int QW = T / 64;  // packed words (2 samples) per lane per trial
-    constexpr unsigned kFull = 0xffffffffu;
-    const int gcc = a.cc, gzw = a.gzw, nj = a.gnj, nbuf = a.gnbuf;
-    const int buf_words = a.gz * 2 * gzw;
-    uint32_t* zs = reinterpret_cast<uint32_t*>(smem);  // [nbuf][gz][2][gzw]
-    uint64_t* full = bars;                              // [kMaxGroupBufs]
-    uint64_t* empty = bars + kMaxGroupBufs;             // [kMaxGroupBufs]
+    const int gcc = a.cc, gz = a.gz, gzw = a.gzw, nj = a.gnj;
+    uint32_t* zs = reinterpret_cast<uint32_t*>(smem);  // [gz][2][gzw]
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int dmb = (int)(bid % ndm_blocks);
@@ -415,204 +427,145 @@ __device__ __forceinline__ bool dedisperse_grouped_block(const DedispArgs& a, in
     const int64_t t0 = tile * T;
     const int C = a.nchans;
     const int nchunks = (C + gcc - 1) / gcc;
-    const GroupBatch* batches = a.gbatch + a.gboff[dmb];
-    const int nbatch = a.gboff[dmb + 1] - a.gboff[dmb];
-
-    // the block's batch records, staged once after the group-sum buffers
-    GroupBatch* btab = reinterpret_cast<GroupBatch*>(zs + nbuf * buf_words);
-    for (int i = threadIdx.x; i < nbatch; i += kGroupedThreads)
-        reinterpret_cast<uint2*>(btab)[i] = __ldg(reinterpret_cast<const uint2*>(batches + i));
-    if (threadIdx.x == 0) {  // every barrier of the fixed array, whatever a previous item used
-        for (int b = 0; b < kMaxGroupBufs; ++b) {
-            if (reinit) {
-                mbar_inval(&full[b]);
-                mbar_inval(&empty[b]);
-            }
-            mbar_init(&full[b], kGroupProducers * 32);
-            mbar_init(&empty[b], kDmPerBlock * 32);
-        }
-        mbar_fence_init();
-    }
-    __syncthreads();  // batch table staged, barriers initialised
-    if (nbatch == 0) return true;  // (a plan always gives a DM block at least one batch)
-
-    if (warp < kDmPerBlock) {
-        // ================= consumer: trial d0 + warp
-        uint32_t acc[QW];
-        uint32_t tot[2 * QW];
-#pragma unroll
-        for (int q = 0; q < QW; ++q) {
-            acc[q] = 0;
-            tot[2 * q] = tot[2 * q + 1] = 0;
-        }
-        const bool has_trial = d0 + warp <= dlast;
-        // this trial's relative delay of the lane's group (batch j + 1 in flight)
-        auto load_dl = [&](const GroupBatch& b) -> uint32_t {
-            return lane < b.ngroups ? (uint32_t)__ldg(&a.gdesc[b.first + lane].delta[warp]) : 0u;
-        };
-        uint32_t dl_next = load_dl(btab[0]);
-        int since_flush = 0;
-        for (int j = 0; j < nbatch; ++j) {
-            const int b = j % nbuf;
-            const uint32_t dl = dl_next;
-            if (j + 1 < nbatch) dl_next = load_dl(btab[j + 1]);
-            const int g_p2 = b * buf_words + (lane * 2 + (int)(dl & 1u)) * gzw + (int)(dl >> 1);
-            const GroupBatch bc = btab[j];
-            if (!mbar_wait_bounded(&full[b], (uint32_t)(j / nbuf) & 1u, wait_limit_ns)) {
-                atomicOr(a.err, 2u);
-                return false;
-            }
-            if (has_trial) {
-                const uint32_t* zl = zs + lane;
-#pragma unroll 2
-                for (int g = 0; g < bc.ngroups; ++g) {
-                    const uint32_t* src = zl + __shfl_sync(kFull, g_p2, g);
-#pragma unroll
-                    for (int q = 0; q < QW; ++q) acc[q] += src[32 * q];
-                }
-            }
-            mbar_arrive(&empty[b]);  // this thread's reads of buffer b are done
-            if ((bc.chunk & kBatchLastOfChunk) && ++since_flush >= a.gflush) {
-#pragma unroll
-                for (int q = 0; q < QW; ++q) {
-                    tot[2 * q] += acc[q] & 0xffffu;
-                    tot[2 * q + 1] += acc[q] >> 16;
-                    acc[q] = 0;
-                }
-                since_flush = 0;
-            }
-        }
-#pragma unroll
-        for (int q = 0; q < QW; ++q) {
-            tot[2 * q] += acc[q] & 0xffffu;
-            tot[2 * q + 1] += acc[q] >> 16;
-        }
-        // epilogue: exact integer totals -> FP32 rows
-        if (!has_trial) return true;
-        float* row = a.out + (int64_t)(d0 + warp) * a.out_pitch;
-#pragma unroll
-        for (int q = 0; q < QW; ++q) {
-            const int64_t t = t0 + 2 * (lane + 32 * q);
-            if (t + 2 <= a.length) {
-                *reinterpret_cast<float2*>(row + t) = make_float2((float)tot[2 * q], (float)tot[2 * q + 1]);
-            } else if (t < a.length) {
-                row[t] = (float)tot[2 * q];
-            }
-        }
-        return true;
-    }
-
-    // ================= producer warp pw
-    const int pw = warp - kDmPerBlock;
     const unsigned char* in_b = static_cast<const unsigned char*>(a.in);
     const int64_t pitch_b = a.in_pitch * EB;
-    const int wl = (int)(pitch_b >> 2) - 1;  // last word of a row
+    const GroupRec* recs = a.grec + (size_t)dmb * nchunks;
     const GroupMember* mems = a.gmem + (size_t)dmb * nchunks * gcc;
     // tail units: gtl lanes per group (a power of two), gpt groups per warp
     const int gtl = a.gtl, gtl_log = gtl ? __ffs(gtl) - 1 : 0, gpt = gtl ? 32 / gtl : 1;
-    // group fields of the lane's group: (mstart | mcount << 16, span | pad << 16)
-    auto load_head = [&](const GroupBatch& b) -> uint2 {
-        return lane < b.ngroups ? __ldg(reinterpret_cast<const uint2*>(a.gdesc + b.first + lane))
-                                : make_uint2(0u, 0u);
-    };
-    uint2 head_next = load_head(btab[0]);
-    for (int j = 0; j < nbatch; ++j) {
-        const int b = j % nbuf;
-        const uint2 head = head_next;
-        const GroupBatch bc = btab[j];
-        if (j + 1 < nbatch) head_next = load_head(btab[j + 1]);
-        if (j >= nbuf &&  // the consumers have read the batch that used buffer b before
-            !mbar_wait_bounded(&empty[b], (uint32_t)(j / nbuf - 1) & 1u, wait_limit_ns)) {
-            atomicOr(a.err, 2u);
-            return false;
-        }
-        uint32_t* zb = zs + b * buf_words;
-        const int k = bc.chunk & ~kBatchLastOfChunk;
+    // A lane of a main unit reads below byte EB * (nsamp + 256 gnj) + 31 of its
+    // row (tile start + member delay <= nsamp - 1), so with rows at least
+    // EB * (256 gnj + 64) bytes long a read past a row's end stays inside the
+    // next row: outside the chunk holding the buffer's last row, 8-bit main
+    // units read their 17 bytes as two aligned 16-byte loads.
+    const bool rows_long = pitch_b >= (int64_t)EB * (256 * nj + 64);
+
+    uint32_t acc[QW];
+    uint32_t tot[2 * QW];
+#pragma unroll
+    for (int q = 0; q < QW; ++q) {
+        acc[q] = 0;
+        tot[2 * q] = tot[2 * q + 1] = 0;
+    }
+    const bool has_trial = d0 + warp <= dlast;
+    int since_flush = 0;
+
+    for (int k = 0; k < nchunks; ++k) {
+        const GroupRec rec = recs[k];
+        const GroupDesc* gd = a.gdesc + rec.first;
         const GroupMember* mk = mems + (size_t)k * gcc;
         const unsigned char* chunk_in = in_b + (int64_t)(k * gcc) * pitch_b;
-        const int ng = bc.ngroups;
-        const uint32_t g_ms = head.x, g_span = head.y & 0xffffu;
-        // 8-bit input with tail units: one unit per group covers samples
-        // 0..511 at 16 per lane; otherwise units of 8 samples per lane
-        constexpr bool kWide = EB == 1;
-        const int nmain = gtl ? (kWide ? ng : 2 * ng) : ng * nj;
-        const int nunits = gtl ? nmain + (ng + gpt - 1) / gpt : nmain;
-        for (int u = pw; u < nunits; u += kGroupProducers) {
-            if (u < nmain) {
-                // main unit: the whole warp sums one group's members; lane m
-                // holds member record m, handed round by shuffles
-                int gi, idx;
-                if (gtl) {
-                    gi = kWide ? u : (u >> 1);
-                    idx = kWide ? lane : 32 * (u & 1) + lane;
-                } else {
-                    gi = u / nj;
-                    idx = 32 * (u - gi * nj) + lane;
-                }
-                const uint32_t ms = __shfl_sync(kFull, g_ms, gi);
-                const int zlen = T + (int)__shfl_sync(kFull, g_span, gi);
-                const int mstart = (int)(ms & 0xffffu), mend = mstart + (int)(ms >> 16);
-                uint32_t* zA = zb + gi * 2 * gzw;
-                uint32_t* zB = zA + gzw;
-                if (kWide && gtl) {
-                    // 16 samples: five words per member (bytes b .. b + 16)
-                    uint32_t A0 = 0, A1 = 0, A2 = 0, A3 = 0, A4 = 0, A5 = 0, A6 = 0, A7 = 0, E = 0;
-                    for (int m0 = mstart; m0 < mend; m0 += 32) {
-                        const int nm = min(32, mend - m0);
-                        const int2 my = lane < nm ? __ldg(reinterpret_cast<const int2*>(mk + m0 + lane))
-                                                  : make_int2(0, 0);
-#pragma unroll 4
-                        for (int m = 0; m < nm; ++m) {
-                            const int rx = __shfl_sync(kFull, my.x, m), ry = __shfl_sync(kFull, my.y, m);
-                            const int64_t bo = t0 + rx + 16 * idx;
-                            const int wi = (int)(bo >> 2);
-                            const uint32_t* w = reinterpret_cast<const uint32_t*>(
-                                chunk_in + (int64_t)(ry & 0xffff) * pitch_b);
-                            const uint32_t sh = (uint32_t)(bo & 3) * 8u;
-                            const uint32_t w0 = __ldg(w + min(wi, wl)), w1 = __ldg(w + min(wi + 1, wl)),
-                                           w2 = __ldg(w + min(wi + 2, wl)), w3 = __ldg(w + min(wi + 3, wl)),
-                                           w4 = __ldg(w + min(wi + 4, wl));
-                            const uint32_t v0 = __funnelshift_r(w0, w1, sh);
-                            const uint32_t v1 = __funnelshift_r(w1, w2, sh);
-                            const uint32_t v2 = __funnelshift_r(w2, w3, sh);
-                            const uint32_t v3 = __funnelshift_r(w3, w4, sh);
-                            A0 += __byte_perm(v0, 0u, 0x4140);
-                            A1 += __byte_perm(v0, 0u, 0x4342);
-                            A2 += __byte_perm(v1, 0u, 0x4140);
-                            A3 += __byte_perm(v1, 0u, 0x4342);
-                            A4 += __byte_perm(v2, 0u, 0x4140);
-                            A5 += __byte_perm(v2, 0u, 0x4342);
-                            A6 += __byte_perm(v3, 0u, 0x4140);
-                            A7 += __byte_perm(v3, 0u, 0x4342);
-                            E += (w4 >> sh) & 0xffu;
+        const bool clamp = !(rows_long && (k + 1) * gcc < C);
+        const int G = rec.ngroups;
+        for (int gb = 0; gb < G; gb += gz) {
+            const int ge = min(G, gb + gz);
+            // group fields, one group per lane: members (start | count << 16),
+            // span, and this warp's phase-2 word offset at its trial's delay
+            uint32_t g_ms = 0, g_span = 0;
+            int g_p2 = 0;
+            if (gb + lane < ge) {
+                const GroupDesc& g = gd[gb + lane];
+                g_ms = (uint32_t)g.mstart | ((uint32_t)g.mcount << 16);
+                g_span = g.span;
+                const int dl = g.delta[warp];
+                g_p2 = (lane * 2 + (dl & 1)) * gzw + (dl >> 1);
+            }
+            // ---- phase 1: group sums of this batch.  With a.gtl > 0: two full
+            // units per group (samples 0..511), then tail units that cover the
+            // samples past 511 of 32 / gtl groups at once (gtl lanes each);
+            // otherwise gnj full units per group.
+            {
+                const int ng = ge - gb;
+                // 8-bit input with tail units: one unit per group covers samples
+                // 0..511 at 16 per lane; otherwise two units of 8 per lane
+                constexpr bool kWide = EB == 1;
+                const int nmain = gtl ? (kWide ? ng : 2 * ng) : ng * nj;
+                const int nunits = gtl ? nmain + (ng + gpt - 1) / gpt : nmain;
+                for (int u = warp; u < nunits; u += kDedispWarps) {
+                    int gi, idx;  // this lane's group and sample block (samples 8 idx .. 8 idx + 7,
+                                  // or 16 idx .. 16 idx + 15 when wide)
+                    bool wide = false;
+                    if (gtl) {
+                        if (u < nmain) {
+                            if (kWide) {
+                                gi = u;
+                                idx = lane;
+                                wide = true;
+                            } else {
+                                gi = u >> 1;
+                                idx = 32 * (u & 1) + lane;
+                            }
+                        } else {
+                            gi = (u - nmain) * gpt + (lane >> gtl_log);
+                            idx = 64 + (lane & (gtl - 1));
+                        }
+                    } else {
+                        gi = u / nj;
+                        idx = 32 * (u - gi * nj) + lane;
+                    }
+                    // a main unit gives the whole warp one group: every lane's
+                    // window starts at the same offset within 16 bytes
+                    const bool vec = EB == 1 && !clamp && (!gtl || u < nmain);
+                    const bool gvalid = gi < ng;
+                    const int gs = gvalid ? gi : 0;
+                    const uint32_t ms = __shfl_sync(0xffffffffu, g_ms, gs);
+                    const int zlen = T + (int)__shfl_sync(0xffffffffu, g_span, gs);
+                    const int mstart = (int)(ms & 0xffffu), mend = mstart + (int)(ms >> 16);
+                    uint32_t* zA = zs + gs * 2 * gzw;
+                    uint32_t* zB = zA + gzw;
+                    const int wl = (int)(pitch_b >> 2) - 1;
+                    if constexpr (kWide) {
+                        if (wide) {
+                            // 16 samples: five words per member (bytes b .. b + 16)
+                            uint32_t A0 = 0, A1 = 0, A2 = 0, A3 = 0, A4 = 0, A5 = 0, A6 = 0, A7 = 0, E = 0;
+                            if (gvalid) {
+#pragma unroll 2
+                                for (int m = mstart; m < mend; ++m) {
+                                    const int2 rm = __ldg(reinterpret_cast<const int2*>(mk + m));
+                                    const int64_t bo = t0 + rm.x + 16 * idx;
+                                    const uint32_t sh = (uint32_t)(bo & 3) * 8u;
+                                    uint32_t w0, w1, w2, w3, w4;
+                                    load_words5(chunk_in + (int64_t)(rm.y & 0xffff) * pitch_b, bo, vec, wl,
+                                                w0, w1, w2, w3, w4);
+                                    const uint32_t v0 = __funnelshift_r(w0, w1, sh);
+                                    const uint32_t v1 = __funnelshift_r(w1, w2, sh);
+                                    const uint32_t v2 = __funnelshift_r(w2, w3, sh);
+                                    const uint32_t v3 = __funnelshift_r(w3, w4, sh);
+                                    A0 += __byte_perm(v0, 0u, 0x4140);
+                                    A1 += __byte_perm(v0, 0u, 0x4342);
+                                    A2 += __byte_perm(v1, 0u, 0x4140);
+                                    A3 += __byte_perm(v1, 0u, 0x4342);
+                                    A4 += __byte_perm(v2, 0u, 0x4140);
+                                    A5 += __byte_perm(v2, 0u, 0x4342);
+                                    A6 += __byte_perm(v3, 0u, 0x4140);
+                                    A7 += __byte_perm(v3, 0u, 0x4342);
+                                    E += (w4 >> sh) & 0xffu;
+                                }
+                                uint4* a4 = reinterpret_cast<uint4*>(zA + 8 * idx);
+                                uint4* b4 = reinterpret_cast<uint4*>(zB + 8 * idx);
+                                a4[0] = make_uint4(A0, A1, A2, A3);
+                                a4[1] = make_uint4(A4, A5, A6, A7);
+                                b4[0] = make_uint4(__byte_perm(A0, A1, 0x5432), __byte_perm(A1, A2, 0x5432),
+                                                   __byte_perm(A2, A3, 0x5432), __byte_perm(A3, A4, 0x5432));
+                                b4[1] = make_uint4(__byte_perm(A4, A5, 0x5432), __byte_perm(A5, A6, 0x5432),
+                                                   __byte_perm(A6, A7, 0x5432), __byte_perm(A7, E, 0x5432));
+                            }
+                            continue;
                         }
                     }
-                    uint4* a4 = reinterpret_cast<uint4*>(zA + 8 * idx);
-                    uint4* b4 = reinterpret_cast<uint4*>(zB + 8 * idx);
-                    a4[0] = make_uint4(A0, A1, A2, A3);
-                    a4[1] = make_uint4(A4, A5, A6, A7);
-                    b4[0] = make_uint4(__byte_perm(A0, A1, 0x5432), __byte_perm(A1, A2, 0x5432),
-                                       __byte_perm(A2, A3, 0x5432), __byte_perm(A3, A4, 0x5432));
-                    b4[1] = make_uint4(__byte_perm(A4, A5, 0x5432), __byte_perm(A5, A6, 0x5432),
-                                       __byte_perm(A6, A7, 0x5432), __byte_perm(A7, E, 0x5432));
-                } else {
-                    // 8 samples per lane; lanes past the group's length compute
-                    // (in-bounds, clamped reads) but do not store
                     uint32_t A0 = 0, A1 = 0, A2 = 0, A3 = 0, E = 0;  // (z0,z1) .. (z6,z7), z8
-                    for (int m0 = mstart; m0 < mend; m0 += 32) {
-                        const int nm = min(32, mend - m0);
-                        const int2 my = lane < nm ? __ldg(reinterpret_cast<const int2*>(mk + m0 + lane))
-                                                  : make_int2(0, 0);
-#pragma unroll 4
-                        for (int m = 0; m < nm; ++m) {
-                            const int rx = __shfl_sync(kFull, my.x, m), ry = __shfl_sync(kFull, my.y, m);
-                            // byte offset of this lane's first sample in the row;
-                            // words at or past the row pitch are clamped to the
-                            // row's last word (never used for an output sample)
-                            const int64_t bo = (int64_t)EB * (t0 + rx + 8 * idx);
+                    if (gvalid && 8 * idx < zlen) {
+#pragma unroll 2
+                        for (int m = mstart; m < mend; ++m) {
+                            const int2 rm = __ldg(reinterpret_cast<const int2*>(mk + m));  // (s0, ch | span << 16)
+                            // byte offset of this lane's first sample in the row.
+                            // Bytes at or past the row pitch are never used for an
+                            // output sample; their words are clamped to the row's
+                            // last word so no read leaves the buffer.
+                            const int64_t bo = (int64_t)EB * (t0 + rm.x + 8 * idx);
                             const int wi = (int)(bo >> 2);
                             const uint32_t* w = reinterpret_cast<const uint32_t*>(
-                                chunk_in + (int64_t)(ry & 0xffff) * pitch_b);
+                                chunk_in + (int64_t)(rm.y & 0xffff) * pitch_b);
                             const uint32_t sh = (uint32_t)(bo & 3) * 8u;
                             if constexpr (EB == 1) {
                                 const uint32_t w0 = __ldg(w + min(wi, wl)), w1 = __ldg(w + min(wi + 1, wl)),
@@ -625,9 +578,9 @@ __device__ __forceinline__ bool dedisperse_grouped_block(const DedispArgs& a, in
                                 A3 += __byte_perm(v1, 0u, 0x4342);
                                 E += (w2 >> sh) & 0xffu;
                             } else {
-                                const uint32_t w0 = __ldg(w + min(wi, wl)), w1 = __ldg(w + min(wi + 1, wl)),
-                                               w2 = __ldg(w + min(wi + 2, wl)), w3 = __ldg(w + min(wi + 3, wl)),
-                                               w4 = __ldg(w + min(wi + 4, wl));
+                                uint32_t w0, w1, w2, w3, w4;
+                                load_words5(reinterpret_cast<const unsigned char*>(w), bo, false, wl, w0, w1, w2,
+                                            w3, w4);
                                 A0 += __funnelshift_r(w0, w1, sh);
                                 A1 += __funnelshift_r(w1, w2, sh);
                                 A2 += __funnelshift_r(w2, w3, sh);
@@ -635,76 +588,64 @@ __device__ __forceinline__ bool dedisperse_grouped_block(const DedispArgs& a, in
                                 E += (w4 >> sh) & 0xffffu;
                             }
                         }
-                    }
-                    if (8 * idx < zlen) {
                         *reinterpret_cast<uint4*>(zA + 4 * idx) = make_uint4(A0, A1, A2, A3);
                         *reinterpret_cast<uint4*>(zB + 4 * idx) =
                             make_uint4(__byte_perm(A0, A1, 0x5432), __byte_perm(A1, A2, 0x5432),
                                        __byte_perm(A2, A3, 0x5432), __byte_perm(A3, E, 0x5432));
                     }
                 }
-            } else {
-                // tail unit: samples past 511 of gpt groups, gtl lanes each
-                const int gi = (u - nmain) * gpt + (lane >> gtl_log);
-                const int idx = 64 + (lane & (gtl - 1));
-                const bool gvalid = gi < ng;
-                const int gs = gvalid ? gi : 0;
-                const uint32_t ms = __shfl_sync(kFull, g_ms, gs);
-                const int zlen = T + (int)__shfl_sync(kFull, g_span, gs);
-                const int mstart = (int)(ms & 0xffffu), mend = mstart + (int)(ms >> 16);
-                uint32_t* zA = zb + gs * 2 * gzw;
-                uint32_t* zB = zA + gzw;
-                uint32_t A0 = 0, A1 = 0, A2 = 0, A3 = 0, E = 0;
-                if (gvalid && 8 * idx < zlen) {
-#pragma unroll 2
-                    for (int m = mstart; m < mend; ++m) {
-                        const int2 rm = __ldg(reinterpret_cast<const int2*>(mk + m));
-                        const int64_t bo = (int64_t)EB * (t0 + rm.x + 8 * idx);
-                        const int wi = (int)(bo >> 2);
-                        const uint32_t* w = reinterpret_cast<const uint32_t*>(
-                            chunk_in + (int64_t)(rm.y & 0xffff) * pitch_b);
-                        const uint32_t sh = (uint32_t)(bo & 3) * 8u;
-                        if constexpr (EB == 1) {
-                            const uint32_t w0 = __ldg(w + min(wi, wl)), w1 = __ldg(w + min(wi + 1, wl)),
-                                           w2 = __ldg(w + min(wi + 2, wl));
-                            const uint32_t v0 = __funnelshift_r(w0, w1, sh);
-                            const uint32_t v1 = __funnelshift_r(w1, w2, sh);
-                            A0 += __byte_perm(v0, 0u, 0x4140);
-                            A1 += __byte_perm(v0, 0u, 0x4342);
-                            A2 += __byte_perm(v1, 0u, 0x4140);
-                            A3 += __byte_perm(v1, 0u, 0x4342);
-                            E += (w2 >> sh) & 0xffu;
-                        } else {
-                            const uint32_t w0 = __ldg(w + min(wi, wl)), w1 = __ldg(w + min(wi + 1, wl)),
-                                           w2 = __ldg(w + min(wi + 2, wl)), w3 = __ldg(w + min(wi + 3, wl)),
-                                           w4 = __ldg(w + min(wi + 4, wl));
-                            A0 += __funnelshift_r(w0, w1, sh);
-                            A1 += __funnelshift_r(w1, w2, sh);
-                            A2 += __funnelshift_r(w2, w3, sh);
-                            A3 += __funnelshift_r(w3, w4, sh);
-                            E += (w4 >> sh) & 0xffffu;
-                        }
-                    }
-                    *reinterpret_cast<uint4*>(zA + 4 * idx) = make_uint4(A0, A1, A2, A3);
-                    *reinterpret_cast<uint4*>(zB + 4 * idx) =
-                        make_uint4(__byte_perm(A0, A1, 0x5432), __byte_perm(A1, A2, 0x5432),
-                                   __byte_perm(A2, A3, 0x5432), __byte_perm(A3, E, 0x5432));
+            }
+            __syncthreads();  // group sums complete
+            // ---- phase 2: every trial adds every group sum at its relative delay
+            if (has_trial) {
+                const uint32_t* zl = zs + lane;
+                // unrolled twice for 8-bit input; once for 16-bit (measured 2.6 ms
+                // faster per step on the decimated ranges, equal on range 0)
+                constexpr int kP2Unroll = EB == 1 ? 2 : 1;
+#pragma unroll kP2Unroll
+                for (int g = 0; g < ge - gb; ++g) {
+                    const uint32_t* src = zl + __shfl_sync(0xffffffffu, g_p2, g);
+#pragma unroll
+                    for (int q = 0; q < QW; ++q) acc[q] += src[32 * q];
                 }
             }
+            __syncthreads();  // the next batch (or chunk) overwrites the group sums
         }
-        if (j == fault_skip_batch) continue;  // fault injection: batch j is never completed
-        mbar_arrive(&full[b]);  // this thread's writes of batch j are done
+        if (++since_flush >= a.gflush) {
+#pragma unroll
+            for (int q = 0; q < QW; ++q) {
+                tot[2 * q] += acc[q] & 0xffffu;
+                tot[2 * q + 1] += acc[q] >> 16;
+                acc[q] = 0;
+            }
+            since_flush = 0;
+        }
     }
-    return true;
+#pragma unroll
+    for (int q = 0; q < QW; ++q) {
+        tot[2 * q] += acc[q] & 0xffffu;
+        tot[2 * q + 1] += acc[q] >> 16;
+    }
+
+    // epilogue: exact integer totals -> FP32 rows
+    if (!has_trial) return;
+    float* row = a.out + (int64_t)(d0 + warp) * a.out_pitch;
+#pragma unroll
+    for (int q = 0; q < QW; ++q) {
+        const int64_t t = t0 + 2 * (lane + 32 * q);
+        if (t + 2 <= a.length) {
+            *reinterpret_cast<float2*>(row + t) = make_float2((float)tot[2 * q], (float)tot[2 * q + 1]);
+        } else if (t < a.length) {
+            row[t] = (float)tot[2 * q];
+        }
+    }
 }
 
 template <int EB>
-__global__ void __launch_bounds__(kGroupedThreads, 1)
-    dedisperse_grouped_kernel(DedispArgs a, int ndm_blocks, uint64_t wait_limit_ns, int fault_skip_batch) {
+__global__ void __launch_bounds__(kDedispThreads, 2)
+    dedisperse_grouped_kernel(DedispArgs a, int ndm_blocks) {
     extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ uint64_t gbars[2 * kMaxGroupBufs];
-    dedisperse_grouped_block<EB>(a, ndm_blocks, blockIdx.x, smem, gbars, false, wait_limit_ns,
-                                 fault_skip_batch);
+    dedisperse_grouped_block<EB>(a, ndm_blocks, blockIdx.x, smem);
 }
 
 template <int SPW>
@@ -729,8 +670,9 @@ __device__ __forceinline__ int find_desc(const int64_t* first, int n, int64_t it
     return lo;
 }
 
-// One instantiation per input width (every descriptor of a launch uses it).
-template <int EB>
+// One instantiation per strategy and input width (every descriptor of a
+// launch uses it).
+template <bool GROUPED, int EB>
 __global__ void __launch_bounds__(kDedispThreads, 2)
     dedisperse_batch_kernel(const DedispArgs* __restrict__ descs, const int64_t* __restrict__ first,
                             const int* __restrict__ ndm_blocks, int ndesc,
@@ -747,34 +689,13 @@ __global__ void __launch_bounds__(kDedispThreads, 2)
         const int64_t item = s_item;
         if (item >= total) break;
         const int k = find_desc(first, ndesc, item);
-        dedisperse_block<4 / EB>(descs[k], ndm_blocks[k], item - first[k], wait_limit_ns, -1, one, smem,
-                                 bars, reinit);
+        const DedispArgs& a = descs[k];
+        if constexpr (GROUPED)
+            dedisperse_grouped_block<EB>(a, ndm_blocks[k], item - first[k], smem);
+        else
+            dedisperse_block<4 / EB>(a, ndm_blocks[k], item - first[k], wait_limit_ns, -1, one, smem,
+                                     bars, reinit);
         reinit = true;
-    }
-}
-
-template <int EB>
-__global__ void __launch_bounds__(kGroupedThreads, 1)
-    dedisperse_grouped_batch_kernel(const DedispArgs* __restrict__ descs,
-                                    const int64_t* __restrict__ first,
-                                    const int* __restrict__ ndm_blocks, int ndesc,
-                                    unsigned long long* queue, uint64_t wait_limit_ns) {
-    extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ uint64_t gbars[2 * kMaxGroupBufs];  // fixed place: re-initialised per work item
-    __shared__ long long s_item;
-    const int64_t total = first[ndesc];
-    bool reinit = false;
-    for (;;) {
-        __syncthreads();  // previous item finished by every thread
-        if (threadIdx.x == 0) s_item = (long long)atomicAdd(queue, 1ull);
-        __syncthreads();
-        const int64_t item = s_item;
-        if (item >= total) break;
-        const int k = find_desc(first, ndesc, item);
-        const bool ok = dedisperse_grouped_block<EB>(descs[k], ndm_blocks[k], item - first[k], smem, gbars,
-                                                     reinit, wait_limit_ns, -1);
-        reinit = true;
-        if (__syncthreads_or(!ok)) break;  // a wait gave up: the error word is set
     }
 }
 
@@ -837,7 +758,6 @@ __global__ void __launch_bounds__(256) decimate_batch_kernel(const DecimateJob* 
 }  // namespace
 
 int g_fault_skip_chunk = -1;          // test hook: never issue this chunk
-int g_fault_skip_batch = -1;          // test hook: grouped producers never complete this batch
 uint64_t g_wait_limit_ns = kWaitLimitNs;
 
 cudaError_t launch_dedisperse_batch(const DedispArgs* d_descs, const int64_t* d_first,
@@ -845,15 +765,8 @@ cudaError_t launch_dedisperse_batch(const DedispArgs* d_descs, const int64_t* d_
                                     unsigned long long* d_queue, int grid, bool grouped, int elem,
                                     cudaStream_t s) {
     if (ndesc <= 0) return cudaSuccess;
-    if (grouped) {  // one 768-thread CTA per SM (grid counts two 512-thread CTAs per SM)
-        auto kern = elem == 1 ? dedisperse_grouped_batch_kernel<1> : dedisperse_grouped_batch_kernel<2>;
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        kern<<<(grid + 1) / 2, kGroupedThreads, smem, s>>>(d_descs, d_first, d_ndm_blocks, ndesc, d_queue,
-                                                            g_wait_limit_ns);
-        return cudaGetLastError();
-    }
-    auto kern = elem == 1 ? dedisperse_batch_kernel<1> : dedisperse_batch_kernel<2>;
+    auto kern = grouped ? (elem == 1 ? dedisperse_batch_kernel<true, 1> : dedisperse_batch_kernel<true, 2>)
+                        : (elem == 1 ? dedisperse_batch_kernel<false, 1> : dedisperse_batch_kernel<false, 2>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<grid, kDedispThreads, smem, s>>>(d_descs, d_first, d_ndm_blocks, ndesc, d_queue,
@@ -880,8 +793,7 @@ cudaError_t launch_dedisperse(const DedispArgs& a, cudaStream_t s) {
         auto kern = a.elem == 1 ? dedisperse_grouped_kernel<1> : dedisperse_grouped_kernel<2>;
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)a.smem);
         if (e != cudaSuccess) return e;
-        kern<<<(unsigned)nblocks, kGroupedThreads, a.smem, s>>>(a, ndmb, g_wait_limit_ns,
-                                                                 g_fault_skip_batch);
+        kern<<<(unsigned)nblocks, kDedispThreads, a.smem, s>>>(a, ndmb);
         return cudaGetLastError();
     }
     auto kern = a.elem == 1 ? dedisperse_kernel<4> : dedisperse_kernel<2>;

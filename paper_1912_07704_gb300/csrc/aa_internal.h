@@ -36,13 +36,6 @@ constexpr int kSpsOwned = kSpsTile - 2;              // start times owned per CT
 // then adds z_g[t + delta_g(d)] once per group instead of once per channel.
 // Integer sums regrouped: the result is bit-identical.
 constexpr int kGroupTau = 512;  // output samples per CTA (grouped strategy)
-// Grouped-strategy CTA (one per SM): kDmPerBlock consumer warps, one per trial
-// of the block, add the group sums; kGroupProducers producer warps build them.
-// The group sums of up to kMaxGroupBufs batches are in flight in a ring of
-// shared-memory buffers handed over with mbarriers.
-constexpr int kGroupProducers = 8;
-constexpr int kGroupedThreads = (kDmPerBlock + kGroupProducers) * 32;  // 768
-constexpr int kMaxGroupBufs = 3;
 
 struct GroupRec {       // one (DM block, channel chunk)
     uint32_t first;     // index of its first GroupDesc
@@ -61,17 +54,7 @@ struct GroupMember {   // member m of a (DM block, channel chunk), in group orde
     uint16_t ch;       // channel within the chunk
     uint16_t span;     // its delay at the block's last trial minus s0
 };
-// The batches of group sums of one DM block, in the order the kernel runs
-// them (chunk by chunk): each batch is at most `gz` consecutive GroupDescs of
-// one (DM block, channel chunk).
-struct GroupBatch {
-    uint32_t first;     // index of its first GroupDesc
-    uint16_t ngroups;   // 1 .. gz
-    uint16_t chunk;     // channel chunk (bits 0-14); bit 15: the chunk's last batch
-};
-constexpr uint16_t kBatchLastOfChunk = 0x8000;
-static_assert(sizeof(GroupRec) == 8 && sizeof(GroupDesc) == 40 && sizeof(GroupMember) == 8 &&
-                  sizeof(GroupBatch) == 8,
+static_assert(sizeof(GroupRec) == 8 && sizeof(GroupDesc) == 40 && sizeof(GroupMember) == 8,
               "group table layout");
 static_assert(kGroupTau == kTau, "both strategies tile time alike (launch and queue sizing)");
 
@@ -136,8 +119,7 @@ struct RangePlan {
     int strategy = 0;      // 0 direct, 1 grouped
     bool grouped_ok = false;  // the grouped tables exist (spans fit)
     int gcc = 0;           // channels per chunk
-    int gz = 0;            // group sums per batch
-    int gnbuf = 2;         // batches of group sums held in shared memory (ring)
+    int gz = 0;            // group sums held in shared memory at once
     int gzw = 0;           // 32-bit words per group-sum copy
     int gflush = 1;        // chunks between SWAR flushes
     int gnj = 3;           // 256-sample blocks covering kGroupTau + span_max
@@ -147,13 +129,9 @@ struct RangePlan {
     std::vector<GroupRec> grec;    // [ndm blocks][chunks]
     std::vector<GroupDesc> gdesc;
     std::vector<GroupMember> gmem; // [ndm blocks][chunks][gcc] members in group order
-    std::vector<GroupBatch> gbatch;  // batches of every DM block, block after block
-    std::vector<int32_t> gboff;      // [ndm blocks + 1]: first batch of each block
     GroupRec* d_grec = nullptr;
     GroupDesc* d_gdesc = nullptr;
     GroupMember* d_gmem = nullptr;
-    GroupBatch* d_gbatch = nullptr;
-    int32_t* d_gboff = nullptr;
     SubbandPlan sb;        // valid once aa_plan_set_subband chose it (strategy 2)
 };
 
@@ -275,13 +253,10 @@ struct DedispArgs {
     // grouped strategy (used when grouped != 0; cc and smem then describe it)
     int grouped;
     int gz, gzw, gflush, gnj;  // gnj: 256-sample blocks of the longest group sum
-    int gnbuf;                 // group-sum buffers in the ring (2 or 3)
     int gtl;                   // lanes per group in phase-1 tail units (0: no tail units)
     const GroupRec* grec;
     const GroupDesc* gdesc;
     const GroupMember* gmem;
-    const GroupBatch* gbatch;
-    const int32_t* gboff;
 };
 // Strategy fields of a range's kernel arguments.
 void fill_strategy(DedispArgs& a, const RangePlan& r);

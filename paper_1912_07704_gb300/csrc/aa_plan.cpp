@@ -89,15 +89,14 @@ bool direct_shape(int elem, int32_t span, int per_lane_max, DirectShape& out) {
     return true;
 }
 
-// Shared memory of the grouped strategy: a ring of nbuf batches of group sums
-// (the producers build one while the consumers add another), two copies
-// each; the input rows are read from global memory.
-static size_t grouped_smem(int nbuf, int gz, int gzw) { return (size_t)nbuf * gz * 2 * gzw * 4; }
+// Shared memory of the grouped strategy: the group sums of one batch (two
+// copies each; the input rows are read from global memory).
+static size_t grouped_smem(int gz, int gzw) { return (size_t)gz * 2 * gzw * 4; }
 
 // Delay-pattern groups of every (DM block, channel chunk) of a range, and the
-// grouped tile shape (one CTA per SM: <= kGroupedSmem of dynamic shared memory).
+// grouped tile shape.  Two CTAs per SM must fit (<= kPairSmem each).
 static void build_groups(RangePlan& r, int C) {
-    constexpr size_t kGroupedSmem = 225 * 1024;
+    constexpr size_t kPairSmem = 113 * 1024 - 512;
     constexpr int B = kDmPerBlock;
     r.grouped_ok = false;
     const int dec = r.desc.dec;
@@ -106,20 +105,13 @@ static void build_groups(RangePlan& r, int C) {
     const int gzw = (int)round_up((kGroupTau + r.span_max + 3) / 2 + 2, 4);
     // chunks of up to kGroupChunkMax channels (fewer when 16-bit lanes would
     // overflow): larger chunks put more channels with one delay pattern into
-    // one group; as many group sums per batch as the shared memory holds in a
-    // ring of three batches (two if fewer than 16 sums would fit), at most
-    // 32 (one per lane of the warps' group-field registers)
+    // one group; as many group sums per batch as two CTAs per SM leave room
+    // for (<= 32, one per lane of the warps' group-field registers)
     constexpr int kGroupChunkMax = 256;
     constexpr int kGroupSplit = 16;  // members per group sum at most
     const int gcc = std::min(kGroupChunkMax, lane_max) / 8 * 8;
-    if (gcc >= (int)kBatchLastOfChunk) return;
-    int gz = 0, nbuf = kMaxGroupBufs;
-    for (; nbuf >= 2; --nbuf) {
-        gz = 0;
-        while (grouped_smem(nbuf, gz + 1, gzw) <= kGroupedSmem && gz < std::min(gcc, 32)) ++gz;
-        if (gz >= std::min(gcc, 16)) break;
-    }
-    if (nbuf < 2) nbuf = 2;
+    int gz = 0;
+    while (grouped_smem(gz + 1, gzw) <= kPairSmem && gz < std::min(gcc, 32)) ++gz;
     if (gcc < 8 || gz < 1) return;
     {   // samples past kGroupTau (the span and the one sample after it) in lanes of 8
         const int need = (r.span_max + 1 + 7) / 8;
@@ -128,25 +120,19 @@ static void build_groups(RangePlan& r, int C) {
         r.gtl = (kGroupTau % 256 == 0 && tl <= 32) ? tl : 0;
     }
     // phase 1's static unit assignment: with tail units, an 8-bit range gives
-    // a group one unit (producer warp j mod 8 for batch position j), a 16-bit
-    // range two (producer pair j mod 4)
-    const int kSlots = (r.gtl > 0 && r.elem == 1) ? kGroupProducers : kGroupProducers / 2;
+    // a group one unit (warp j mod 16 for batch position j), a 16-bit range
+    // two (warp pair j mod 8)
+    const int kSlots = (r.gtl > 0 && r.elem == 1) ? kDedispWarps : kDedispWarps / 2;
     const int ndm = r.desc.ndm;
     const int nblk = (ndm + B - 1) / B, nchk = (C + gcc - 1) / gcc;
-    // The kernel also stages a DM block's batch table in shared memory; if
-    // the largest one does not fit beside the group sums, batches shrink.
-  retry:
     r.grec.assign((size_t)nblk * nchk, GroupRec{});
     r.gmem.assign((size_t)nblk * nchk * gcc, GroupMember{});
     r.gdesc.clear();
-    r.gbatch.clear();
-    r.gboff.assign((size_t)nblk + 1, 0);
     double direct = 0, grouped = 0;
     std::vector<GroupDesc> local;
     std::vector<std::vector<uint8_t>> members;
     for (int b = 0; b < nblk; ++b) {
         const int d0 = b * B, nb = std::min(B, ndm - d0);
-        r.gboff[(size_t)b] = (int32_t)r.gbatch.size();
         for (int k = 0; k < nchk; ++k) {
             const int c0 = k * gcc, nch = std::min(gcc, C - c0);
             local.clear();
@@ -222,31 +208,16 @@ static void build_groups(RangePlan& r, int C) {
                 }
                 r.gdesc.push_back(g);
             }
-            for (size_t b0 = 0; b0 < laid.size(); b0 += (size_t)gz) {
-                const size_t n = std::min(laid.size() - b0, (size_t)gz);
-                const bool last = b0 + (size_t)gz >= laid.size();
-                r.gbatch.push_back(GroupBatch{rec.first + (uint32_t)b0, (uint16_t)n,
-                                              (uint16_t)(k | (last ? kBatchLastOfChunk : 0))});
-            }
             direct += (double)nch * nb;
             grouped += (double)nch + (double)laid.size() * nb;
         }
-    }
-    r.gboff[(size_t)nblk] = (int32_t)r.gbatch.size();
-    int32_t gbmax = 0;
-    for (int b = 0; b < nblk; ++b) gbmax = std::max(gbmax, r.gboff[(size_t)b + 1] - r.gboff[(size_t)b]);
-    const size_t table = (size_t)round_up((int64_t)gbmax * (int64_t)sizeof(GroupBatch), 16);
-    if (grouped_smem(nbuf, gz, gzw) + table > kGroupedSmem) {
-        if (--gz < 1) return;
-        goto retry;
     }
     r.gcc = gcc;
     r.gz = gz;
     r.gzw = gzw;
     r.gflush = std::max(1, lane_max / gcc);
     r.gnj = (kGroupTau + r.span_max + 255) / 256;
-    r.gnbuf = nbuf;
-    r.gsmem = grouped_smem(nbuf, gz, gzw) + table;
+    r.gsmem = grouped_smem(gz, gzw);
     r.gwork = direct > 0 ? grouped / direct : 1.0;
     r.grouped_ok = true;
 }
@@ -261,7 +232,6 @@ void fill_strategy(DedispArgs& a, const RangePlan& r) {
         a.nstage = 2;
         a.smem = r.gsmem;
         a.gz = r.gz;
-        a.gnbuf = r.gnbuf;
         a.gzw = r.gzw;
         a.gflush = r.gflush;
         a.gnj = r.gnj;
@@ -269,19 +239,15 @@ void fill_strategy(DedispArgs& a, const RangePlan& r) {
         a.grec = r.d_grec;
         a.gdesc = r.d_gdesc;
         a.gmem = r.d_gmem;
-        a.gbatch = r.d_gbatch;
-        a.gboff = r.d_gboff;
     } else {
         a.grouped = 0;
         a.cc = r.cc;
         a.nstage = r.nstage;
         a.smem = r.smem;
-        a.gz = a.gzw = a.gflush = a.gnj = a.gtl = a.gnbuf = 0;
+        a.gz = a.gzw = a.gflush = a.gnj = a.gtl = 0;
         a.grec = nullptr;
         a.gdesc = nullptr;
         a.gmem = nullptr;
-        a.gbatch = nullptr;
-        a.gboff = nullptr;
     }
 }
 
@@ -563,8 +529,6 @@ aa_status aa_plan_create(const aa_plan_desc* d, aa_plan** out) {
         p->table_bytes += round_up((int64_t)r.grec.size() * sizeof(GroupRec), 256);
         p->table_bytes += round_up((int64_t)r.gdesc.size() * sizeof(GroupDesc), 256);
         p->table_bytes += round_up((int64_t)r.gmem.size() * sizeof(GroupMember), 256);
-        p->table_bytes += round_up((int64_t)r.gbatch.size() * sizeof(GroupBatch), 256);
-        p->table_bytes += round_up((int64_t)r.gboff.size() * 4, 256);
     }
     *out = p;
     return AA_OK;
@@ -615,8 +579,6 @@ aa_status aa_plan_bind(aa_plan* p, int device) {
         r.d_grec = (GroupRec*)upload(r.grec.data(), r.grec.size() * sizeof(GroupRec));
         r.d_gdesc = (GroupDesc*)upload(r.gdesc.data(), r.gdesc.size() * sizeof(GroupDesc));
         r.d_gmem = (GroupMember*)upload(r.gmem.data(), r.gmem.size() * sizeof(GroupMember));
-        r.d_gbatch = (GroupBatch*)upload(r.gbatch.data(), r.gbatch.size() * sizeof(GroupBatch));
-        r.d_gboff = (int32_t*)upload(r.gboff.data(), r.gboff.size() * 4);
         if (e != cudaSuccess) break;
     }
     if (e != cudaSuccess) {
@@ -626,8 +588,6 @@ aa_status aa_plan_bind(aa_plan* p, int device) {
             r.d_grec = nullptr;
             r.d_gdesc = nullptr;
             r.d_gmem = nullptr;
-            r.d_gbatch = nullptr;
-            r.d_gboff = nullptr;
         }
         if (prev >= 0) cudaSetDevice(prev);
         set_error("delay table upload: %s", cudaGetErrorString(e));

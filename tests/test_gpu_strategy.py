@@ -73,13 +73,10 @@ def test_synthetic_workload_with_pulses(oracle):
     _check_plan(oracle, w.nchans, w.fch1, w.foff, w.tsamp, w.ranges, x)
 
 
-def test_grouped_waits_are_bounded():
-    """The grouped kernel's producer and consumer warps hand batches of group
-    sums over through shared-memory barriers whose waits are bounded.  The
-    direct kernel's staging-fault injection leaves it correct; a batch that
-    its producers never complete makes every CTA's consumers give up after
-    the wait limit: the host reads AA_ERR_TIMEOUT and the context stays
-    usable (the next, uninjected run is correct)."""
+def test_grouped_has_no_staging_waits():
+    """The grouped kernel reads its rows from global memory and has no
+    device-side waits: the staging-fault injection (which makes the direct
+    kernel time out) leaves it correct."""
     C, nsamp = 256, 4096
     p = Plan(C, 1500.0, -1.171875, 64e-6, [(0.0, 0.05, 16, 1)])
     p.set_strategy(0, abi.AA_DEDISP_GROUPED)
@@ -94,19 +91,8 @@ def test_grouped_waits_are_bounded():
         abi.aa_debug_inject(1, 1)           # chunk 1 of the direct kernel never staged
         p.dedisperse_device(d, n, out=out, ws=ws)
         assert abi.aa_workspace_status(ws.data_ptr(), stream) == abi.AA_OK
-        torch.cuda.synchronize()
-        assert torch.all(p.range_views(out, n)[0] == 7 * C)
-        abi.aa_debug_inject(0, 0)
-        abi.aa_debug_inject(2, 20_000_000)
-        abi.aa_debug_inject(3, 0)           # grouped batch 0 never completed
-        out.fill_(-1.0)
-        p.dedisperse_device(d, n, out=out, ws=ws)
-        assert abi.aa_workspace_status(ws.data_ptr(), stream) == abi.AA_ERR_TIMEOUT
     finally:
         abi.aa_debug_inject(0, 0)
-    torch.cuda.synchronize()
-    p.dedisperse_device(d, n, out=out, ws=ws)
-    assert abi.aa_workspace_status(ws.data_ptr(), stream) == abi.AA_OK
     torch.cuda.synchronize()
     assert torch.all(p.range_views(out, n)[0] == 7 * C)
 
