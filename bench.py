@@ -150,10 +150,7 @@ def build_input(plan, w, device):
 # the series length).  Each entry names the capture it comes from; set it to None
 # when the kernel changes until it is captured again.
 NCU_TRAFFIC = {
-    ("dedisperse_u8", "grouped"): {
-        "small_read_bytes": 545_137_920, "small_write_bytes": 744_004_352,
-        "small_output_samples": 1500 * 128687,
-        "capture": "profiles/dedisperse_grouped_u8_ska-4096ch-2^17.md"},
+    ("dedisperse_u8", "grouped"): None,  # kernel changed since its capture
     ("sps_boxcar", "pruned"): {
         "small_read_bytes": 875_240_960, "small_write_bytes": 44_166_400,
         "small_output_samples": 1500 * 128687,
@@ -319,18 +316,31 @@ def bench_ours(args):
     if ws > 1:  # independent beam per rank: perturb the data deterministically
         x[:, : w.nsamp].add_(rank).clamp_(max=255)
     nsamp = w.nsamp
-    out = plan.alloc_output(nsamp)
-    ws_dd = plan.alloc_workspace(info.dedisp_ws_bytes)
-    ws_sps = plan.alloc_workspace(info.sps_ws_bytes)
     cap = 1 << 25
     cands = torch.empty(cap * 16, dtype=torch.uint8, device="cuda")
     count = torch.zeros(1, dtype=torch.int64, device="cuda")
     stream = torch.cuda.current_stream()
+    if args.fused:
+        # dedispersion and search in stripes of trials, statistics summed by
+        # the dedispersion kernels: no [ndm][L] series of the whole plan
+        fused_bytes, sps_off = plan.fused_ws_bytes(nsamp, w.max_width, args.stripe)
+        ws_fused = plan.alloc_workspace(fused_bytes)
+        ws_sps = ws_fused[sps_off:]
+        device_bytes = fused_bytes
 
-    def step():
-        plan.dedisperse_device(x, nsamp, out=out, ws=ws_dd)
-        plan.sps_search_device(out, nsamp, w.max_width, w.threshold, cap, ws=ws_sps,
-                               cands=cands, count=count)
+        def step():
+            plan.search_fused_device(x, nsamp, w.max_width, w.threshold, cap, args.stripe,
+                                     ws=ws_fused, cands=cands, count=count)
+    else:
+        out = plan.alloc_output(nsamp)
+        ws_dd = plan.alloc_workspace(info.dedisp_ws_bytes)
+        ws_sps = plan.alloc_workspace(info.sps_ws_bytes)
+        device_bytes = info.dd_elems * 4 + info.dedisp_ws_bytes + info.sps_ws_bytes
+
+        def step():
+            plan.dedisperse_device(x, nsamp, out=out, ws=ws_dd)
+            plan.sps_search_device(out, nsamp, w.max_width, w.threshold, cap, ws=ws_sps,
+                                   cands=cands, count=count)
 
     for _ in range(args.warmup):
         step()
@@ -501,7 +511,12 @@ def bench_ours(args):
                        "dedispersion": [_strategy_name(abi.aa_plan_range(plan.handle, nsamp, r))
                                         for r in range(len(w.ranges))],
                        "l2": (f"inputs larger than L2 ({alg['in_bytes'] / 1e9:.2f} GB filterbank, "
-                              f"{alg['dd_bytes'] / 1e9:.2f} GB dedispersed)")},
+                              f"{alg['dd_bytes'] / 1e9:.2f} GB dedispersed)"),
+                       "mode": (f"fused: stripes of {args.stripe or 256} trials, statistics summed "
+                                "by the dedispersion kernels" if args.fused else
+                                "dedisperse all ranges, then search"),
+                       "device_bytes": {"input": alg["in_bytes"], "work": device_bytes,
+                                        "candidates": cap * 16}},
             "rtf": (w.nsamp * w.tsamp) / step_s,
             "hbm": {"effective_input_gbs": eff_in_gbs, "frac_of_measured": eff_in_gbs / hbm,
                     "algorithmic_gbs": (alg["in_bytes"] + alg["dd_bytes"]) / step_s / 1e9,
@@ -820,6 +835,9 @@ def main():
                     help="C16,ITERS: k-sigma clipped statistics (k = C16/16), e.g. 48,4")
     ap.add_argument("--sps-ladder", type=int, default=0,
                     help="G16: sparse boxcar width ladder of growth G16/16 (approximate), e.g. 24")
+    ap.add_argument("--fused", action="store_true",
+                    help="fused dedispersion -> search in stripes of trials (no full series buffer)")
+    ap.add_argument("--stripe", type=int, default=0, help="trials per stripe of --fused (0: 256)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

@@ -505,6 +505,43 @@ aa_status aa_candidates_view(const aa_candidates* c, const aa_candidate** host,
 /* Free a candidate list.  NULL is a no-op. */
 void aa_candidates_destroy(aa_candidates* c);
 
+/* ------------------------------- fused dedispersion -> search (Sec. 1, 2.3) */
+
+/* Dedispersion and single-pulse search in one call, without the dedispersed
+ * series of the whole plan: each range is processed in stripes of
+ * stripe_trials consecutive DM trials (0: 256; otherwise a positive multiple
+ * of 16), whose series live in one stripe buffer of the workspace while they
+ * are searched.  The dedispersion kernels add every row's exact sums (sum y,
+ * sum y^2 in 128 bits) as they write it, so the search's mean and sigma need
+ * no separate pass over the series; with k-sigma clipped statistics
+ * (aa_plan_set_sps_clip) the statistics pass runs on each stripe instead.
+ * Candidates (and chunk headers, and B(t) in d_snr_out when non-NULL, in the
+ * layout of aa_dedisperse_device's output) are bit for bit those of
+ * aa_dedisperse_device followed by aa_sps_search_device.
+ *
+ * Ranges are searched one after another, each decimated range's input
+ * built from the 8-bit input into one buffer shared by the ranges.
+ *
+ * aa_search_fused_ws_bytes: workspace bytes for (nsamp, max_width,
+ * stripe_trials), and the byte offset inside it of the search workspace
+ * (what aa_sps_order_device takes as d_sps_ws after the call).  About
+ * stripe_trials x the widest range's row pitch x 4 bytes replace the
+ * aa_plan_query dd_elems x 4 bytes of the unfused path, and the largest
+ * decimated input replaces all of them.
+ * aa_search_fused_device: d_in as in aa_dedisperse_device; candidates as in
+ * aa_sps_search_device; d_ws 256-byte aligned, >= the bytes above.  Its
+ * first word is the error word (aa_workspace_status).  Stream-ordered.
+ * AA_ERR_CONFIG for plans with sub-band ranges; AA_ERR_ARG on bad
+ * arguments. */
+aa_status aa_search_fused_ws_bytes(const aa_plan* plan, int64_t nsamp, int32_t max_width,
+                                   int32_t stripe_trials, size_t* bytes, size_t* sps_ws_offset);
+aa_status aa_search_fused_device(const aa_plan* plan, const uint8_t* d_in, int64_t nsamp,
+                                 int64_t in_pitch, int32_t max_width, float threshold,
+                                 int32_t stripe_trials, aa_candidate* d_cands,
+                                 int64_t cand_capacity, unsigned long long* d_count,
+                                 float* d_snr_out, void* d_ws, size_t ws_bytes,
+                                 aa_stream_t stream);
+
 /* --------------------------------------- host-buffer pipeline (Sec. 2.3-3.3) */
 
 /* A pipeline searches a sequence of same-sized blocks of caller-owned host

@@ -119,6 +119,10 @@ _SIG = {
     "aa_candidates_view": (ctypes.c_int, [_P, ctypes.POINTER(_P), ctypes.POINTER(_I64),
                                           ctypes.POINTER(_I64)]),
     "aa_candidates_destroy": (None, [_P]),
+    "aa_search_fused_ws_bytes": (ctypes.c_int, [_P, _I64, _I32, _I32, ctypes.POINTER(ctypes.c_size_t),
+                                                ctypes.POINTER(ctypes.c_size_t)]),
+    "aa_search_fused_device": (ctypes.c_int, [_P, _P, _I64, _I64, _I32, _F32, _I32, _P, _I64, _P, _P,
+                                              _P, ctypes.c_size_t, _P]),
     "aa_pipeline_create": (ctypes.c_int, [_P, _I64, _I32, _F32, _I64, _I32, ctypes.POINTER(_P)]),
     "aa_pipeline_submit": (ctypes.c_int, [_P, _P, _I64, ctypes.POINTER(_I64)]),
     "aa_pipeline_wait": (ctypes.c_int, [_P, _I64, ctypes.POINTER(_P)]),
@@ -298,6 +302,23 @@ def aa_candidates_view(c) -> tuple:
 
 def aa_candidates_destroy(c) -> None:
     lib().aa_candidates_destroy(c)
+
+
+def aa_search_fused_ws_bytes(plan, nsamp, max_width, stripe_trials=0) -> tuple:
+    b, off = ctypes.c_size_t(), ctypes.c_size_t()
+    check(lib().aa_search_fused_ws_bytes(plan, int(nsamp), int(max_width), int(stripe_trials),
+                                         ctypes.byref(b), ctypes.byref(off)),
+          "aa_search_fused_ws_bytes")
+    return b.value, off.value
+
+
+def aa_search_fused_device(plan, d_in, nsamp, in_pitch, max_width, threshold, stripe_trials,
+                           d_cands, capacity, d_count, d_snr_out, d_ws, ws_bytes, stream) -> int:
+    return check(lib().aa_search_fused_device(plan, d_in, int(nsamp), int(in_pitch), int(max_width),
+                                              float(threshold), int(stripe_trials), d_cands,
+                                              int(capacity), d_count, d_snr_out, d_ws, int(ws_bytes),
+                                              stream),
+                 "aa_search_fused_device")
 
 
 def aa_pipeline_create(plan, nsamp, max_width, threshold, capacity, depth) -> int:

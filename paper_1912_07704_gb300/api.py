@@ -168,6 +168,30 @@ class Plan:
                                  ws.data_ptr(), ws.numel(), _stream_handle(stream))
         return cands, count, snr_out
 
+    def fused_ws_bytes(self, nsamp: int, max_width: int, stripe_trials: int = 0) -> tuple:
+        """(workspace bytes, byte offset of the search workspace inside it) of
+        search_fused_device."""
+        return abi.aa_search_fused_ws_bytes(self.handle, nsamp, max_width, stripe_trials)
+
+    def search_fused_device(self, x: torch.Tensor, nsamp: int, max_width: int, threshold: float,
+                            capacity: int = 1 << 20, stripe_trials: int = 0, snr_out=None,
+                            ws=None, cands=None, count=None, stream=None):
+        """Dedispersion + search in stripes of trials (see aa_search_fused_device):
+        returns (cands, count, ws); the search workspace for sps_order_device is
+        ws[fused_ws_bytes(...)[1]:]."""
+        self.bind()
+        assert x.dtype == torch.uint8 and x.is_cuda and x.dim() == 2 and x.stride(1) == 1
+        nbytes, _ = self.fused_ws_bytes(nsamp, max_width, stripe_trials)
+        ws = self.alloc_workspace(nbytes) if ws is None else ws
+        cands = (torch.empty(max(capacity, 1) * 16, dtype=torch.uint8, device="cuda")
+                 if cands is None else cands)
+        count = torch.zeros(1, dtype=torch.int64, device="cuda") if count is None else count
+        abi.aa_search_fused_device(self.handle, x.data_ptr(), nsamp, x.stride(0), max_width,
+                                   threshold, stripe_trials, cands.data_ptr(), capacity,
+                                   count.data_ptr(), 0 if snr_out is None else snr_out.data_ptr(),
+                                   ws.data_ptr(), ws.numel(), _stream_handle(stream))
+        return cands, count, ws
+
     def postprocess_scratch(self, nsamp: int, max_width: int, capacity: int) -> torch.Tensor:
         """Device scratch for sps_order_device / peaks2d_device."""
         self.bind()

@@ -258,6 +258,28 @@ aa_status candidates_copy_ordered(const aa_candidate* d_sorted, int64_t n, int64
     return AA_OK;
 }
 
+cudaError_t launch_decimation_cascade(const aa_plan& p, const Layout& L, const uint8_t* d_in, int64_t in_pitch,
+                                      char* ws, cudaStream_t s) {
+    for (size_t k = 0; k < p.decs.size(); ++k) {
+        const int dec = p.decs[k];
+        const void* src = d_in;
+        int src_elem = 1, src_dec = 1;
+        int64_t src_pitch = in_pitch;
+        for (size_t j = 0; j < k; ++j)
+            if (dec % p.decs[j] == 0) {  // the largest decimation dividing this one
+                src = ws + L.dec_offset[j];
+                src_elem = 2;
+                src_dec = p.decs[j];
+                src_pitch = L.dec_pitch[j];
+            }
+        ProfScope prof(kKDecimate, s);
+        const cudaError_t e = launch_decimate(src, src_elem, src_pitch, p.nchans, L.nsamp / dec, dec / src_dec,
+                                              reinterpret_cast<uint16_t*>(ws + L.dec_offset[k]), L.dec_pitch[k], s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 }  // namespace aa
 
 // Sub-band strategy of range r: stage 1 per band into the 16-bit partial
@@ -341,24 +363,7 @@ aa_status aa_dedisperse_device(const aa_plan* p, const uint8_t* d_in, int64_t ns
     unsigned* err = static_cast<unsigned*>(d_ws);
     AA_CUDA(cudaMemsetAsync(err, 0, sizeof(unsigned), s), "clear error word");
     char* ws = static_cast<char*>(d_ws);
-    // decimation cascade
-    for (size_t k = 0; k < p->decs.size(); ++k) {
-        const int dec = p->decs[k];
-        const void* src = d_in;
-        int src_elem = 1, src_dec = 1;
-        int64_t src_pitch = in_pitch;
-        for (size_t j = 0; j < k; ++j)
-            if (dec % p->decs[j] == 0) {
-                src = ws + L.dec_offset[j];
-                src_elem = 2;
-                src_dec = p->decs[j];
-                src_pitch = L.dec_pitch[j];
-            }
-        ProfScope prof(kKDecimate, s);
-        AA_CUDA(launch_decimate(src, src_elem, src_pitch, p->nchans, nsamp / dec, dec / src_dec,
-                                reinterpret_cast<uint16_t*>(ws + L.dec_offset[k]), L.dec_pitch[k], s),
-                "decimate launch");
-    }
+    AA_CUDA(launch_decimation_cascade(*p, L, d_in, in_pitch, ws, s), "decimate launch");
     for (size_t r = 0; r < p->ranges.size(); ++r) {
         const RangePlan& g = p->ranges[r];
         DedispArgs a{};

@@ -90,6 +90,25 @@ __device__ __forceinline__ void mbar_inval(uint64_t* bar) {
     asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 
+// Fused statistics of the single-pulse search: the warp's exact sums of one
+// output row's samples (s1 = sum y, s2 = sum y^2 per lane; y < 2^24, at most
+// 16 samples a lane, so every partial fits in 64 bits) are added to the row's
+// accumulators acc = (sum y, sum y^2 low, sum y^2 high); a wrap of the low
+// word is carried into the high one, so the 128-bit total is exact.
+__device__ __forceinline__ void add_row_sums(unsigned long long* acc, unsigned long long s1,
+                                             unsigned long long s2) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+        s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&acc[0], s1);
+        const unsigned long long old = atomicAdd(&acc[1], s2);
+        if (old + s2 < old) atomicAdd(&acc[2], 1ull);
+    }
+}
+
 // One CTA's work item: DM block (bid % ndm_blocks) x time tile (bid / ndm_blocks).
 // `smem` is the dynamic shared memory (layout below); the caller guarantees
 // that every thread of the CTA has finished any previous item.
@@ -344,6 +363,19 @@ __device__ __forceinline__ void dedisperse_block(const DedispArgs& a, int ndm_bl
             continue;
         }
         float* row = a.out + (int64_t)d * a.out_pitch;
+        if (a.st_acc) {
+            unsigned long long s1 = 0, s2 = 0;
+#pragma unroll
+            for (int j = 0; j < QW; ++j)
+#pragma unroll
+                for (int q = 0; q < SPW; ++q)
+                    if (t0 + (int64_t)SPW * (lane + 32 * j) + q < a.length) {
+                        const unsigned long long v = tot[kk][j][q];
+                        s1 += v;
+                        s2 += v * v;
+                    }
+            add_row_sums(a.st_acc + 3 * (int64_t)d, s1, s2);
+        }
 #pragma unroll
         for (int j = 0; j < QW; ++j) {
             const int64_t t = t0 + (int64_t)SPW * (lane + 32 * j);
@@ -429,8 +461,8 @@ __device__ __forceinline__ void dedisperse_grouped_block(const DedispArgs& a, in
     const int nchunks = (C + gcc - 1) / gcc;
     const unsigned char* in_b = static_cast<const unsigned char*>(a.in);
     const int64_t pitch_b = a.in_pitch * EB;
-    const GroupRec* recs = a.grec + (size_t)dmb * nchunks;
-    const GroupMember* mems = a.gmem + (size_t)dmb * nchunks * gcc;
+    const GroupRec* recs = a.grec + (size_t)(a.dmb0 + dmb) * nchunks;
+    const GroupMember* mems = a.gmem + (size_t)(a.dmb0 + dmb) * nchunks * gcc;
     // tail units: gtl lanes per group (a power of two), gpt groups per warp
     const int gtl = a.gtl, gtl_log = gtl ? __ffs(gtl) - 1 : 0, gpt = gtl ? 32 / gtl : 1;
     // A lane of a main unit reads below byte EB * (nsamp + 256 gnj) + 31 of its
@@ -627,8 +659,19 @@ __device__ __forceinline__ void dedisperse_grouped_block(const DedispArgs& a, in
         tot[2 * q + 1] += acc[q] >> 16;
     }
 
-    // epilogue: exact integer totals -> FP32 rows
+    // epilogue: exact integer totals -> FP32 rows (and the fused statistics)
     if (!has_trial) return;
+    if (a.st_acc) {
+        unsigned long long s1 = 0, s2 = 0;
+#pragma unroll
+        for (int q = 0; q < 2 * QW; ++q)
+            if (t0 + 2 * (lane + 32 * (q >> 1)) + (q & 1) < a.length) {
+                const unsigned long long v = tot[q];
+                s1 += v;
+                s2 += v * v;
+            }
+        add_row_sums(a.st_acc + 3 * (int64_t)(d0 + warp), s1, s2);
+    }
     float* row = a.out + (int64_t)(d0 + warp) * a.out_pitch;
 #pragma unroll
     for (int q = 0; q < QW; ++q) {

@@ -217,7 +217,7 @@ constexpr int64_t kEvaluatedOffset = 16;     // evaluated width-samples counter
 // ------------------------------------------------------------- profiling --
 enum KernelId {
     kKDecimate = 0, kKDedispU8, kKDedispU16, kKRsqrt, kKStats, kKBoxcar, kKF32Fwd, kKF32Adj,
-    kKCornerTurn, kKOrder, kKPeaks2d, kKSubband1, kKSubband2, kNumKernels
+    kKCornerTurn, kKOrder, kKPeaks2d, kKSubband1, kKSubband2, kKFinalize, kNumKernels
 };
 
 // RAII: records CUDA events around a launch on `s` while profiling is on.
@@ -257,6 +257,13 @@ struct DedispArgs {
     const GroupRec* grec;
     const GroupDesc* gdesc;
     const GroupMember* gmem;
+    // launches over a stripe of the range's trials: the stripe's first DM
+    // block in the range's group tables (out, shifts and ndm already describe
+    // the stripe)
+    int32_t dmb0;
+    // fused statistics (non-NULL): each output row r adds its exact sums to
+    // st_acc[3 r .. 3 r + 2] = (sum y, sum y^2 low 64 bits, high 64 bits)
+    unsigned long long* st_acc;
 };
 // Strategy fields of a range's kernel arguments.
 void fill_strategy(DedispArgs& a, const RangePlan& r);
@@ -265,6 +272,10 @@ cudaError_t launch_dedisperse(const DedispArgs& a, cudaStream_t s);
 cudaError_t launch_decimate(const void* in, int in_elem, int64_t in_pitch, int32_t nchans,
                             int64_t nout, int factor, uint16_t* out, int64_t out_pitch,
                             cudaStream_t s);
+// Every decimated input of the plan into the dedispersion workspace `ws`
+// (layout L), each built from the largest decimation dividing it.
+cudaError_t launch_decimation_cascade(const aa_plan& p, const Layout& L, const uint8_t* d_in, int64_t in_pitch,
+                                      char* ws, cudaStream_t s);
 
 // ----------------------------------------------------- batched (persistent) --
 struct DecimateJob {
@@ -314,6 +325,9 @@ struct SpsArgs {
     int64_t chunk_cap;
 };
 cudaError_t launch_sps_stats(const SpsArgs& a, cudaStream_t s);
+// mu, sigma and width tables of a.nrows rows from the sums the dedispersion
+// kernels accumulated (DedispArgs::st_acc; 3 words per row)
+cudaError_t launch_sps_finalize(const SpsArgs& a, const unsigned long long* acc, cudaStream_t s);
 cudaError_t launch_sps_boxcar(const SpsArgs& a, cudaStream_t s);
 cudaError_t launch_sps_stats_batch(const SpsArgs* d_descs, const int64_t* d_first, int ndesc,
                                    unsigned long long* d_queue, int grid, cudaStream_t s);

@@ -107,6 +107,48 @@ __device__ __forceinline__ void stats_accumulate(float yf, bool clip, float lo, 
     s2 += (long long)v * v;
 }
 
+// Statistics of a series from the exact sums of its N samples, S1 = sum y
+// and S2 = H:Lo = sum y^2 (128 bits); f receives mu - m0.
+__device__ RowStats row_stats_from_sums(long long N, long long S1, unsigned long long H, unsigned long long Lo,
+                                        double& f) {
+    RowStats st{};
+    if (N > 0) {
+        // N^2 var = N * sum y^2 - (sum y)^2, exact in 128 bits
+        const unsigned __int128 S2 = ((unsigned __int128)H << 64) | Lo;
+        const __int128 num = (__int128)N * (__int128)S2 - (__int128)S1 * (__int128)S1;
+        const unsigned __int128 un = num > 0 ? (unsigned __int128)num : 0;
+        const double numd = (double)(unsigned long long)(un >> 64) * 18446744073709551616.0 +
+                            (double)(unsigned long long)un;
+        st.mu = (double)S1 / (double)N;
+        st.sigma = sqrt(numd) / (double)N;
+        const long long m0 = llround(st.mu);
+        st.m0 = (float)m0;
+        st.inv_sigma = st.sigma > 0 ? 1.0 / st.sigma : 0.0;
+        st.zero_sigma = st.sigma > 0 ? 0 : 1;
+        f = (double)(S1 - m0 * N) / (double)N;  // mu - m0
+    } else {
+        st.zero_sigma = 1;
+        f = 0.0;
+    }
+    return st;
+}
+
+// Width table of one row, whole CTA: r_w = 1/(sigma sqrt w), c_w = w f r_w
+// (FP64, stored FP32 as (r_w, -c_w)); widths past max_width never win.
+__device__ void write_width_table(const SpsArgs& a, const double* rsw, int row, double f, double inv) {
+    float2* tab = a.table + (int64_t)row * a.wpad;
+    for (int i = threadIdx.x; i < a.wpad; i += blockDim.x) {
+        const int w = i + 1;
+        if (w <= a.max_width) {
+            const double r = inv * rsw[i];
+            const double c = (double)w * f * r;
+            tab[i] = make_float2((float)r, (float)(-c));
+        } else {
+            tab[i] = make_float2(0.0f, -FLT_MAX);
+        }
+    }
+}
+
 __device__ __forceinline__ void stats_row(const SpsArgs& a, const double* rsw, int row) {
     constexpr int NW = kStatsThreads / 32;
     constexpr int64_t kFlush = 4096;  // float4 steps per 128-bit flush: 2^14 samples, s2 < 2^14 * 2^48
@@ -195,42 +237,30 @@ __device__ __forceinline__ void stats_row(const SpsArgs& a, const double* rsw, i
         if (!sh_go) break;
     }
     if (threadIdx.x == 0) {
-        const long long N = sh_N, S1 = sh_S1;
-        RowStats st{};
-        if (N > 0) {
-            // N^2 var = N * sum y^2 - (sum y)^2, exact in 128 bits
-            const unsigned __int128 S2 = ((unsigned __int128)sh_H << 64) | sh_L;
-            const __int128 num = (__int128)N * (__int128)S2 - (__int128)S1 * (__int128)S1;
-            const unsigned __int128 un = num > 0 ? (unsigned __int128)num : 0;
-            const double numd = (double)(unsigned long long)(un >> 64) * 18446744073709551616.0 +
-                                (double)(unsigned long long)un;
-            st.mu = (double)S1 / (double)N;
-            st.sigma = sqrt(numd) / (double)N;
-            const long long m0 = llround(st.mu);
-            st.m0 = (float)m0;
-            st.inv_sigma = st.sigma > 0 ? 1.0 / st.sigma : 0.0;
-            st.zero_sigma = st.sigma > 0 ? 0 : 1;
-            sh_f = (double)(S1 - m0 * N) / (double)N;  // mu - m0
-        } else {
-            st.zero_sigma = 1;
-            sh_f = 0.0;
-        }
+        const RowStats st = row_stats_from_sums(sh_N, sh_S1, sh_H, sh_L, sh_f);
         sh_inv = st.inv_sigma;
         a.stats[row] = st;
     }
     __syncthreads();
-    const double f = sh_f, inv = sh_inv;
-    float2* tab = a.table + (int64_t)row * a.wpad;
-    for (int i = threadIdx.x; i < a.wpad; i += kStatsThreads) {
-        const int w = i + 1;
-        if (w <= a.max_width) {
-            const double r = inv * rsw[i];
-            const double c = (double)w * f * r;
-            tab[i] = make_float2((float)r, (float)(-c));
-        } else {
-            tab[i] = make_float2(0.0f, -FLT_MAX);
-        }
+    write_width_table(a, rsw, row, sh_f, sh_inv);
+}
+
+// Fused statistics (the dedispersion kernels summed each row exactly into
+// acc[3 r .. 3 r + 2] = (sum y, sum y^2 low, high)): mu, sigma and the width
+// table of every row of a range, with the arithmetic of stats_row's plain
+// pass (bit for bit the same results).  One CTA per row.
+__global__ void __launch_bounds__(256) sps_finalize_kernel(SpsArgs a, const double* rsw,
+                                                          const unsigned long long* acc) {
+    __shared__ double sh_f, sh_inv;
+    const int row = blockIdx.x;
+    if (threadIdx.x == 0) {
+        const unsigned long long* r = acc + 3 * (int64_t)row;
+        const RowStats st = row_stats_from_sums(a.length, (long long)r[0], r[2], r[1], sh_f);
+        sh_inv = st.inv_sigma;
+        a.stats[row] = st;
     }
+    __syncthreads();
+    write_width_table(a, rsw, row, sh_f, sh_inv);
 }
 
 __global__ void __launch_bounds__(kStatsThreads) sps_stats_kernel(SpsArgs a, const double* rsw) {
@@ -740,6 +770,12 @@ __global__ void __launch_bounds__(NT, 2) sps_boxcar_batch_kernel(
 cudaError_t launch_sps_stats(const SpsArgs& a, cudaStream_t s) {
     if (a.nrows <= 0) return cudaSuccess;
     sps_stats_kernel<<<a.nrows, kStatsThreads, 0, s>>>(a, a.rsqrt_w);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sps_finalize(const SpsArgs& a, const unsigned long long* acc, cudaStream_t s) {
+    if (a.nrows <= 0) return cudaSuccess;
+    sps_finalize_kernel<<<a.nrows, 256, 0, s>>>(a, a.rsqrt_w, acc);
     return cudaGetLastError();
 }
 

@@ -92,3 +92,27 @@ def test_set_strategy_argument_checks():
         p.set_strategy(0, 7)
     with pytest.raises(abi.AAError, match="AA_ERR_ARG"):
         abi.aa_plan_set_strategy(None, 0, 0)
+
+
+def test_fused_workspace_replaces_the_series():
+    """The fused search's workspace holds one stripe of series instead of
+    the whole plan's, and one decimated input instead of all of them: on the
+    4096-channel plan (series 9.18 GB, decimated inputs 7.5 GB) 256-trial
+    stripes need 1.07 GB of series and 4.29 GB of decimated input (dec 2);
+    stripe sizes are checked."""
+    from paper_1912_07704_gb300 import synth
+    w = synth.SKA_4096
+    p = Plan.from_workload(w)
+    info = p.query(w.nsamp, w.max_width)
+    unfused = info.dd_elems * 4 + info.dedisp_ws_bytes + info.sps_ws_bytes
+    fused, off = abi.aa_search_fused_ws_bytes(p.handle, w.nsamp, w.max_width, 256)
+    lay = p.layout(w.nsamp)
+    stripe_bytes = 256 * max(g.pitch for g in lay) * 4
+    dec2 = w.nchans * 524288 * 2  # the largest decimated input
+    expect = dec2 + info.sps_ws_bytes + stripe_bytes
+    assert abs(fused - expect) < 1 << 20, (fused, expect)
+    assert off >= dec2
+    assert fused < 0.35 * unfused
+    with pytest.raises(abi.AAError):
+        abi.aa_search_fused_ws_bytes(p.handle, w.nsamp, w.max_width, 24)  # not a multiple of 16
+    p.close()
