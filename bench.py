@@ -150,7 +150,10 @@ def build_input(plan, w, device):
 # the series length).  Each entry names the capture it comes from; set it to None
 # when the kernel changes until it is captured again.
 NCU_TRAFFIC = {
-    ("dedisperse_u8", "grouped"): None,  # kernel changed since its capture
+    ("dedisperse_u8", "grouped"): {
+        "small_read_bytes": 543_437_824, "small_write_bytes": 740_257_536,
+        "small_output_samples": 1500 * 128687,
+        "capture": "profiles/dedisperse_grouped_u8_ska-4096ch-2^17.md"},
     ("sps_boxcar", "pruned"): {
         "small_read_bytes": 875_240_960, "small_write_bytes": 44_166_400,
         "small_output_samples": 1500 * 128687,

@@ -101,6 +101,51 @@ void oracle_subband_rel(int32_t nchans, double fch1, double foff, double tsamp, 
     }
 }
 
+/* FDMT-style tree dedispersion (an approximation of the brute-force sum:
+ * delays are split between subbands, not computed per channel).  Channels
+ * are taken in order of delta_c = f_c^-2 - f_top^-2 (falling frequency);
+ * dk[k] is the k-th smallest.  A subband [a, b] of that order with delay
+ * delta (of its channel b relative to its channel a) is split at
+ * m = a + ceil((b - a + 1) / 2) into [a, m-1] with delay
+ *   round_half_away(delta * (dk[m-1] - dk[a]) / (dk[b] - dk[a]))
+ * and [m, b] starting gap = round_half_away(delta * (dk[m] - dk[a]) /
+ * (dk[b] - dk[a])) later, with delay delta - gap; a single channel has
+ * delay 0.  e[k] receives the delay of the k-th channel for the whole band's
+ * delay delta at offset base. */
+static void fdmt_split(const double* dk, int32_t a, int32_t b, int64_t delta, int64_t base, int64_t* e)
+{
+    if (a == b) {
+        e[a] = base;
+        return;
+    }
+    const int32_t m = a + (b - a + 2) / 2;
+    const double span = dk[b] - dk[a];
+    const int64_t gap = span > 0.0 ? llround((double)delta * (dk[m] - dk[a]) / span) : 0;
+    const int64_t du = span > 0.0 ? llround((double)delta * (dk[m - 1] - dk[a]) / span) : 0;
+    fdmt_split(dk, a, m - 1, du, base, e);
+    fdmt_split(dk, m, b, delta - gap, base + gap, e);
+}
+
+/* Effective delay of every channel (channel order, out[c]) when the whole
+ * band's delay -- its lowest-frequency channel relative to its highest -- is
+ * D samples. */
+void oracle_fdmt_delays(int32_t nchans, double fch1, double foff, int64_t D, int32_t* out)
+{
+    double ft = oracle_f_top(fch1, foff, nchans);
+    double* dk = (double*)malloc(sizeof(double) * (size_t)nchans);
+    int64_t* e = (int64_t*)malloc(sizeof(int64_t) * (size_t)nchans);
+    if (!dk || !e) { free(dk); free(e); return; }
+    for (int32_t k = 0; k < nchans; ++k) {
+        const int32_t c = foff < 0 ? k : nchans - 1 - k;  /* k-th highest frequency */
+        const double fc = fch1 + (double)c * foff;
+        dk[k] = 1.0 / (fc * fc) - 1.0 / (ft * ft);
+    }
+    fdmt_split(dk, 0, nchans - 1, D, 0, e);
+    for (int32_t k = 0; k < nchans; ++k) out[foff < 0 ? k : nchans - 1 - k] = (int32_t)e[k];
+    free(dk);
+    free(e);
+}
+
 /* Time decimation by summation; the trailing partial bin is dropped. */
 void oracle_decimate(const uint8_t* x, int32_t nchans, int64_t nsamp, int64_t pitch,
                      int32_t dec, uint16_t* out, int64_t out_pitch)

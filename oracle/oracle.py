@@ -70,6 +70,8 @@ def lib():
         L.oracle_moments.restype = None
         L.oracle_subband_rel.argtypes = [i32, f64, f64, f64, f64, i32, i32, vp]
         L.oracle_subband_rel.restype = None
+        L.oracle_fdmt_delays.argtypes = [i32, f64, f64, i64, vp]
+        L.oracle_fdmt_delays.restype = None
         L.oracle_moments_clipped.argtypes = [vp, i64, i32, i32, ctypes.POINTER(f64),
                                              ctypes.POINTER(f64), ctypes.POINTER(i64)]
         L.oracle_moments_clipped.restype = None
@@ -358,6 +360,44 @@ def dedisperse_subband(x, nchans, fch1, foff, tsamp, rng: OracleRange, band, coa
         if L:
             out[i] = dedisperse_row(xr, eff[i].astype(np.int32), 0, L)
     return out, eff, rmax, s2max
+
+
+# ----------------------------------------------------------------------------
+# FDMT-style tree dedispersion (approximate; exact integer sums of the
+# delays the tree's splits give)
+# ----------------------------------------------------------------------------
+
+def fdmt_delays(nchans, fch1, foff, D) -> np.ndarray:
+    """Per-channel delays of the tree for a whole-band delay of D samples."""
+    out = np.empty(nchans, dtype=np.int32)
+    lib().oracle_fdmt_delays(int(nchans), float(fch1), float(foff), int(D), _ptr(out))
+    return out
+
+
+def fdmt_bottom(nchans, foff) -> int:
+    """The lowest-frequency channel (the one whose delay is the band's)."""
+    return nchans - 1 if foff < 0 else 0
+
+
+def fdmt_table(nchans, fch1, foff, rng: OracleRange) -> np.ndarray:
+    """Delay table [ndm][nchans] of the tree form of a range: trial i takes
+    the whole-band delay D_i = s(bottom channel, i) of the brute-force plan."""
+    b = fdmt_bottom(nchans, foff)
+    if rng.ndm == 0:
+        return np.zeros((0, nchans), np.int32)
+    return np.stack([fdmt_delays(nchans, fch1, foff, int(rng.shifts[i][b])) for i in range(rng.ndm)])
+
+
+def dedisperse_fdmt(x, nchans, fch1, foff, tsamp, rng: OracleRange):
+    """y[i][t] = sum_c xr[c][t + e_i(c)], t < L (the brute-force length:
+    the bottom channel keeps its brute-force delay)."""
+    tab = fdmt_table(nchans, fch1, foff, rng)
+    xr = range_input(x, rng.dec)
+    out = np.zeros((rng.ndm, rng.length), dtype=np.int64)
+    for i in range(rng.ndm):
+        if rng.length:
+            out[i] = dedisperse_row(xr, tab[i], 0, rng.length)
+    return out, tab
 
 
 # ----------------------------------------------------------------------------

@@ -97,6 +97,32 @@ cudaError_t launch_subband_stage2(const uint16_t* z, int64_t band_stride, int64_
                                   int ncoarse, int m, int ndm, const int32_t* s2, int span, float* out,
                                   int64_t out_pitch, int64_t length, cudaStream_t s);
 
+// FDMT-style tree dedispersion of a range (AA_DEDISP_FDMT, an approximation):
+// the channels in falling-frequency order form a binary tree of subbands
+// (subband [a, b] split at a + ceil((b - a + 1) / 2)); a subband's sum at
+// delay delta (of its last channel relative to its first) adds its upper
+// half's sum at delay du(delta) and its lower half's at delta - gap(delta),
+// read gap(delta) samples later.  Depths are computed deepest first into
+// 32-bit rows; the root's rows are the range's trials (the whole-band delay
+// of trial i is the bottom channel's brute-force delay), written as FP32.
+struct FdmtRow {
+    int32_t u, l;   // rows of the next-deeper depth (>= 0) or channel -(ref + 1) (< 0)
+    int32_t gap;    // the lower half is read at t + gap
+    int32_t delta;  // this row's delay: valid for t < nsamp_dec - delta
+};
+static_assert(sizeof(FdmtRow) == 16, "FDMT row layout");
+struct FdmtPlan {
+    int depths = 0;               // merge levels (the root is depth 0)
+    std::vector<FdmtRow> rows;    // deepest depth first, the root's (one per trial) last
+    std::vector<int64_t> first;   // [depths + 1]: start of each depth's rows in that order
+    int32_t max_rows = 0;         // rows of the largest intermediate depth
+    double work = 1.0;            // rows computed / (ndm x nchans): adds relative to direct
+    FdmtRow* d_rows = nullptr;
+};
+cudaError_t launch_fdmt_depth(const FdmtRow* rows, int nrows, int leaf_elem, const void* leaves,
+                              int64_t leaf_pitch, const uint32_t* prev, uint32_t* out, int64_t pitch,
+                              int64_t nsamp, float* fout, int64_t fpitch, int64_t flen, cudaStream_t s);
+
 // Per-range strategy, derived once at plan creation (immutable afterwards).
 struct RangePlan {
     aa_dm_range desc{};
@@ -133,6 +159,7 @@ struct RangePlan {
     GroupDesc* d_gdesc = nullptr;
     GroupMember* d_gmem = nullptr;
     SubbandPlan sb;        // valid once aa_plan_set_subband chose it (strategy 2)
+    FdmtPlan fd;           // valid once aa_plan_set_fdmt chose it (strategy 3)
 };
 
 }  // namespace aa
@@ -153,7 +180,7 @@ struct aa_plan {
     bool ready = false;
     void* d_tables = nullptr;
     size_t table_bytes = 0;
-    void* d_sub = nullptr;  // sub-band delay tables of every range using them
+    void* d_sub = nullptr;  // sub-band and FDMT tables of every range using them
 };
 
 namespace aa {
@@ -171,6 +198,9 @@ struct Layout {
     // sub-band ranges: 16-bit partial series [nsub][ncoarse][sub_pitch] (bytes
     // into the workspace; -1 for other ranges) and their length
     std::vector<int64_t> sub_offset, sub_pitch, sub_len;
+    // FDMT ranges: two 32-bit depth buffers of fdmt_rows rows at pitch
+    // fdmt_pitch (bytes into the workspace; -1 when no range uses FDMT)
+    int64_t fdmt_offset = -1, fdmt_pitch = 0, fdmt_rows = 0;
     int64_t dedisp_ws = 0;
     // single-pulse workspace: [error word + chunk counter][1/sqrt(w)][row stats]
     //                         [width tables][candidate chunk headers]
@@ -217,7 +247,7 @@ constexpr int64_t kEvaluatedOffset = 16;     // evaluated width-samples counter
 // ------------------------------------------------------------- profiling --
 enum KernelId {
     kKDecimate = 0, kKDedispU8, kKDedispU16, kKRsqrt, kKStats, kKBoxcar, kKF32Fwd, kKF32Adj,
-    kKCornerTurn, kKOrder, kKPeaks2d, kKSubband1, kKSubband2, kKFinalize, kNumKernels
+    kKCornerTurn, kKOrder, kKPeaks2d, kKSubband1, kKSubband2, kKFinalize, kKFdmt, kNumKernels
 };
 
 // RAII: records CUDA events around a launch on `s` while profiling is on.

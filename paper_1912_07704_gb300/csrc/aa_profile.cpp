@@ -11,7 +11,7 @@ namespace aa {
 static const char* kKernelNames[kNumKernels] = {
     "decimate", "dedisperse_u8", "dedisperse_u16", "sps_rsqrt_table",
     "sps_stats", "sps_boxcar", "f32_forward", "f32_adjoint", "corner_turn", "sps_order", "peaks2d", "dedisperse_subband_stage1",
-    "dedisperse_subband_stage2", "sps_finalize"};
+    "dedisperse_subband_stage2", "sps_finalize", "dedisperse_fdmt"};
 
 namespace {
 struct Pending {
