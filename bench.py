@@ -208,7 +208,7 @@ def strided_rows(ndm: int, count: int, k: int = 0) -> list:
 
 
 def run_oracle_sample(w, x_host, rows_per_range: int, threads: int, subband: bool = False,
-                      k: int = 0):
+                      k: int = 0, fdmt: bool = False):
     """Oracle (CPU) on a bounded sample: `rows_per_range` full-length DM trials
     of every range, strided over the range (see strided_rows; k selects the
     trial of a one-trial sample), decimated inputs prepared outside the timed
@@ -224,6 +224,9 @@ def run_oracle_sample(w, x_host, rows_per_range: int, threads: int, subband: boo
                                                 subband_bands(g.dec), SUBBAND_COARSE)
             g.shifts = eff.astype(np.int32)
             g.length = max(0, g.nsamp_dec - (rmax + s2max))
+    if fdmt:  # effective delays of the tree form (same lengths)
+        for g in pl:
+            g.shifts = o.fdmt_table(w.nchans, w.fch1, w.foff, g)
     t_dec = 0.0
     inputs = []
     for g in pl:
@@ -245,7 +248,8 @@ def run_oracle_sample(w, x_host, rows_per_range: int, threads: int, subband: boo
            "a different trial per step, striding over each range")
     desc = (f"{rows_per_range} full-length DM trial(s) per range ({nrows} of {ntrials}; {how}), "
             f"time extrapolated to all trials by output samples, decimation time amortised "
-            f"over all trials" + (", sub-band form" if subband else ""))
+            f"over all trials" + (", sub-band form" if subband else "")
+            + (", FDMT tree form" if fdmt else ""))
     return samples, secs, cores, desc
 
 
@@ -280,6 +284,9 @@ def bench_reference(args):
 
 
 def _strategy_name(info) -> str:
+    if info.strategy == 3:
+        return (f"FDMT tree ({info.fdmt_depths} depths, largest {info.fdmt_max_rows} rows, "
+                f"{info.fdmt_work:.4f} of the direct adds)")
     if info.strategy == 2:
         return (f"subband (bands of {info.subband_channels} ch, coarse trials of "
                 f"{info.subband_coarse_trials}, {info.subband_work:.3f} of the direct adds, "
@@ -304,6 +311,9 @@ def bench_ours(args):
         # coarse trials of 16 fine trials
         for r, rg in enumerate(w.ranges):
             plan.set_subband(r, subband_bands(rg[3]), SUBBAND_COARSE)
+    elif args.strategy == "fdmt":
+        for r in range(len(w.ranges)):
+            plan.set_fdmt(r)
     elif args.strategy != "auto":
         for r in range(len(w.ranges)):
             plan.set_strategy(r, abi.AA_DEDISP_GROUPED if args.strategy == "grouped"
@@ -459,7 +469,26 @@ def bench_ours(args):
         per_launch = (ent["small_read_bytes"] + ent["small_write_bytes"]) * scale / len(rows)
         return per_launch, f"ncu capture {ent['capture']}, scaled x{scale:.2f} by output samples"
 
-    if dominant == "sps_boxcar":
+    if dominant == "dedisperse_fdmt":
+        # HBM-bound gather-adds: every row of every tree depth reads two rows
+        # and writes one (32-bit; leaves are 8/16-bit input rows, counted as 4
+        # bytes: an upper estimate); rows = fdmt_work x ndm x nchans per range
+        fd_s = kern[dominant]["ms_per_step"] / 1e3
+        nbytes = 0.0
+        for r, g in enumerate(alg["lay"]):
+            info = abi.aa_plan_range(plan.handle, nsamp, r)
+            if info.strategy == 3:
+                nbytes += info.fdmt_work * g.ndm * w.nchans * g.nsamp_dec * 12
+        nl = kern[dominant]["launches"] / max(args.steps, 1)
+        achieved = nbytes / fd_s
+        hbm_peak = float(peaks.get("hbm_gbs", 6678.2)) * 1e9
+        roof = {"kernel": dominant, "bound": "hbm", "achieved": achieved / 1e9, "peak": hbm_peak / 1e9,
+                "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": None,
+                "traffic_source": "no capture of the tree kernels",
+                "algorithmic_bytes_per_launch": nbytes / max(nl, 1),
+                "ops": "per tree row: two rows read and one written, 4 bytes a sample "
+                       "(rows = fdmt_work x ndm x nchans); peak = measured HBM copy bandwidth"}
+    elif dominant == "sps_boxcar":
         achieved = BOXCAR_OPS_PER_WS * evaluated / box_s
         tb, tnote = traffic("sps_boxcar")
         roof = {"kernel": "sps_boxcar", "bound": "alu", "sm_count": sm_count, "achieved": achieved / 1e9,
@@ -492,13 +521,16 @@ def bench_ours(args):
     if not args.no_cpu_baseline and rank == 0 and ws == 1:
         xh = x[:, :nsamp].cpu().numpy()
         s, secs, cores, desc = run_oracle_sample(w, xh, 3, os.cpu_count() or 1,
-                                                 subband=args.strategy == "subband")
+                                                 subband=args.strategy == "subband",
+                                                 fdmt=args.strategy == "fdmt")
         cpu = {"value": s / secs, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
 
     if rank == 0:
         line = {
-            "metric": (METRIC if args.strategy != "subband" else
-                       METRIC.replace("dedispersion", "sub-band dedispersion (approximate)")),
+            "metric": (METRIC.replace("dedispersion", "sub-band dedispersion (approximate)")
+                       if args.strategy == "subband" else
+                       METRIC.replace("dedispersion", "FDMT tree dedispersion (approximate)")
+                       if args.strategy == "fdmt" else METRIC),
             "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * step_s, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u8->int32 (dedispersion), f32 (SNR)",
@@ -831,9 +863,11 @@ def main():
                                            "cornerturn", "postprocess"],
                     default="ska")
     ap.add_argument("--stream-chunks", type=int, default=6)
-    ap.add_argument("--strategy", choices=["auto", "direct", "grouped", "subband"], default="auto",
+    ap.add_argument("--strategy", choices=["auto", "direct", "grouped", "subband", "fdmt"],
+                    default="auto",
                     help="dedispersion strategy of every range (auto: the plan's choice; "
-                         "subband: the approximate two-stage sum, a different metric)")
+                         "subband / fdmt: the approximate two-stage / tree sums, a different "
+                         "metric)")
     ap.add_argument("--sps-clip", default="",
                     help="C16,ITERS: k-sigma clipped statistics (k = C16/16), e.g. 48,4")
     ap.add_argument("--sps-ladder", type=int, default=0,

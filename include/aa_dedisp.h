@@ -145,6 +145,9 @@ typedef struct aa_range_info {
     int32_t subband_channels;       /* AA_DEDISP_SUBBAND: channels per band (else 0) */
     int32_t subband_coarse_trials;  /* AA_DEDISP_SUBBAND: fine trials per coarse trial */
     double subband_work;     /* adds of the sub-band strategy / adds of the direct one */
+    int32_t fdmt_depths;     /* AA_DEDISP_FDMT: merge levels of the channel tree (else 0) */
+    int32_t fdmt_max_rows;   /* AA_DEDISP_FDMT: rows of its largest intermediate level */
+    double fdmt_work;        /* adds of the FDMT strategy / adds of the direct one */
 } aa_range_info;
 
 /* Strategy and memory requests for `nsamp` samples and boxcar widths up to
@@ -175,6 +178,14 @@ aa_status aa_plan_query(const aa_plan* plan, int64_t nsamp, int32_t max_width,
 
 /* Layout of range r (0 <= r < nranges) for `nsamp` samples. */
 aa_status aa_plan_range(const aa_plan* plan, int64_t nsamp, int32_t r, aa_range_info* info);
+
+/* Effective delay table [ndm][nchans] (decimated samples) of range r under
+ * the strategy in use: the brute-force delays for the direct and grouped
+ * strategies (= aa_plan_shifts), the band reference's delay plus the
+ * channel's delay within its band for sub-band ranges, the delays the tree's
+ * splits give for FDMT ranges.  Host only.  AA_ERR_ARG for a bad range, NULL
+ * out or cap < ndm x nchans. */
+aa_status aa_plan_effective_shifts(const aa_plan* plan, int32_t r, int32_t* out, int64_t cap);
 
 /* Copy range r's delay table, int32 [ndm][nchans] row-major (decimated
  * samples), into caller-owned host memory `out` (capacity `cap` elements). */
@@ -249,7 +260,8 @@ aa_status aa_workspace_status(void* d_ws, aa_stream_t stream);
  *     channels whose delays differ from the block's first trial by the same
  *     amounts at every trial are first summed once; each trial then adds the
  *     group sums.  Available when the plan could build the group tables. */
-typedef enum { AA_DEDISP_DIRECT = 0, AA_DEDISP_GROUPED = 1, AA_DEDISP_SUBBAND = 2 } aa_dedisp_strategy;
+typedef enum { AA_DEDISP_DIRECT = 0, AA_DEDISP_GROUPED = 1, AA_DEDISP_SUBBAND = 2,
+               AA_DEDISP_FDMT = 3 } aa_dedisp_strategy;
 
 /* Sub-band dedispersion of range r (AA_DEDISP_SUBBAND): an approximation of
  * the brute-force sum with fewer adds, the cheaper-than-brute-force family
@@ -276,6 +288,27 @@ typedef enum { AA_DEDISP_DIRECT = 0, AA_DEDISP_GROUPED = 1, AA_DEDISP_SUBBAND = 
  * aa_plan_set_strategy, call it while no work of the plan is in flight. */
 aa_status aa_plan_set_subband(aa_plan* plan, int32_t r, int32_t band_channels,
                               int32_t coarse_trials);
+
+/* FDMT-style tree dedispersion of range r (AA_DEDISP_FDMT): an
+ * approximation of the brute-force sum (the dedispersion module's cited
+ * work, Sec. 1) whose adds per output sample grow with log2(nchans) and the
+ * range's delay span instead of nchans x ndm: the channels, in
+ * falling-frequency order, form a binary tree of subbands (subband [a, b]
+ * split at a + ceil((b - a + 1) / 2)); a subband's series at delay delta
+ * (its last channel relative to its first) is its upper half's series at
+ * delay round(delta (d[m-1] - d[a]) / (d[b] - d[a])) plus its lower half's
+ * at delay delta - gap, read gap = round(delta (d[m] - d[a]) / (d[b] - d[a]))
+ * samples later (d = f^-2 - f_top^-2, rounding half away from zero, FP64);
+ * a single channel has delay 0.  Trial i of the range takes the whole band at
+ * delay D_i = its bottom channel's brute-force delay, so the output length
+ * is the brute-force one; every other channel's effective delay stays within
+ * a closed-form bound of its brute-force delay (about log2(nchans) / 2 + log2(nchans)^2 / 4
+ * samples).  Sums are exact integers (32-bit intermediate rows, FP32 output).
+ * The workspace grows by two depth buffers (aa_plan_query dedisp_ws_bytes;
+ * aa_range_info fdmt_max_rows rows each).  Not available in batched runs.
+ * AA_ERR_ARG for a bad range, AA_ERR_CONFIG if sums could exceed 31 bits,
+ * AA_ERR_NOMEM if a bound plan cannot upload the tree. */
+aa_status aa_plan_set_fdmt(aa_plan* plan, int32_t r);
 
 /* Select the strategy of range r (aa_plan_create picks one from the number
  * of adds each needs).  AA_ERR_ARG for a bad range or strategy value,
@@ -531,7 +564,7 @@ void aa_candidates_destroy(aa_candidates* c);
  * aa_search_fused_device: d_in as in aa_dedisperse_device; candidates as in
  * aa_sps_search_device; d_ws 256-byte aligned, >= the bytes above.  Its
  * first word is the error word (aa_workspace_status).  Stream-ordered.
- * AA_ERR_CONFIG for plans with sub-band ranges; AA_ERR_ARG on bad
+ * AA_ERR_CONFIG for plans with sub-band or FDMT ranges; AA_ERR_ARG on bad
  * arguments. */
 aa_status aa_search_fused_ws_bytes(const aa_plan* plan, int64_t nsamp, int32_t max_width,
                                    int32_t stripe_trials, size_t* bytes, size_t* sps_ws_offset);

@@ -48,7 +48,8 @@ class aa_range_info(ctypes.Structure):
                 ("smem_bytes", ctypes.c_int32), ("strategy", ctypes.c_int32),
                 ("grouped_available", ctypes.c_int32), ("grouped_work", ctypes.c_double),
                 ("subband_channels", ctypes.c_int32), ("subband_coarse_trials", ctypes.c_int32),
-                ("subband_work", ctypes.c_double)]
+                ("subband_work", ctypes.c_double), ("fdmt_depths", ctypes.c_int32),
+                ("fdmt_max_rows", ctypes.c_int32), ("fdmt_work", ctypes.c_double)]
 
 
 class aa_plan_info(ctypes.Structure):
@@ -133,6 +134,8 @@ _SIG = {
     "aa_corner_turn_device": (ctypes.c_int, [_P, _I64, _I32, _I64, _P, _I64, _P]),
     "aa_plan_set_sps_clip": (ctypes.c_int, [_P, _I32, _I32]),
     "aa_plan_set_subband": (ctypes.c_int, [_P, _I32, _I32, _I32]),
+    "aa_plan_set_fdmt": (ctypes.c_int, [_P, _I32]),
+    "aa_plan_effective_shifts": (ctypes.c_int, [_P, _I32, _P, _I64]),
     "aa_plan_set_sps_ladder": (ctypes.c_int, [_P, _I32]),
     "aa_postprocess_ws_bytes": (ctypes.c_int, [_P, _I64, _I32, _I64,
                                                ctypes.POINTER(ctypes.c_size_t)]),
@@ -372,6 +375,18 @@ def aa_plan_set_sps_ladder(plan, growth_x16: int) -> None:
     check(lib().aa_plan_set_sps_ladder(plan, int(growth_x16)), "aa_plan_set_sps_ladder")
 
 
+def aa_plan_effective_shifts(plan, r: int, ndm: int, nchans: int):
+    import numpy as np
+    out = np.empty((ndm, nchans), dtype=np.int32)
+    check(lib().aa_plan_effective_shifts(plan, int(r), out.ctypes.data, out.size),
+          "aa_plan_effective_shifts")
+    return out
+
+
+def aa_plan_set_fdmt(plan, r: int) -> None:
+    check(lib().aa_plan_set_fdmt(plan, int(r)), "aa_plan_set_fdmt")
+
+
 def aa_plan_set_subband(plan, r: int, band_channels: int, coarse_trials: int) -> None:
     check(lib().aa_plan_set_subband(plan, int(r), int(band_channels), int(coarse_trials)),
           "aa_plan_set_subband")
@@ -460,6 +475,7 @@ def aa_dedisperse_f32_mse_device(plan, d_x, nsamp, x_pitch, d_w, d_tmpl, d_loss,
 AA_DEDISP_DIRECT = 0
 AA_DEDISP_GROUPED = 1
 AA_DEDISP_SUBBAND = 2
+AA_DEDISP_FDMT = 3
 
 
 def aa_plan_set_strategy(plan, r: int, strategy: int) -> None:

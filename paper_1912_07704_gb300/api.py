@@ -108,6 +108,10 @@ class Plan:
         """Sub-band dedispersion (an approximation) for range r."""
         abi.aa_plan_set_subband(self.handle, r, band_channels, coarse_trials)
 
+    def set_fdmt(self, r: int) -> None:
+        """FDMT-style tree dedispersion (an approximation) for range r."""
+        abi.aa_plan_set_fdmt(self.handle, r)
+
     def set_strategy(self, r: int, strategy: int) -> None:
         """Dedispersion strategy of range r: abi.AA_DEDISP_DIRECT or
         abi.AA_DEDISP_GROUPED (same result, different grouping of the sums)."""

@@ -23,7 +23,7 @@ LIB = os.path.join(HERE, "libaa_gb300.so")
 SOURCES = ["aa_plan.cpp", "aa_api.cpp", "aa_api_f32.cpp", "aa_profile.cpp", "aa_dedisp.cu",
            "aa_sps.cu", "aa_noalloc.cu", "aa_adjoint.cu", "aa_batch.cpp", "aa_autotune.cpp",
            "aa_server.cpp", "aa_fil.cpp", "aa_corner.cu", "aa_post.cu", "aa_subband.cu",
-           "aa_pipeline.cpp", "aa_fused.cpp"]
+           "aa_pipeline.cpp", "aa_fused.cpp", "aa_fdmt.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -282,6 +282,46 @@ cudaError_t launch_decimation_cascade(const aa_plan& p, const Layout& L, const u
 
 }  // namespace aa
 
+// FDMT strategy of range r: the depths of its channel tree, deepest first,
+// through two 32-bit depth buffers of the workspace; the root writes the
+// range's output rows.
+static aa_status launch_fdmt(const aa_plan* p, size_t r, const Layout& L, const void* in, int64_t in_pitch,
+                             float* d_out, char* ws, cudaStream_t s) {
+    const RangePlan& g = p->ranges[r];
+    const FdmtPlan& fd = g.fd;
+    if (L.length[r] <= 0 || g.desc.ndm <= 0) return AA_OK;
+    if (!fd.d_rows || fd.depths < 1) {
+        set_error("range %zu: FDMT tables are not on the device", r);
+        return AA_ERR_STATE;
+    }
+    if (L.fdmt_offset < 0 || L.fdmt_rows < fd.max_rows) {
+        set_error("range %zu: FDMT workspace missing from the layout", r);
+        return AA_ERR_STATE;
+    }
+    const int64_t nd = L.nsamp_dec[r];
+    uint32_t* buf[2] = {reinterpret_cast<uint32_t*>(ws + L.fdmt_offset),
+                        reinterpret_cast<uint32_t*>(ws + L.fdmt_offset +
+                                                    round_up(L.fdmt_rows * L.fdmt_pitch * 4, 256))};
+    for (int q = 0; q < fd.depths; ++q) {
+        const int depth = fd.depths - 1 - q;  // deepest first
+        const FdmtRow* rows = fd.d_rows + fd.first[(size_t)q];
+        const int nrows = (int)(fd.first[(size_t)q + 1] - fd.first[(size_t)q]);
+        const uint32_t* prev = buf[(depth + 1) & 1];  // the next-deeper depth (or unused)
+        ProfScope prof(kKFdmt, s);
+        const cudaError_t e =
+            depth == 0 ? launch_fdmt_depth(rows, nrows, g.elem, in, in_pitch, prev, nullptr, L.fdmt_pitch, nd,
+                                           d_out + L.row_offset[r], L.pitch[r], L.length[r], s)
+                       : launch_fdmt_depth(rows, nrows, g.elem, in, in_pitch, prev, buf[depth & 1], L.fdmt_pitch,
+                                           nd, nullptr, 0, 0, s);
+        if (e != cudaSuccess) {
+            set_error("FDMT depth %d launch: %s", depth, cudaGetErrorString(e));
+            cudaGetLastError();
+            return AA_ERR_CUDA;
+        }
+    }
+    return AA_OK;
+}
+
 // Sub-band strategy of range r: stage 1 per band into the 16-bit partial
 // series (direct kernel), stage 2 over all coarse trials into the range's
 // output rows (32-bit sums).
@@ -377,6 +417,11 @@ aa_status aa_dedisperse_device(const aa_plan* p, const uint8_t* d_in, int64_t ns
         }
         if (g.strategy == 2) {
             st = launch_subband(p, r, L, a.in, a.in_pitch, d_out, ws, err, s);
+            if (st != AA_OK) return st;
+            continue;
+        }
+        if (g.strategy == 3) {
+            st = launch_fdmt(p, r, L, a.in, a.in_pitch, d_out, ws, s);
             if (st != AA_OK) return st;
             continue;
         }

@@ -124,8 +124,8 @@ aa_status aa_batch_create(aa_plan* const* plans, const int64_t* nsamps, int32_t 
         if (!plans[i]) { set_error("plan %d is NULL", i); return AA_ERR_ARG; }
         if (nsamps[i] < 0) { set_error("nsamp of beam %d is negative", i); return AA_ERR_ARG; }
         for (const auto& rg : plans[i]->ranges)
-            if (rg.strategy == 2) {
-                set_error("beam %d: sub-band ranges are not available in batched runs", i);
+            if (rg.strategy == 2 || rg.strategy == 3) {
+                set_error("beam %d: sub-band and FDMT ranges are not available in batched runs", i);
                 return AA_ERR_CONFIG;
             }
         if (plans[i]->clip_iters > 0 && nsamps[i] >= (int64_t(1) << 31)) {

@@ -55,8 +55,8 @@ aa_status fused_layout(const aa_plan& p, int64_t nsamp, int32_t max_width, int32
         return AA_ERR_ARG;
     }
     for (size_t r = 0; r < p.ranges.size(); ++r)
-        if (p.ranges[r].strategy == 2) {
-            set_error("range %zu uses sub-band dedispersion, which the fused search does not stripe", r);
+        if (p.ranges[r].strategy == 2 || p.ranges[r].strategy == 3) {
+            set_error("range %zu uses sub-band or FDMT dedispersion, which the fused search does not stripe", r);
             return AA_ERR_CONFIG;
         }
     f.L = make_layout(p, nsamp, max_width);

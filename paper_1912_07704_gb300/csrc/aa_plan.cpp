@@ -7,6 +7,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <cstdint>
 #include <new>
 
 #include "aa_internal.h"
@@ -354,6 +355,16 @@ Layout make_layout(const aa_plan& p, int64_t nsamp, int32_t max_width) {
         L.sub_len.push_back(len1);
         ws += round_up((int64_t)r.sb.nsub * r.sb.ncoarse * pitch * 2, 256);
     }
+    for (size_t q = 0; q < p.ranges.size(); ++q) {
+        const RangePlan& r = p.ranges[q];
+        if (r.strategy != 3) continue;
+        L.fdmt_pitch = std::max(L.fdmt_pitch, round_up(std::max<int64_t>(nsamp / r.desc.dec, 1), 64));
+        L.fdmt_rows = std::max<int64_t>(L.fdmt_rows, r.fd.max_rows);
+    }
+    if (L.fdmt_rows > 0) {  // two 32-bit depth buffers shared by the FDMT ranges
+        L.fdmt_offset = ws;
+        ws += 2 * round_up(L.fdmt_rows * L.fdmt_pitch * 4, 256);
+    }
     L.dedisp_ws = ws;  // always holds at least the error word
     L.max_width = max_width;
     if (max_width > 0) {
@@ -395,8 +406,10 @@ static aa_status upload_subband(aa_plan* p) {
     // the same per-table rounding as the placement below
     auto table_bytes = [](size_t n) { return (size_t)round_up((int64_t)n * 4 + 256, 256); };
     size_t bytes = 0;
-    for (const auto& r : p->ranges)
+    for (const auto& r : p->ranges) {
         if (r.strategy == 2) bytes += table_bytes(r.sb.rel.size()) + table_bytes(r.sb.s2.size());
+        if (r.strategy == 3) bytes += table_bytes(r.fd.rows.size() * 4);
+    }
     int prev = -1;
     cudaGetDevice(&prev);
     cudaSetDevice(p->device);
@@ -404,19 +417,30 @@ static aa_status upload_subband(aa_plan* p) {
         cudaFree(p->d_sub);
         p->d_sub = nullptr;
     }
-    for (auto& r : p->ranges) r.sb.d_rel = r.sb.d_s2 = nullptr;
+    for (auto& r : p->ranges) {
+        r.sb.d_rel = r.sb.d_s2 = nullptr;
+        r.fd.d_rows = nullptr;
+    }
     aa_status st = AA_OK;
     if (bytes) {
         void* mem = nullptr;
         cudaError_t e = cudaMalloc(&mem, bytes);
         if (e != cudaSuccess) {
             cudaGetLastError();
-            set_error("cudaMalloc(%zu) for sub-band tables: %s", bytes, cudaGetErrorString(e));
+            set_error("cudaMalloc(%zu) for sub-band / FDMT tables: %s", bytes, cudaGetErrorString(e));
             st = AA_ERR_NOMEM;
         } else {
             p->d_sub = mem;
             size_t off = 0;
             for (auto& r : p->ranges) {
+                if (r.strategy == 3) {
+                    r.fd.d_rows = reinterpret_cast<FdmtRow*>((char*)mem + off);
+                    off += table_bytes(r.fd.rows.size() * 4);
+                    if (e == cudaSuccess)
+                        e = cudaMemcpy(r.fd.d_rows, r.fd.rows.data(), r.fd.rows.size() * sizeof(FdmtRow),
+                                       cudaMemcpyHostToDevice);
+                    continue;
+                }
                 if (r.strategy != 2) continue;
                 r.sb.d_rel = reinterpret_cast<int32_t*>((char*)mem + off);
                 off += table_bytes(r.sb.rel.size());
@@ -428,7 +452,7 @@ static aa_status upload_subband(aa_plan* p) {
                     e = cudaMemcpy(r.sb.d_s2, r.sb.s2.data(), r.sb.s2.size() * 4, cudaMemcpyHostToDevice);
             }
             if (e != cudaSuccess) {
-                set_error("upload of sub-band tables: %s", cudaGetErrorString(e));
+                set_error("upload of sub-band / FDMT tables: %s", cudaGetErrorString(e));
                 st = AA_ERR_CUDA;
             }
         }
@@ -598,7 +622,7 @@ aa_status aa_plan_bind(aa_plan* p, int device) {
     p->ready = true;
     if (prev >= 0 && prev != device) cudaSetDevice(prev);
     for (const auto& r : p->ranges)
-        if (r.strategy == 2) return upload_subband(p);
+        if (r.strategy == 2 || r.strategy == 3) return upload_subband(p);
     return AA_OK;
 }
 
@@ -670,6 +694,9 @@ aa_status aa_plan_range(const aa_plan* p, int64_t nsamp, int32_t r, aa_range_inf
     info->subband_channels = g.strategy == 2 ? g.sb.k : 0;
     info->subband_coarse_trials = g.strategy == 2 ? g.sb.m : 0;
     info->subband_work = g.strategy == 2 ? g.sb.work : 0.0;
+    info->fdmt_depths = g.strategy == 3 ? g.fd.depths : 0;
+    info->fdmt_max_rows = g.strategy == 3 ? g.fd.max_rows : 0;
+    info->fdmt_work = g.strategy == 3 ? g.fd.work : 0.0;
     return AA_OK;
 }
 
@@ -797,6 +824,174 @@ aa_status aa_plan_set_subband(aa_plan* p, int32_t r, int32_t band_channels, int3
             return st;
         }
     }
+    return AA_OK;
+}
+
+aa_status aa_plan_set_fdmt(aa_plan* p, int32_t r) {
+    clear_error();
+    if (!p) { set_error("plan is NULL"); return AA_ERR_ARG; }
+    if (r < 0 || r >= (int32_t)p->ranges.size()) { set_error("range %d out of bounds", r); return AA_ERR_ARG; }
+    RangePlan& g = p->ranges[r];
+    const int32_t C = p->nchans, ndm = g.desc.ndm;
+    if (C < 2) { set_error("the FDMT tree needs at least two channels"); return AA_ERR_CONFIG; }
+    if ((int64_t)C * 255 * g.desc.dec >= (int64_t(1) << 31)) {
+        set_error("range %d: sums of %d channels at decimation %d exceed 31 bits", r, C, g.desc.dec);
+        return AA_ERR_CONFIG;
+    }
+    // channels in falling-frequency order and their f^-2 - f_top^-2, in the
+    // operation order of the plan's delays
+    std::vector<double> dk((size_t)C);
+    std::vector<int32_t> chan((size_t)C);
+    for (int32_t k = 0; k < C; ++k) {
+        const int32_t c = p->foff < 0 ? k : C - 1 - k;
+        const double fc = p->fch1 + (double)c * p->foff;
+        chan[(size_t)k] = c;
+        dk[(size_t)k] = 1.0 / (fc * fc) - 1.0 / (p->f_top * p->f_top);
+    }
+    // split of subband [a, b] at delay delta: (upper delay, gap, lower delay)
+    auto split = [&](int32_t a, int32_t b, int64_t delta, int32_t& m, int64_t& du, int64_t& gap) {
+        m = a + (b - a + 2) / 2;
+        const double span = dk[(size_t)b] - dk[(size_t)a];
+        gap = span > 0.0 ? llround((double)delta * (dk[(size_t)m] - dk[(size_t)a]) / span) : 0;
+        du = span > 0.0 ? llround((double)delta * (dk[(size_t)m - 1] - dk[(size_t)a]) / span) : 0;
+    };
+    const int32_t bottom = p->foff < 0 ? C - 1 : 0;
+    struct Node { int32_t a, b; int64_t lo, hi; int32_t row0; };
+    FdmtPlan fd;
+    // depth by depth from the root: the delays each node must provide (a
+    // contiguous range covering what its parent reads)
+    std::vector<std::vector<Node>> depth;
+    std::vector<int64_t> rootD((size_t)ndm);
+    for (int32_t i = 0; i < ndm; ++i) rootD[(size_t)i] = g.shifts[(size_t)i * C + bottom];
+    std::vector<Node> cur;
+    if (ndm > 0 && C > 1) {
+        const int64_t lo = *std::min_element(rootD.begin(), rootD.end());
+        const int64_t hi = *std::max_element(rootD.begin(), rootD.end());
+        cur.push_back(Node{0, C - 1, lo, hi, 0});
+    }
+    // children of a node for the delays [lo, hi] it provides; leaves are not nodes
+    auto children = [&](const Node& n, std::vector<Node>& out) {
+        int32_t m;
+        int64_t du, gap;
+        int64_t ulo = INT64_MAX, uhi = INT64_MIN, llo = INT64_MAX, lhi = INT64_MIN;
+        for (int64_t d = n.lo; d <= n.hi; ++d) {
+            split(n.a, n.b, d, m, du, gap);
+            ulo = std::min(ulo, du);
+            uhi = std::max(uhi, du);
+            llo = std::min(llo, d - gap);
+            lhi = std::max(lhi, d - gap);
+        }
+        split(n.a, n.b, n.lo, m, du, gap);
+        if (m - 1 > n.a) out.push_back(Node{n.a, m - 1, ulo, uhi, 0});
+        if (n.b > m) out.push_back(Node{m, n.b, llo, lhi, 0});
+    };
+    while (!cur.empty()) {
+        depth.push_back(cur);
+        std::vector<Node> nxt;
+        for (const Node& n : cur) children(n, nxt);
+        cur.swap(nxt);
+    }
+    fd.depths = (int)depth.size();
+    // rows of each depth (the root's: one per trial)
+    std::vector<int32_t> nrows(depth.size(), 0);
+    for (size_t d = 1; d < depth.size(); ++d)
+        for (Node& n : depth[d]) {
+            n.row0 = nrows[d];
+            nrows[d] += (int32_t)(n.hi - n.lo + 1);
+        }
+    if (!depth.empty()) nrows[0] = ndm;
+    // node of each depth by its first channel (the subbands of a depth are disjoint)
+    std::vector<std::vector<int32_t>> at(depth.size(), std::vector<int32_t>((size_t)C, -1));
+    for (size_t d = 0; d < depth.size(); ++d)
+        for (size_t j = 0; j < depth[d].size(); ++j) at[d][(size_t)depth[d][j].a] = (int32_t)j;
+    // reference to the row providing subband [a, b] at delay delta, one depth deeper
+    auto ref = [&](size_t d, int32_t a, int32_t b, int64_t delta) -> int32_t {
+        if (a == b) return -(chan[(size_t)a] + 1);  // leaf: the channel's own row (delay 0)
+        const int32_t j = d + 1 < depth.size() ? at[d + 1][(size_t)a] : -1;
+        if (j < 0 || depth[d + 1][(size_t)j].b != b) return INT32_MIN;  // unreachable
+        const Node& n = depth[d + 1][(size_t)j];
+        if (delta < n.lo || delta > n.hi) return INT32_MIN;
+        return n.row0 + (int32_t)(delta - n.lo);
+    };
+    fd.first.assign(depth.size() + 1, 0);
+    for (size_t q = 0; q < depth.size(); ++q) {  // deepest first
+        const size_t d = depth.size() - 1 - q;
+        fd.first[q] = (int64_t)fd.rows.size();
+        auto emit = [&](const Node& n, int64_t delta) {
+            int32_t m;
+            int64_t du, gap;
+            split(n.a, n.b, delta, m, du, gap);
+            FdmtRow row{ref(d, n.a, m - 1, du), ref(d, m, n.b, delta - gap), (int32_t)gap, (int32_t)delta};
+            fd.rows.push_back(row);
+        };
+        if (d == 0) {
+            for (int32_t i = 0; i < ndm; ++i) emit(depth[0][0], rootD[(size_t)i]);
+        } else {
+            for (const Node& n : depth[d])
+                for (int64_t delta = n.lo; delta <= n.hi; ++delta) emit(n, delta);
+            fd.max_rows = std::max(fd.max_rows, nrows[d]);
+        }
+    }
+    fd.first[depth.size()] = (int64_t)fd.rows.size();
+    for (const FdmtRow& row : fd.rows)
+        if (row.u == INT32_MIN || row.l == INT32_MIN) {
+            set_error("internal: FDMT tree reference missing");
+            return AA_ERR_STATE;
+        }
+    fd.work = ndm > 0 ? (double)fd.rows.size() / ((double)ndm * C) : 1.0;
+    const FdmtPlan old = g.fd;
+    const int old_strategy = g.strategy;
+    g.fd = std::move(fd);
+    g.strategy = 3;
+    if (p->ready) {
+        const aa_status st = upload_subband(p);
+        if (st != AA_OK) {
+            g.fd = old;
+            g.strategy = old_strategy;
+            upload_subband(p);
+            return st;
+        }
+    }
+    return AA_OK;
+}
+
+aa_status aa_plan_effective_shifts(const aa_plan* p, int32_t r, int32_t* out, int64_t cap) {
+    clear_error();
+    if (!p || !out) { set_error("plan/out is NULL"); return AA_ERR_ARG; }
+    if (r < 0 || r >= (int32_t)p->ranges.size()) { set_error("range %d out of bounds", r); return AA_ERR_ARG; }
+    const RangePlan& g = p->ranges[r];
+    const int32_t C = p->nchans, ndm = g.desc.ndm;
+    if (cap < (int64_t)ndm * C) { set_error("capacity %lld < %lld", (long long)cap, (long long)ndm * C); return AA_ERR_ARG; }
+    if (g.strategy == 2) {  // reference channel's delay + the channel's within its band
+        const SubbandPlan& sb = g.sb;
+        for (int32_t i = 0; i < ndm; ++i) {
+            const int32_t j = i / sb.m;
+            size_t off = 0;
+            for (int b = 0; b < sb.nsub; ++b) {
+                const int c0 = b * sb.k, kb = std::min(C, c0 + sb.k) - c0;
+                for (int cl = 0; cl < kb; ++cl)
+                    out[(int64_t)i * C + c0 + cl] = sb.s2[(size_t)i * sb.nsub + b] + sb.rel[off + (size_t)j * kb + cl];
+                off += (size_t)sb.ncoarse * kb;
+            }
+        }
+        return AA_OK;
+    }
+    if (g.strategy == 3) {  // walk the tree from each trial's root row
+        const FdmtPlan& fd = g.fd;
+        // rows of depth d start at fd.first[depths - 1 - d]
+        auto walk = [&](auto&& self, int d, int32_t row, int64_t base, int32_t* e) -> void {
+            const FdmtRow& x = fd.rows[(size_t)(fd.first[(size_t)(fd.depths - 1 - d)] + row)];
+            for (int half = 0; half < 2; ++half) {
+                const int32_t ref = half ? x.l : x.u;
+                const int64_t b = base + (half ? x.gap : 0);
+                if (ref < 0) e[-(ref + 1)] = (int32_t)b;
+                else self(self, d + 1, ref, b, e);
+            }
+        };
+        for (int32_t i = 0; i < ndm; ++i) walk(walk, 0, i, 0, out + (int64_t)i * C);
+        return AA_OK;
+    }
+    std::memcpy(out, g.shifts.data(), g.shifts.size() * 4);
     return AA_OK;
 }
 

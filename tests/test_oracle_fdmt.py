@@ -119,3 +119,28 @@ def test_fdmt_against_brute_force_delays(oracle):
         b = oracle.fdmt_bottom(C, foff)
         assert np.array_equal(tab[:, b], g.shifts[:, b])
         assert np.abs(tab.astype(np.int64) - g.shifts).max() <= bound
+
+
+@pytest.mark.parametrize("nchans,fch1,foff,ranges", [
+    (100, 1450.0, -3.0, [(0.0, 2.0, 37, 1), (74.0, 3.0, 21, 2), (187.0, 8.0, 19, 8)]),
+    (37, 1200.0, 2.5, [(0.0, 5.0, 20, 1)]),
+    (4096, 1508.0, -0.0732421875, [(600.0, 1.0, 200, 8)]),
+])
+def test_library_tree_equals_oracle(oracle, nchans, fch1, foff, ranges):
+    """The library's host-built tree (aa_plan_set_fdmt) gives the oracle's
+    effective delays for every channel and trial (two implementations of the
+    split rule, compared through aa_plan_effective_shifts)."""
+    from paper_1912_07704_gb300 import abi
+    from paper_1912_07704_gb300.api import Plan
+    T = 1 << 17
+    p = Plan(nchans, fch1, foff, 64e-6, ranges)
+    pl = oracle.plan(nchans, fch1, foff, 64e-6, ranges, T)
+    for r, g in enumerate(pl):
+        p.set_fdmt(r)
+        info = abi.aa_plan_range(p.handle, T, r)
+        assert info.strategy == abi.AA_DEDISP_FDMT and info.length == g.length
+        eff = abi.aa_plan_effective_shifts(p.handle, r, g.ndm, nchans)
+        assert np.array_equal(eff, oracle.fdmt_table(nchans, fch1, foff, g))
+        p.set_strategy(r, abi.AA_DEDISP_DIRECT)  # back to the exact sum
+        assert np.array_equal(abi.aa_plan_effective_shifts(p.handle, r, g.ndm, nchans), g.shifts)
+    p.close()
