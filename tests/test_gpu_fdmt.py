@@ -72,7 +72,8 @@ def test_fdmt_4096_channels(oracle):
     # the host path runs the same tree
     dd = plan.dedisperse(x)
     host = dd.to_tensor()
-    assert torch.equal(host, out[: host.numel()])
+    for a, b in zip(plan.range_views(host, nsamp), plan.range_views(out, nsamp)):
+        assert torch.equal(a, b)
     dd.close()
     plan.close()
 
