@@ -413,7 +413,10 @@ aa_status aa_batch_candidates(aa_batch* batch, aa_stream_t stream, aa_candidates
  * Chunks queue on the host and are admitted into slots (own stream and device
  * workspace; slot count = min(max_slots, what memory_budget allows after the
  * beams' resident buffers)) as slots free up; a beam's chunks run in order,
- * chunks of different beams overlap on the device. */
+ * chunks of different beams overlap on the device.  When the plan has no
+ * sub-band or FDMT range, a slot runs aa_search_fused_device (same results)
+ * and holds its workspace instead of the series of every trial, so a budget
+ * admits more slots. */
 typedef struct aa_server aa_server;
 
 typedef struct aa_chunk_info {

@@ -16,7 +16,10 @@
 // Requests queue on the host; the loop admits a queued chunk into a free
 // slot (own stream and device workspace; the number of slots is fixed by the
 // memory budget) as soon as the chunk's beam has no chunk in flight, so that
-// chunks of different beams overlap on the device.
+// chunks of different beams overlap on the device.  A slot runs the fused
+// dedispersion -> search (stripes of trials, statistics from the
+// dedispersion kernels) when the plan allows it, so it holds one stripe of
+// series instead of every row.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -98,6 +101,10 @@ struct aa_server {
     int64_t completed = 0;
     int32_t max_in_flight = 0;
     double first_arrival = -1, last_done = 0;
+    // fused dedispersion -> search (aa_search_fused_device) when the plan
+    // allows it: a slot then holds one stripe of series, not every row
+    bool fused = false;
+    size_t fused_ws = 0;
 };
 
 namespace {
@@ -123,13 +130,20 @@ aa_status launch_chunk(aa_server& s, Slot& sl, Request& r) {
     }
     AA_CUDA(cudaMemcpy2DAsync(dst + hist, s.pitch, r.host, r.host_pitch, s.N, C, cudaMemcpyHostToDevice, st),
             "chunk upload");
-    const Layout L = make_layout(*s.plan, len, s.W);
-    aa_status e = aa_dedisperse_device(s.plan, dst, len, s.pitch, sl.dd, sl.dd_ws, (size_t)L.dedisp_ws,
-                                       reinterpret_cast<aa_stream_t>(st));
-    if (e != AA_OK) return e;
-    e = aa_sps_search_device(s.plan, len, sl.dd, s.W, s.thr, sl.cands, s.cap, sl.count, nullptr,
-                             sl.sps_ws, (size_t)L.sps_ws, reinterpret_cast<aa_stream_t>(st));
-    if (e != AA_OK) return e;
+    if (s.fused) {
+        const aa_status e = aa_search_fused_device(s.plan, dst, len, s.pitch, s.W, s.thr, 0, sl.cands, s.cap,
+                                                   sl.count, nullptr, sl.dd_ws, s.fused_ws,
+                                                   reinterpret_cast<aa_stream_t>(st));
+        if (e != AA_OK) return e;
+    } else {
+        const Layout L = make_layout(*s.plan, len, s.W);
+        aa_status e = aa_dedisperse_device(s.plan, dst, len, s.pitch, sl.dd, sl.dd_ws, (size_t)L.dedisp_ws,
+                                           reinterpret_cast<aa_stream_t>(st));
+        if (e != AA_OK) return e;
+        e = aa_sps_search_device(s.plan, len, sl.dd, s.W, s.thr, sl.cands, s.cap, sl.count, nullptr,
+                                 sl.sps_ws, (size_t)L.sps_ws, reinterpret_cast<aa_stream_t>(st));
+        if (e != AA_OK) return e;
+    }
     AA_CUDA(cudaMemcpyAsync(sl.h_count, sl.count, 8, cudaMemcpyDeviceToHost, st), "count readback");
     AA_CUDA(cudaEventRecord(sl.done, st), "record completion");
     AA_CUDA(cudaEventRecord(b.last, st), "record beam progress");
@@ -237,8 +251,10 @@ aa_status aa_server_create(aa_plan* plan, int32_t nbeams, int64_t chunk_nsamp, i
     s->pitch = L.in_pitch_min;
     // resident state: two block buffers per beam
     const int64_t beam_bytes = 2 * (int64_t)plan->nchans * s->pitch;
-    const int64_t slot_bytes = L.dedisp_ws + L.dd_elems * 4 + L.sps_ws +
-                               cand_capacity * (int64_t)sizeof(aa_candidate) + 4096;
+    s->fused = aa_search_fused_ws_bytes(plan, block, max_width, 0, &s->fused_ws, nullptr) == AA_OK;
+    clear_error();  // plans with sub-band or FDMT ranges keep the unfused path
+    const int64_t work_bytes = s->fused ? (int64_t)s->fused_ws : L.dedisp_ws + L.dd_elems * 4 + L.sps_ws;
+    const int64_t slot_bytes = work_bytes + cand_capacity * (int64_t)sizeof(aa_candidate) + 4096;
     if (memory_budget <= 0) {
         size_t fr = 0, tot = 0;
         cudaMemGetInfo(&fr, &tot);
@@ -263,9 +279,13 @@ aa_status aa_server_create(aa_plan* plan, int32_t nbeams, int64_t chunk_nsamp, i
     for (auto& sl : s->slots) {
         cudaError_t e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
-        if (e == cudaSuccess) e = cudaMalloc(&sl.dd_ws, (size_t)L.dedisp_ws);
-        if (e == cudaSuccess) e = cudaMalloc(&sl.dd, (size_t)std::max<int64_t>(L.dd_elems * 4, 256));
-        if (e == cudaSuccess) e = cudaMalloc(&sl.sps_ws, (size_t)L.sps_ws);
+        if (s->fused) {  // one fused workspace per slot
+            if (e == cudaSuccess) e = cudaMalloc(&sl.dd_ws, std::max<size_t>(s->fused_ws, 256));
+        } else {
+            if (e == cudaSuccess) e = cudaMalloc(&sl.dd_ws, (size_t)L.dedisp_ws);
+            if (e == cudaSuccess) e = cudaMalloc(&sl.dd, (size_t)std::max<int64_t>(L.dd_elems * 4, 256));
+            if (e == cudaSuccess) e = cudaMalloc(&sl.sps_ws, (size_t)L.sps_ws);
+        }
         if (e == cudaSuccess) e = cudaMalloc(&sl.cands, (size_t)cand_capacity * sizeof(aa_candidate));
         if (e == cudaSuccess) e = cudaMalloc(&sl.count, 256);
         if (e == cudaSuccess) e = cudaMallocHost(&sl.h_count, 64);
