@@ -739,7 +739,7 @@ def bench_stream(args):
     st_sat, _ = run(lockstep=True)
     data_s = nbeams * nchunk * chunk_s
     # per-slot device work area of the two search paths (the server runs the
-    # fused one), and the slots a 16 GB budget would admit with each
+    # fused one), and the slots a 48 GiB budget would admit with each
     from paper_1912_07704_gb300 import abi as _abi
     block = st_rt.history_nsamp + N
     qi = plan.query(block, base.max_width)
@@ -747,7 +747,7 @@ def bench_stream(args):
     fused, _ = _abi.aa_search_fused_ws_bytes(plan.handle, block, base.max_width, 0)
     resident = 2 * nbeams * base.nchans * plan.query(block).in_pitch_min
     per_slot = lambda work: work + (1 << 22) * 16 + 4096
-    budget = 16 << 30
+    budget = 48 << 30
     line = {"metric": "streaming serve: chunk latency and sustained real-time factor",
             "workload": f"{nbeams} beams x {base.nchans} ch, 2^16-sample chunks, 1.2x real-time Poisson",
             "chunks": nbeams * nchunk, "history_nsamp": st_rt.history_nsamp, "slots": st_rt.slots,
@@ -757,7 +757,7 @@ def bench_stream(args):
             "saturated_rtf": data_s / st_sat.span, "saturated_latency_p99_s": st_sat.latency_p99,
             "candidates": ncand,
             "slot_work_bytes": {"fused": fused, "unfused": unfused},
-            "slots_in_16GiB_budget": {"fused": (budget - resident) // per_slot(fused),
+            "slots_in_48GiB_budget": {"fused": (budget - resident) // per_slot(fused),
                                       "unfused": (budget - resident) // per_slot(unfused)}}
     print(json.dumps(line), flush=True)
 
