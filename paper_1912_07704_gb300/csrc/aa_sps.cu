@@ -327,15 +327,6 @@ __device__ void block_minmax(long long& mn, long long& mx, long long* scratch) {
 constexpr int M = kSpsSlots;
 constexpr int NT = kSpsThreads;
 
-// Position of element i of the staged series / prefix sums in shared memory:
-// 16-byte blocks are XOR-swizzled within groups of eight (block j stored at
-// j ^ ((j >> 3) & 3)).  A thread's window loads are 16-byte loads 64 bytes
-// apart from its neighbours', so without the swizzle the eight threads of a
-// quarter-warp hit two of the eight 16-byte bank groups; with it they hit
-// eight.  Blocks stay whole (16-byte loads stay aligned) and 32 consecutive
-// floats still fall in 32 different banks.
-__device__ __forceinline__ int swz(int i) { return i ^ (((i >> 5) & 3) << 2); }
-
 // Exact-FP32 tiles.  P is the prefix-sum array of the staged series (index
 // i <-> start time t0-1+i): P[i] = sum of y - m0 over the valid samples before
 // i, -kBig once a window would run past the series end.  Every window sum
@@ -369,7 +360,7 @@ __device__ __forceinline__ float warp_segment_bound(const float* __restrict__ P,
     const int lane = threadIdx.x & 31;
     const int lo = b.p_first + w1, hi = min(b.ylen - 1, b.p_first + M * 32 - 1 + w2);
     float pmax = -FLT_MAX;
-    for (int j = lo + lane; j <= hi; j += 32) pmax = fmaxf(pmax, P[swz(j)]);
+    for (int j = lo + lane; j <= hi; j += 32) pmax = fmaxf(pmax, P[j]);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) pmax = fmaxf(pmax, __shfl_xor_sync(0xffffffffu, pmax, o));
     const float drift = b.f >= 0.0f ? (float)w1 * b.f : (float)w2 * b.f;
@@ -396,7 +387,7 @@ __device__ __forceinline__ int boxcar_prefix(const float* __restrict__ P,
                                              const float2* __restrict__ tab, int wpad,
                                              const float (&base)[M], const WarpBound& bnd,
                                              const uint32_t* lmask, float (&B)[M], int (&C)[M]) {
-    const int pb = M * threadIdx.x;
+    const float* pb = P + M * threadIdx.x;
     int evaluated = 0;
 #pragma unroll
     for (int i = 0; i < M; ++i) {
@@ -433,7 +424,7 @@ __device__ __forceinline__ int boxcar_prefix(const float* __restrict__ P,
         float win[2 * M];  // win[k] = P[p_thread + w0 + k]
 #pragma unroll
         for (int k = 0; k < 2 * M; k += 4) {
-            const float4 v = *reinterpret_cast<const float4*>(P + swz(pb + w0 + k));
+            const float4 v = *reinterpret_cast<const float4*>(pb + w0 + k);
             win[k] = v.x; win[k + 1] = v.y; win[k + 2] = v.z; win[k + 3] = v.w;
         }
         float Bc[M];  // best SNR of this chunk, per slot
@@ -473,11 +464,11 @@ __device__ __forceinline__ int boxcar_prefix(const float* __restrict__ P,
 __device__ __noinline__ float boxcar_exact_slot(const float* __restrict__ ys,
                                                 const float2* __restrict__ tab, int wpad, int i,
                                                 const uint32_t* lmask) {
-    const int yb = M * threadIdx.x + i;
+    const float* yb = ys + M * threadIdx.x + i;
     long long S = 0;
     float best = -FLT_MAX;
     for (int w = 1; w <= wpad; ++w) {
-        const float v = ys[swz(yb + w - 1)];
+        const float v = yb[w - 1];
         if (v < kSentinelTest) break;  // window left [0, L): later widths invalid too
         S += (long long)v;
         if (lmask && !ladder_has(lmask, w)) continue;
@@ -505,7 +496,7 @@ __device__ __forceinline__ void boxcar_block(const SpsArgs& a, int ntiles, int64
     const int wpad = a.wpad;
     const int ylen = kSpsTile + wpad + M;
     float* ys = sm;
-    float2* tab = reinterpret_cast<float2*>(sm + ((ylen + 31) & ~31));  // swizzle groups of 32
+    float2* tab = reinterpret_cast<float2*>(sm + ((ylen + 3) & ~3));
     const int row = (int)(bid / ntiles);
     const int64_t tile = bid - (int64_t)row * ntiles;
     const int64_t t0 = tile * kSpsOwned;
@@ -528,7 +519,7 @@ __device__ __forceinline__ void boxcar_block(const SpsArgs& a, int ntiles, int64
         }
 #pragma unroll
         for (int u = 0; u < kBatch; ++u)
-            if (i0b + u * NT < ylen) ys[swz(i0b + u * NT)] = v[u];
+            if (i0b + u * NT < ylen) ys[i0b + u * NT] = v[u];
     }
     const float2* gtab = a.table + (int64_t)row * wpad;
     {
@@ -555,7 +546,7 @@ __device__ __forceinline__ void boxcar_block(const SpsArgs& a, int ntiles, int64
     const int i0 = min(ylen, threadIdx.x * seg), i1 = min(ylen, i0 + seg);
     long long run = 0, mn = 0, mx = 0;
     for (int i = i0; i < i1; ++i) {
-        const float v = ys[swz(i)];
+        const float v = ys[i];
         if (v > kSentinelTest) {
             run += (long long)(int)v;
             mn = min(mn, run);
@@ -577,8 +568,8 @@ __device__ __forceinline__ void boxcar_block(const SpsArgs& a, int ntiles, int64
         __syncthreads();
         float runf = (float)before;
         for (int i = i0; i < i1; ++i) {
-            const float v = ys[swz(i)];
-            ys[swz(i)] = i > vb + 1 ? -kBig : runf;
+            const float v = ys[i];
+            ys[i] = i > vb + 1 ? -kBig : runf;
             if (v > kSentinelTest) runf += v;
         }
         __syncthreads();
@@ -589,7 +580,7 @@ __device__ __forceinline__ void boxcar_block(const SpsArgs& a, int ntiles, int64
         for (int i = 0; i < M; ++i) {
             const int p = M * threadIdx.x + i;
             const bool valid = p >= va && p <= vb;
-            base[i] = valid ? P[swz(p)] : kBig;
+            base[i] = valid ? P[p] : kBig;
             if (valid) pmin = fminf(pmin, base[i]);
         }
 #pragma unroll
@@ -666,19 +657,19 @@ __device__ __forceinline__ void boxcar_block(const SpsArgs& a, int ntiles, int64
         const int cw0 = (int)(plist[q] >> 16) * M;
         const int64_t t = t0 - 1 + p;
         const int wmax = (int)min((int64_t)a.max_width, L - t);
-        // exact path: ys[swz(p + w - 1)] = y[t+w-1] - m0
+        const float* yq = ys + p;  // exact path: yq[w-1] = y[t+w-1] - m0
         const float target = Bs[p];
         float best = -FLT_MAX;
         int bw = 0x7fffffff;
         if (fast) {
             // prefix form: S_w = P[p+w] - P[p], exact
             const float* P = ys;
-            const float b0 = P[swz(p)];
+            const float b0 = P[p];
             for (int w0 = cw0; w0 < wmax; w0 += 32) {
                 const int w = w0 + lane + 1;
                 if (w <= wmax && (!lmask || ladder_has(lmask, w))) {
                     const float2 rc = __ldg(gtab + w - 1);
-                    const float snr = fmaf(P[swz(p + w)] - b0, rc.x, rc.y);
+                    const float snr = fmaf(P[p + w] - b0, rc.x, rc.y);
                     if (snr > best) { best = snr; bw = w; }
                 }
                 // widths are visited in increasing order: stop at the chunk
@@ -689,7 +680,7 @@ __device__ __forceinline__ void boxcar_block(const SpsArgs& a, int ntiles, int64
             long long base = 0;
             for (int w0 = 0; w0 < wmax; w0 += 32) {
                 const int w = w0 + lane + 1;
-                long long v = (w <= wmax) ? (long long)ys[swz(p + w - 1)] : 0;
+                long long v = (w <= wmax) ? (long long)yq[w - 1] : 0;
 #pragma unroll
                 for (int o = 1; o < 32; o <<= 1) {
                     const long long u = __shfl_up_sync(0xffffffffu, v, o);
@@ -818,7 +809,7 @@ cudaError_t launch_rsqrt_table(double* t, int wpad, cudaStream_t s) {
 
 size_t sps_boxcar_smem(int wpad) {
     const int ylen = kSpsTile + wpad + M;
-    return (size_t)((ylen + 31) & ~31) * 4 + (size_t)sps_region_bytes(wpad);
+    return (size_t)((ylen + 3) & ~3) * 4 + (size_t)sps_region_bytes(wpad);
 }
 
 cudaError_t launch_sps_boxcar(const SpsArgs& a, cudaStream_t s) {
