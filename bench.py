@@ -625,17 +625,20 @@ def bench_adjoint(args):
 
 
 def bench_batched(args):
-    """32 uneven beams (1024/4096 ch, 2^17..2^20 samples, DM_max 500..3000):
-    one CUDA graph of persistent work-queue kernels vs the beams run one
-    after another through the single-beam path, same GPU, same results."""
+    """Batched beams in one CUDA graph vs the beams run one after another
+    through the single-beam path, same GPU, same results.  `batched`: 32
+    uneven beams (1024/4096 ch, 2^17..2^20 samples, DM_max 500..3000);
+    `batched-small`: 128 short beams (512/1024 ch, 2^15..2^16 samples,
+    DM_max 100..400)."""
     import torch
     from paper_1912_07704_gb300 import synth
     from paper_1912_07704_gb300.api import Batch, Plan
-    beams = synth.batched_beams(32)
+    small = args.workload == "batched-small"
+    beams = synth.small_beams(128) if small else synth.batched_beams(32)
     plans = [Plan.from_workload(w) for w in beams]
     for p in plans:
         p.bind()
-    batch = Batch(plans, [w.nsamp for w in beams], 8192, 6.0, capacity=1 << 25)
+    batch = Batch(plans, [w.nsamp for w in beams], 8192, 6.0, capacity=1 << 28)
     dm_samples = 0
     for i, (w, p) in enumerate(zip(beams, plans)):
         def delays(dm, w=w):
@@ -647,9 +650,22 @@ def bench_batched(args):
         del x
         dm_samples += p.query(w.nsamp).dm_trial_samples
     torch.cuda.synchronize()
-    t_batch = _time_cuda(batch.run, args.steps, args.warmup)
+    forms = {}
+    arr, total = None, None
+    for k in [int(v) for v in args.batch_branches.split(",")]:
+        batch.set_branches(k)
+        forms[k] = _time_cuda(batch.run, args.steps, args.warmup)
+        arr_k, total_k = batch.candidates()
+        if arr is None:
+            arr, total = arr_k, total_k
+        else:
+            # past the capacity the stored subset depends on arrival order: totals only
+            same = total_k == total and (total > (1 << 28) or
+                                         (len(arr_k) == len(arr) and bool((arr_k == arr).all())))
+            assert same, f"graph form {k} found other candidates ({total_k} vs {total})"
+    best = int(args.batch_branches.split(",")[0])  # the reported form: the first listed
+    t_batch = forms[best]
     nwaves, nbytes = batch.info()
-    arr, total = batch.candidates()
     # the same beams through the single-beam path, one after another
     info = [p.query(w.nsamp, 8192) for p, w in zip(plans, beams)]
     out = torch.empty(max(i.dd_elems for i in info), dtype=torch.float32, device="cuda")
@@ -665,11 +681,14 @@ def bench_batched(args):
             p.sps_search_device(out, w.nsamp, 8192, 6.0, 1 << 25, ws=wss, cands=cands, count=count)
 
     t_single = _time_cuda(one_by_one, args.steps, args.warmup)
-    line = {"metric": "batched beams: DM-trial samples/s", "workload": "32 uneven beams",
+    line = {"metric": "batched beams: DM-trial samples/s",
+            "workload": "128 short beams" if small else "32 uneven beams",
             "unit": "DM-trial samples/s", "steps": args.steps, "warmup": args.warmup,
             "batched_value": dm_samples / (t_batch / 1e3),
             "single_beam_sum_value": dm_samples / (t_single / 1e3),
             "batched_ms": t_batch, "single_beams_ms": t_single, "speedup": t_single / t_batch,
+            "batched_form": "persistent work queues" if best == 0 else f"{best} graph branches",
+            "ms_by_form": {("persistent" if k == 0 else f"branches_{k}"): v for k, v in forms.items()},
             "waves": nwaves, "batch_device_bytes": nbytes, "dm_trial_samples": dm_samples,
             "candidates": total}
     print(json.dumps(line), flush=True)
@@ -872,7 +891,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["ska", "ska-small", "adjoint", "batched", "stream",
+    ap.add_argument("--workload", choices=["ska", "ska-small", "adjoint", "batched", "batched-small", "stream",
                                            "cornerturn", "postprocess"],
                     default="ska")
     ap.add_argument("--stream-chunks", type=int, default=6)
@@ -883,6 +902,10 @@ def main():
                          "metric)")
     ap.add_argument("--sps-clip", default="",
                     help="C16,ITERS: k-sigma clipped statistics (k = C16/16), e.g. 48,4")
+    ap.add_argument("--batch-branches", default="8,0",
+                    help="batched workloads: graph forms to time (0 = persistent work-queue kernels, "
+                         "k = each beam's kernels on k concurrent branches); the first is reported "
+                         "(8 = the library's default), the others are listed beside it")
     ap.add_argument("--sps-ladder", type=int, default=0,
                     help="G16: sparse boxcar width ladder of growth G16/16 (approximate), e.g. 24")
     ap.add_argument("--fused", action="store_true",
@@ -895,7 +918,7 @@ def main():
         bench_reference(args)
     elif args.workload == "adjoint":
         bench_adjoint(args)
-    elif args.workload == "batched":
+    elif args.workload in ("batched", "batched-small"):
         bench_batched(args)
     elif args.workload == "stream":
         bench_stream(args)

@@ -361,10 +361,10 @@ aa_status aa_plan_autotune(aa_plan* plan, int64_t nsamp_probe, const char* cache
 /* ------------------------------------------------------ batched beams -- */
 
 /* Many independent beams (each with its own plan and length) searched by one
- * CUDA graph: per stage (decimation, dedispersion, statistics, boxcar +
- * peaks) one persistent kernel whose work queue spans every beam of a wave;
- * beams are grouped into waves whose working set fits wave_budget_bytes
- * (<= 0: half of the free device memory) and waves reuse one buffer region.
+ * CUDA graph.  Beams are grouped into waves whose working set fits
+ * wave_budget_bytes (<= 0: half of the free device memory) and waves reuse
+ * one buffer region; within a wave the graph issues each beam's kernels on 8
+ * concurrent branches (see aa_batch_set_branches for the other form).
  * Plans are bound to the current device if needed; they must stay alive
  * while the batch exists.  The library allocates all device memory at
  * creation (inputs included: see aa_batch_input).  nbeams <= 256. */
@@ -389,6 +389,18 @@ aa_status aa_batch_dd_view(const aa_batch* batch, int32_t beam, const float** d_
 
 /* Number of waves and total device bytes held by the batch. */
 aa_status aa_batch_info(const aa_batch* batch, int32_t* nwaves, int64_t* device_bytes);
+
+/* How the graph issues each wave (re-records the graph; the buffers, waves
+ * and results are unchanged).  branches = 0: one persistent work-queue
+ * kernel per stage spanning the wave's beams; branches = k in [1, 64] (8 at
+ * creation): each beam's own kernels, as the single-beam path
+ * launches them (decimation cascade, one dedispersion launch per range,
+ * statistics and boxcar + peaks per range), on k concurrent graph branches,
+ * the wave's beams dealt largest first to the least-loaded branch by
+ * channel-adds.  The candidate set of a run does not depend on the form.
+ * AA_ERR_ARG outside [0, 64]; AA_ERR_CUDA if the graph cannot be recorded
+ * (the batch then has no graph until a later call succeeds). */
+aa_status aa_batch_set_branches(aa_batch* batch, int32_t branches);
 
 /* Launch the captured graph on `stream` (asynchronous). */
 aa_status aa_batch_run(aa_batch* batch, aa_stream_t stream);

@@ -158,6 +158,7 @@ _SIG = {
     "aa_batch_info": (ctypes.c_int, [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I64)]),
     "aa_batch_dd_view": (ctypes.c_int, [_P, _I32, ctypes.POINTER(_P)]),
     "aa_batch_run": (ctypes.c_int, [_P, _P]),
+    "aa_batch_set_branches": (ctypes.c_int, [_P, _I32]),
     "aa_batch_candidates": (ctypes.c_int, [_P, _P, ctypes.POINTER(_P)]),
     "aa_server_create": (ctypes.c_int, [_P, _I32, _I64, _I32, _F32, _I64, _I64, _I32,
                                         ctypes.POINTER(_P)]),
@@ -523,6 +524,10 @@ def aa_batch_info(batch) -> tuple:
 
 def aa_batch_run(batch, stream) -> None:
     check(lib().aa_batch_run(batch, stream), "aa_batch_run")
+
+
+def aa_batch_set_branches(batch, branches: int) -> None:
+    check(lib().aa_batch_set_branches(batch, branches), "aa_batch_set_branches")
 
 
 def aa_batch_candidates(batch, stream) -> tuple:

@@ -420,8 +420,8 @@ class Pipeline:
 
 
 class Batch:
-    """Several beams searched by one CUDA graph of persistent work-queue
-    kernels (see aa_batch_create).  The plans must outlive the batch."""
+    """Several beams searched by one CUDA graph (see aa_batch_create and
+    aa_batch_set_branches).  The plans must outlive the batch."""
 
     def __init__(self, plans, nsamps, max_width, threshold, capacity=1 << 24, wave_budget=0):
         for p in plans:
@@ -456,6 +456,11 @@ class Batch:
 
     def info(self) -> tuple:
         return abi.aa_batch_info(self.handle)
+
+    def set_branches(self, branches: int):
+        """0: persistent work-queue kernels per stage; k >= 1: each beam's own
+        kernels on k concurrent graph branches (see aa_batch_set_branches)."""
+        abi.aa_batch_set_branches(self.handle, int(branches))
 
     def run(self, stream=None):
         abi.aa_batch_run(self.handle, _stream_handle(stream))

@@ -221,6 +221,22 @@ def batched_beams(n: int = 32, seed: int = PULSE_SEED + 2) -> list:
     return beams
 
 
+def small_beams(n: int = 128, seed: int = PULSE_SEED + 3) -> list:
+    """Many short beams (a multi-beam receiver's blocks of a few seconds):
+    channels 512 or 1024 over the same 300 MHz band, lengths U{2^15..2^16},
+    DM_max ~ U[100, 400] with clipped plans."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    beams = []
+    for i in range(n):
+        C = int(rng.choice([512, 1024]))
+        T = int(rng.integers(1 << 15, (1 << 16) + 1))
+        dm_max = float(rng.uniform(100.0, 400.0))
+        foff = -300.0 / C
+        beams.append(Workload(f"short{i}-{C}ch-{T}", C, 1508.0, foff, 64e-6, T,
+                              clipped_ska_ranges(dm_max), 8192, 6.0, 300 + i))
+    return beams
+
+
 # Record layout of a single-pulse candidate (16 bytes, the library's format).
 CANDIDATE_RECORD = np.dtype([("dm_index", "<u4"), ("t", "<u4"), ("width", "<u2"),
                              ("range", "u1"), ("reserved", "u1"), ("snr", "<f4")])

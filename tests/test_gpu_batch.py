@@ -1,5 +1,6 @@
-"""Batched beams (one CUDA graph of persistent work-queue kernels) against
-the same beams run one at a time, and the autotuner."""
+"""Batched beams (one CUDA graph: each beam's kernels on concurrent branches,
+or persistent work-queue kernels per stage) against the same beams run one
+at a time, and the autotuner."""
 import os
 
 import numpy as np
@@ -74,6 +75,34 @@ def test_batch_equals_beams_alone(oracle, budget):
     b.run()
     arr2, total2 = b.candidates()
     assert total2 == total and np.array_equal(arr2, arr)
+    b.close()
+
+
+@pytest.mark.parametrize("budget", [0, 1], ids=["one-wave", "wave-per-beam"])
+@pytest.mark.parametrize("branches", [1, 3])
+def test_branched_graph_equals_persistent(oracle, budget, branches):
+    """Every graph form (8 branches at creation, 1 or 3 branches, the
+    persistent work-queue kernels) finds the same candidates and the same
+    dedispersed series; switching re-records the graph without touching the
+    buffers."""
+    plans, data = make_beams(oracle)
+    b, arr, total = batched(plans, data, budget)
+    b.set_branches(branches)
+    b.run()
+    arr_b, total_b = b.candidates()
+    assert total_b == total and np.array_equal(arr_b, arr)
+    for i, (p, x) in enumerate(zip(plans, data)):
+        if b.info()[0] == 1 or i == len(BEAMS) - 1:  # series kept by the last wave only
+            d, nsamp = p.device_input(x)
+            ref = p.range_views(p.dedisperse_device(d, nsamp), nsamp)
+            got = p.range_views(b.dd_view(i), nsamp)
+            assert all(torch.equal(u, v) for u, v in zip(got, ref)), f"beam {i}"
+    b.set_branches(0)
+    b.run()
+    arr_p, total_p = b.candidates()
+    assert total_p == total and np.array_equal(arr_p, arr)
+    with pytest.raises(Exception):
+        b.set_branches(65)
     b.close()
 
 

@@ -1,5 +1,6 @@
-"""The batched path (one CUDA graph of persistent work-queue kernels over
-many beams) against the ORACLE, not against the single-beam GPU path.
+"""The batched path (one CUDA graph over many beams, in its default form of
+each beam's kernels on concurrent branches, and in the persistent work-queue
+form) against the ORACLE, not against the single-beam GPU path.
 
 Beams: the four small uneven beams of test_gpu_batch (64-128 channels,
 decimations 1/2/4/8/16 with the dec-16 range among them), plus two beams of
@@ -143,3 +144,22 @@ def test_dd_view_refuses_overwritten_waves(oracle):
     for g, o in zip(v, ys):
         assert np.array_equal(g.double().cpu().numpy(), o.astype(np.float64))
     b.close()
+
+
+def test_persistent_form_equals_checked_form(batch_run):
+    """The persistent work-queue form gives the candidates and the series of
+    the default form checked against the oracle above (on every row)."""
+    b, beams, arr = batch_run
+    before = [[v.clone() for v in p.range_views(b.dd_view(i), x.shape[1])]
+              for i, (_, p, x, _) in enumerate(beams)]
+    b.set_branches(0)
+    try:
+        b.run()
+        torch.cuda.synchronize()
+        arr_p, total_p = b.candidates()
+        assert total_p == len(arr) and np.array_equal(arr_p, arr)
+        for i, (_, p, x, _) in enumerate(beams):
+            after = p.range_views(b.dd_view(i), x.shape[1])
+            assert all(torch.equal(u, v) for u, v in zip(before[i], after)), f"beam {i}"
+    finally:
+        b.set_branches(8)

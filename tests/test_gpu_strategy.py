@@ -97,9 +97,11 @@ def test_grouped_has_no_staging_waits():
     assert torch.all(p.range_views(out, n)[0] == 7 * C)
 
 
-def test_grouped_in_batch():
-    """The persistent batched kernel runs grouped and direct ranges side by
-    side; every beam's candidates equal those of the beam searched alone."""
+@pytest.mark.parametrize("branches", [8, 0], ids=["branches", "persistent"])
+def test_grouped_in_batch(branches):
+    """Grouped and direct ranges side by side in a batch (each beam's kernels
+    on graph branches, or the persistent batched kernel); every beam's
+    candidates equal those of the beam searched alone."""
     from paper_1912_07704_gb300.api import Batch, candidates_from_device
     C, fch1, foff, ts, W, thr = 1024, 1508.0, -0.29296875, 64e-6, 32, 4.5
     rng = np.random.default_rng(13)
@@ -121,6 +123,7 @@ def test_grouped_in_batch():
         torch.cuda.synchronize()
         alone.append(candidates_from_device(cands, count, 1 << 16))
     b = Batch(plans, [x.shape[1] for x in xs], W, thr, capacity=1 << 18)
+    b.set_branches(branches)
     for i, x in enumerate(xs):
         b.input_view(i)[:, : x.shape[1]].copy_(torch.from_numpy(x))
     b.run()
