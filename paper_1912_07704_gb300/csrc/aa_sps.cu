@@ -51,9 +51,9 @@ constexpr int kStatsThreads = 512;
 // its bit is set.  Chunks 0-3 always; then c_0 = 4 and
 // c_{n+1} = max(c_n + 1, ceil(c_n * g16 / 16)).  Whole CTA; words past
 // nchunks are cleared.
-constexpr int kLadderWords = 65536 / kSpsSlots / 32;  // chunks of the widest search
+__host__ __device__ constexpr int ladder_words(int wpad) { return (wpad / kSpsSlots + 31) / 32; }
 __device__ __forceinline__ void fill_ladder(uint32_t* mask, int nchunks, int g16) {
-    for (int i = threadIdx.x; i < kLadderWords; i += blockDim.x) mask[i] = 0;
+    for (int i = threadIdx.x; i < (nchunks + 31) / 32; i += blockDim.x) mask[i] = 0;
     __syncthreads();
     if (threadIdx.x == 0) {
         for (int c = 0; c < min(4, nchunks); ++c) mask[c >> 5] |= 1u << (c & 31);
@@ -339,53 +339,84 @@ constexpr int NT = kSpsThreads;
 // it alone.
 constexpr float kBig = 1.2676506002282294e30f;  // 2^100
 
-// Bound of one warp over a width segment [w1, w2].  For every start slot p
-// of the warp and w in the segment, S_w(p) <= max P(ends) - min P(starts)
-// and -w f <= -w1 f (f >= 0) or -w2 f (f < 0), so SNR_w <= ub =
-// (pmax - pmin - drift) / (sigma sqrt(w1)) when positive.  Evaluated in FP32
-// with the rounding of each step bounded and added (|f| <= 1/2 since
-// m0 = round(mu); pmax - pmin is exact).
-struct WarpBound {
-    float pmin;        // min of P over the warp's valid starts (FLT_MAX: none)
-    float f;           // mu - m0
+// Block maxima of the prefix sums: Q[j] = max P[i] over i in
+// [kQSpan j, kQSpan (j+1)), for the pruning bounds of the wide widths.
+constexpr int kQSpan = 128;
+__host__ __device__ constexpr int sps_q_count(int wpad) {
+    return (kSpsTile + wpad + M + kQSpan - 1) / kQSpan;
+}
+
+// Bound of one thread's M starts over a width segment [w1, w2].  For a start
+// p in [ps, pl] (pl = ps + M - 1) and a width w, the window's end is p + w, so
+// S_w(p) <= P[end] - pmin and w >= max(w1, end - pl); -w f <= -wlo f (f >= 0)
+// or -w2 f (f < 0).  So SNR_w(p) <= (P[end] - pmin - drift) / (sigma sqrt(wlo))
+// for every end, maximised over the ends:
+//  * w1 <= kQSpan: the ends [ps + w1, pl + w2] read one by one (as aligned
+//    16-byte vectors from ps + w1 - 1, a superset), wlo = w1;
+//  * wider: per block j of Q overlapping the ends, Q[j] with
+//    wlo = max(w1, kQSpan j - pl).
+// FP32 with the rounding of each step bounded and added (|f| <= 1/2 since
+// m0 = round(mu); the differences of the exact integer sums P are exact;
+// rsqrtf within 2 ulp), then widened by 1e-4 relative and absolute.
+struct ThreadBound {
+    const float* Q;
+    float pmin;       // min of P over the thread's valid starts (FLT_MAX: none)
+    float f;          // mu - m0
     float inv_sigma;
-    float cut;         // blocks bounded below this are skipped (-FLT_MAX: none)
-    const double* rsqrt_w;
-    int max_width, ylen, p_first;
-    bool active;       // pruning enabled
+    float cut;        // segments bounded below this are skipped (-FLT_MAX: none)
+    int max_width, ylen, nq, ps;
+    bool active;      // pruning enabled
 };
 
-__device__ __forceinline__ float warp_segment_bound(const float* __restrict__ P, const WarpBound& b,
-                                                    int w1, int w2) {
-    const int lane = threadIdx.x & 31;
-    const int lo = b.p_first + w1, hi = min(b.ylen - 1, b.p_first + M * 32 - 1 + w2);
-    float pmax = -FLT_MAX;
-    for (int j = lo + lane; j <= hi; j += 32) pmax = fmaxf(pmax, P[j]);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) pmax = fmaxf(pmax, __shfl_xor_sync(0xffffffffu, pmax, o));
-    const float drift = b.f >= 0.0f ? (float)w1 * b.f : (float)w2 * b.f;
-    const float diff = pmax - b.pmin;
-    const float rs = (float)b.rsqrt_w[w1 - 1];
+__device__ __forceinline__ float piece_bound(float top, const ThreadBound& b, int wlo, int whi) {
+    const float drift = b.f >= 0.0f ? (float)wlo * b.f : (float)whi * b.f;
+    const float diff = top - b.pmin;
+    const float rs = rsqrtf((float)wlo);
     // 6 roundings of at most 2^-24 relative each on magnitudes <= |diff| + |drift|
     const float slack = (fabsf(diff) + fabsf(drift)) * b.inv_sigma * rs * 1e-6f + 1e-6f;
-    const float ub = (diff - drift) * b.inv_sigma * rs + slack;
-    return ub * (1.0f + 1e-4f) + 1e-4f;
+    return (diff - drift) * b.inv_sigma * rs + slack;
+}
+
+__device__ __forceinline__ float thread_segment_bound(const float* __restrict__ P, const ThreadBound& b,
+                                                      int w1, int w2) {
+    if (b.pmin == FLT_MAX) return -FLT_MAX;
+    const int pl = b.ps + M - 1;
+    const int hi = min(b.ylen - 1, pl + w2);
+    float ub;
+    if (w1 <= kQSpan) {
+        // ylen is a multiple of 4, so the last vector ends inside the staged series
+        float pmax = -FLT_MAX;
+        for (int e = (b.ps + w1 - 1) & ~3; e <= hi; e += 4) {
+            const float4 v = *reinterpret_cast<const float4*>(P + e);
+            pmax = fmaxf(fmaxf(pmax, fmaxf(v.x, v.y)), fmaxf(v.z, v.w));
+        }
+        ub = piece_bound(pmax, b, w1, w2);
+    } else {
+        ub = -FLT_MAX;
+        const int j1 = min(b.nq - 1, hi / kQSpan);
+        for (int j = (b.ps + w1) / kQSpan; j <= j1; ++j)
+            ub = fmaxf(ub, piece_bound(b.Q[j], b, max(w1, j * kQSpan - pl), w2));
+    }
+    return ub + fabsf(ub) * 1e-4f + 1e-4f;
 }
 
 // Main loop.  With pruning, the widths after the first chunk are checked in
 // power-of-two blocks [w0+1, 2 w0] (w0 = 16, 32, ...), and inside a block
 // that survives and spans more than 128 widths, in segments [w0+1, w0+128].
-// A block or segment is skipped when its warp bound is below max(cut, min
-// over the warp's slots of the running B): below the running B it can
-// change neither B nor C of any slot (exact for every slot); below the
+// A thread can skip a block or segment when its bound is below max(cut, min
+// over its slots of the running B): below the running B it can change
+// neither B nor C of any of its slots (exact for every slot); below the
 // threshold cut it can only change sub-threshold values (exact for every
-// B >= threshold and for every peak decision).  Widths are visited in
-// increasing order, so the running B of the small widths prunes the wide
-// ones, and a warp far before a bright pulse evaluates only the segments
-// whose window ends can reach it.
+// B >= threshold and for every peak decision).  The warp skips it when all
+// of its threads can (the warp evaluates chunks in lockstep; evaluating a
+// chunk a thread could skip changes nothing of the above).  Widths are
+// visited in increasing order, so the running B of the small widths prunes
+// the wide ones; a thread before a bright pulse evaluates the widths whose
+// windows end near the pulse, not the wider ones, whose bound the pulse's
+// SNR at the narrower width already exceeds.
 __device__ __forceinline__ int boxcar_prefix(const float* __restrict__ P,
                                              const float2* __restrict__ tab, int wpad,
-                                             const float (&base)[M], const WarpBound& bnd,
+                                             const float (&base)[M], const ThreadBound& bnd,
                                              const uint32_t* lmask, float (&B)[M], int (&C)[M]) {
     const float* pb = P + M * threadIdx.x;
     int evaluated = 0;
@@ -399,20 +430,16 @@ __device__ __forceinline__ int boxcar_prefix(const float* __restrict__ P,
         const bool blk = (w0 & (w0 - 1)) == 0;  // first chunk of a power-of-two block
         if (bnd.active && w0 >= 16 && (blk || (w0 >= 2 * kSeg && (w0 & (kSeg - 1)) == 0))) {
             int w_end = blk ? 2 * w0 : w0 + kSeg;
-            bool skip = bnd.pmin == FLT_MAX;
-            if (!skip) {
-                float bmin = B[0];
+            float bmin = B[0];
 #pragma unroll
-                for (int i = 1; i < M; ++i) bmin = fminf(bmin, B[i]);
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1)
-                    bmin = fminf(bmin, __shfl_xor_sync(0xffffffffu, bmin, o));
-                const float floor_b = fmaxf(bnd.cut, bmin);
-                skip = warp_segment_bound(P, bnd, w0 + 1, min(w_end, bnd.max_width)) < floor_b;
-                if (!skip && blk && w0 >= 2 * kSeg) {
-                    w_end = w0 + kSeg;
-                    skip = warp_segment_bound(P, bnd, w0 + 1, min(w_end, bnd.max_width)) < floor_b;
-                }
+            for (int i = 1; i < M; ++i) bmin = fminf(bmin, B[i]);
+            const float floor_b = fmaxf(bnd.cut, bmin);
+            bool skip = !__any_sync(0xffffffffu,
+                                    thread_segment_bound(P, bnd, w0 + 1, min(w_end, bnd.max_width)) >= floor_b);
+            if (!skip && blk && w0 >= 2 * kSeg) {
+                w_end = w0 + kSeg;
+                skip = !__any_sync(0xffffffffu,
+                                   thread_segment_bound(P, bnd, w0 + 1, min(w_end, bnd.max_width)) >= floor_b);
             }
             if (skip) {
                 w0 = w_end - M;  // next block or segment
@@ -490,13 +517,15 @@ __host__ __device__ constexpr int sps_region_bytes(int wpad) {
 __device__ __forceinline__ void boxcar_block(const SpsArgs& a, int ntiles, int64_t bid, float* sm) {
     __shared__ long long scratch[2 * NT / 32];
     __shared__ unsigned long long s_base;
-    __shared__ uint32_t s_ladder[kLadderWords];
-    const uint32_t* lmask = a.ladder_g16 > 0 ? s_ladder : nullptr;
-    if (lmask) fill_ladder(s_ladder, a.wpad / M, a.ladder_g16);  // visible after the staging barrier
     const int wpad = a.wpad;
     const int ylen = kSpsTile + wpad + M;
     float* ys = sm;
     float2* tab = reinterpret_cast<float2*>(sm + ((ylen + 3) & ~3));
+    float* Qs = sm + ((ylen + 3) & ~3) + sps_region_bytes(wpad) / 4;
+    const int nq = sps_q_count(wpad);
+    uint32_t* s_ladder = reinterpret_cast<uint32_t*>(Qs + ((nq + 3) & ~3));
+    const uint32_t* lmask = a.ladder_g16 > 0 ? s_ladder : nullptr;
+    if (lmask) fill_ladder(s_ladder, wpad / M, a.ladder_g16);  // visible after the staging barrier
     const int row = (int)(bid / ntiles);
     const int64_t tile = bid - (int64_t)row * ntiles;
     const int64_t t0 = tile * kSpsOwned;
@@ -574,6 +603,20 @@ __device__ __forceinline__ void boxcar_block(const SpsArgs& a, int ntiles, int64
         }
         __syncthreads();
         const float* P = ys;
+        if (a.prune) {  // block maxima Q, one warp per block
+            for (int j = warp; j < nq; j += NT / 32) {
+                float m = -FLT_MAX;
+#pragma unroll
+                for (int u = 0; u < kQSpan / 32; ++u) {
+                    const int i = j * kQSpan + u * 32 + lane;
+                    if (i < ylen) m = fmaxf(m, P[i]);
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+                if (lane == 0) Qs[j] = m;
+            }
+            __syncthreads();
+        }
         float base[M];
         float pmin = FLT_MAX;
 #pragma unroll
@@ -583,17 +626,16 @@ __device__ __forceinline__ void boxcar_block(const SpsArgs& a, int ntiles, int64
             base[i] = valid ? P[p] : kBig;
             if (valid) pmin = fminf(pmin, base[i]);
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) pmin = fminf(pmin, __shfl_xor_sync(0xffffffffu, pmin, o));
-        WarpBound bnd;
+        ThreadBound bnd;
+        bnd.Q = Qs;
         bnd.pmin = pmin;
         bnd.f = (float)(st.mu - (double)m0);
         bnd.inv_sigma = (float)st.inv_sigma;
         bnd.cut = a.threshold > 0.0f ? a.threshold - 1e-3f : -FLT_MAX;
-        bnd.rsqrt_w = a.rsqrt_w;
         bnd.max_width = a.max_width;
         bnd.ylen = ylen;
-        bnd.p_first = M * 32 * warp;
+        bnd.nq = nq;
+        bnd.ps = M * threadIdx.x;
         bnd.active = a.prune != 0;
         const int chunks = boxcar_prefix(P, tab, wpad, base, bnd, lmask, B, C);
         if (a.evaluated && (threadIdx.x & 31) == 0)
@@ -809,7 +851,8 @@ cudaError_t launch_rsqrt_table(double* t, int wpad, cudaStream_t s) {
 
 size_t sps_boxcar_smem(int wpad) {
     const int ylen = kSpsTile + wpad + M;
-    return (size_t)((ylen + 3) & ~3) * 4 + (size_t)sps_region_bytes(wpad);
+    return (size_t)((ylen + 3) & ~3) * 4 + (size_t)sps_region_bytes(wpad) +
+           (size_t)((sps_q_count(wpad) + 3) & ~3) * 4 + (size_t)ladder_words(wpad) * 4;
 }
 
 cudaError_t launch_sps_boxcar(const SpsArgs& a, cudaStream_t s) {
