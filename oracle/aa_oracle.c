@@ -344,6 +344,74 @@ void oracle_boxcar_widths(const int64_t* y, int64_t n, double mu, double sigma, 
     }
 }
 
+/* Decimated width ladder (approximate search for wide boxcars: the cited
+ * search method, Sec. 1, evaluates wide boxcars on the series decimated by
+ * pairs).  Level 0: widths 1..min(W0, W) of the windows starting at t.
+ * Level k >= 1 (while W0 * 2^(k-1) < W): widths w = m * 2^k with
+ * W0/2 < m <= W0 and w <= W, of the windows starting at the level-k grid
+ * point s = floor(t / 2^k) * 2^k <= t, i.e. m consecutive samples of the
+ * series decimated k times by pairs; every window inside [0, n).  SNR as in
+ * oracle_boxcar; widths are visited in increasing order (level 0, then
+ * level 1, ...), so ties go to the smallest width.  B, smallest maximising
+ * width and margin as oracle_boxcar; sbest = the start of the maximising
+ * window (t, or the grid point of its level).  Returns -1 if the prefix
+ * sums cannot be allocated, else 0. */
+int oracle_boxcar_dec(const int64_t* y, int64_t n, double mu, double sigma, int32_t W, int32_t W0,
+                      int64_t t0, int64_t t1, double* B, int32_t* wbest, double* margin,
+                      int64_t* sbest)
+{
+    int64_t* P = (int64_t*)malloc((size_t)(n + 1) * sizeof(int64_t));
+    if (!P) return -1;
+    P[0] = 0;
+    for (int64_t i = 0; i < n; ++i) P[i + 1] = P[i] + y[i];
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t t = t0; t < t1; ++t) {
+        int64_t k0 = t - t0;
+        if (sigma == 0.0) {
+            B[k0] = 0.0;
+            wbest[k0] = 1;
+            margin[k0] = INFINITY;
+            sbest[k0] = t;
+            continue;
+        }
+        double best = -INFINITY, second = -INFINITY;
+        int32_t bw = 0;
+        int64_t bs = t;
+        for (int64_t w = 1; w <= (int64_t)W0 && w <= (int64_t)W && t + w <= n; ++w) {
+            double snr = ((double)(P[t + w] - P[t]) - (double)w * mu) / (sigma * sqrt((double)w));
+            if (snr > best) {
+                second = best;
+                best = snr;
+                bw = (int32_t)w;
+            } else if (snr > second) {
+                second = snr;
+            }
+        }
+        for (int k = 1; ((int64_t)W0 << (k - 1)) < (int64_t)W; ++k) {
+            int64_t s = (t >> k) << k;
+            for (int64_t m = W0 / 2 + 1; m <= W0; ++m) {
+                int64_t w = m << k;
+                if (w > (int64_t)W || s + w > n) break;
+                double snr = ((double)(P[s + w] - P[s]) - (double)w * mu) / (sigma * sqrt((double)w));
+                if (snr > best) {
+                    second = best;
+                    best = snr;
+                    bw = (int32_t)w;
+                    bs = s;
+                } else if (snr > second) {
+                    second = snr;
+                }
+            }
+        }
+        B[k0] = best;
+        wbest[k0] = bw;
+        margin[k0] = best - second;
+        sbest[k0] = bs;
+    }
+    free(P);
+    return 0;
+}
+
 /* Thresholded local maxima of B over [0, n): returns the number found and
  * writes up to cap indices. */
 int64_t oracle_peaks(const double* B, int64_t n, double thr, int64_t* out_t, int64_t cap)

@@ -79,6 +79,8 @@ def lib():
         L.oracle_boxcar_widths.argtypes = [vp, i64, f64, f64, i32, vp, i64, i64, vp, vp, vp]
         L.oracle_boxcar_widths.restype = None
         L.oracle_boxcar.restype = None
+        L.oracle_boxcar_dec.argtypes = [vp, i64, f64, f64, i32, i32, i64, i64, vp, vp, vp, vp]
+        L.oracle_boxcar_dec.restype = ctypes.c_int
         L.oracle_peaks.argtypes = [vp, i64, f64, vp, i64]
         L.oracle_peaks.restype = i64
         L.oracle_forward_f64.argtypes = [vp, i32, i64, vp, vp, i64, vp]
@@ -233,9 +235,10 @@ def ladder_widths(W: int, g16: int) -> np.ndarray:
 
 
 def boxcar(y: np.ndarray, mu: float, sigma: float, W: int, t0: int = 0, t1: int | None = None,
-           wset: np.ndarray | None = None):
+           wset: np.ndarray | None = None, dec_w0: int | None = None):
     """(B, wbest, margin) for t in [t0, t1); wset: optional bool mask of the
-    widths 1..W taking part."""
+    widths 1..W taking part; dec_w0: the decimated width ladder with W0 =
+    dec_w0 base widths (oracle_boxcar_dec), instead of every width."""
     y = np.ascontiguousarray(y, dtype=np.int64)
     n = y.size
     t1 = n if t1 is None else t1
@@ -243,6 +246,9 @@ def boxcar(y: np.ndarray, mu: float, sigma: float, W: int, t0: int = 0, t1: int 
     B = np.empty(m, np.float64)
     wb = np.empty(m, np.int32)
     mg = np.empty(m, np.float64)
+    if dec_w0:
+        assert wset is None
+        return boxcar_dec(y, mu, sigma, W, dec_w0, t0, t1)[:3]
     if m and wset is None:
         lib().oracle_boxcar(_ptr(y), n, float(mu), float(sigma), int(W), int(t0), int(t1),
                             _ptr(B), _ptr(wb), _ptr(mg))
@@ -252,6 +258,25 @@ def boxcar(y: np.ndarray, mu: float, sigma: float, W: int, t0: int = 0, t1: int 
         lib().oracle_boxcar_widths(_ptr(y), n, float(mu), float(sigma), int(W), _ptr(ws), int(t0),
                                    int(t1), _ptr(B), _ptr(wb), _ptr(mg))
     return B, wb, mg
+
+
+def boxcar_dec(y: np.ndarray, mu: float, sigma: float, W: int, W0: int, t0: int = 0,
+               t1: int | None = None):
+    """(B, wbest, margin, start of the maximising window) of the decimated
+    width ladder with W0 base widths (oracle_boxcar_dec) for t in [t0, t1)."""
+    assert W0 >= 2 and W0 % 2 == 0
+    y = np.ascontiguousarray(y, dtype=np.int64)
+    n = y.size
+    t1 = n if t1 is None else t1
+    m = max(0, t1 - t0)
+    B = np.empty(m, np.float64)
+    wb = np.empty(m, np.int32)
+    mg = np.empty(m, np.float64)
+    sb = np.empty(m, np.int64)
+    if m and lib().oracle_boxcar_dec(_ptr(y), n, float(mu), float(sigma), int(W), int(W0), int(t0),
+                                     int(t1), _ptr(B), _ptr(wb), _ptr(mg), _ptr(sb)) != 0:
+        raise MemoryError("oracle_boxcar_dec: prefix sums")
+    return B, wb, mg, sb
 
 
 def peaks_thr(B: np.ndarray, thr: float) -> np.ndarray:
@@ -272,12 +297,13 @@ class Candidate:
 
 
 def search_row(y: np.ndarray, W: int, thr: float, dm_index: int, rng: int,
-               t_lo: int = 0, t_hi: int | None = None, clip=None, wset=None):
+               t_lo: int = 0, t_hi: int | None = None, clip=None, wset=None, dec_w0=None):
     """Candidates of one DM series with t in [t_lo, t_hi).
 
     Returns (candidates, B, wbest, mu, sigma) with B/wbest over [t_lo, t_hi).
     clip = (c16, max_iters) takes mu, sigma from iterative k-sigma clipping;
-    wset restricts the widths (bool mask over 1..W, e.g. ladder_widths).
+    wset restricts the widths (bool mask over 1..W, e.g. ladder_widths);
+    dec_w0 selects the decimated width ladder with that many base widths.
     Rows with sigma == 0 have B = 0 and no candidates.  Near-decision entries
     (|B - thr| < FRAGILE_THR, neighbour or width-argmax margin < FRAGILE_CMP)
     are flagged fragile; entries just below the threshold that could flip
@@ -288,7 +314,11 @@ def search_row(y: np.ndarray, W: int, thr: float, dm_index: int, rng: int,
     t_hi = n if t_hi is None else min(t_hi, n)
     mu, sigma = row_moments(y, clip)
     a, b = max(0, t_lo - 1), min(n, t_hi + 1)
-    B, wb, mg = boxcar(y, mu, sigma, W, a, b, wset)
+    if dec_w0:
+        B, wb, mg, sb = boxcar_dec(y, mu, sigma, W, dec_w0, a, b)
+    else:
+        B, wb, mg = boxcar(y, mu, sigma, W, a, b, wset)
+        sb = np.arange(a, b, dtype=np.int64)  # every window starts at its own t
     cands = []
     if sigma == 0.0 or t_hi <= t_lo:
         return cands, B[t_lo - a:t_hi - a], wb[t_lo - a:t_hi - a], mu, sigma
@@ -304,8 +334,12 @@ def search_row(y: np.ndarray, W: int, thr: float, dm_index: int, rng: int,
         left = B[k - 1] if t > 0 else -np.inf
         right = B[k + 1] if t + 1 < n else -np.inf
         is_peak = t in peak_set
-        near = (abs(v - thr) < FRAGILE_THR or abs(v - left) < FRAGILE_CMP
-                or abs(v - right) < FRAGILE_CMP)
+        # a neighbour holding the same window (a decimated-ladder plateau) is
+        # equal by construction on both sides, not a near decision
+        same_l = t > 0 and k > 0 and sb[k - 1] == sb[k] and wb[k - 1] == wb[k]
+        same_r = t + 1 < n and k + 1 < len(B) and sb[k + 1] == sb[k] and wb[k + 1] == wb[k]
+        near = (abs(v - thr) < FRAGILE_THR or (abs(v - left) < FRAGILE_CMP and not same_l)
+                or (abs(v - right) < FRAGILE_CMP and not same_r))
         if is_peak or near:
             fragile = near or mg[k] < FRAGILE_CMP
             cands.append(Candidate(dm_index, t, int(wb[k]), rng, float(v), bool(fragile)))
