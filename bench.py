@@ -323,6 +323,8 @@ def bench_ours(args):
         plan.set_sps_clip(c16, iters)
     if args.sps_ladder:
         plan.set_sps_ladder(args.sps_ladder)
+    if args.sps_dec:
+        plan.set_sps_decimated(args.sps_dec)
     plan.bind(local)
     info = plan.query(w.nsamp, w.max_width)
     x = build_input(plan, w, "cuda")
@@ -542,7 +544,9 @@ def bench_ours(args):
                                       f"<= {args.sps_clip.split(',')[1]} passes"
                                       if args.sps_clip else "plain mean and sigma"),
                        "widths": (f"sparse ladder, growth {args.sps_ladder}/16 (approximate)"
-                                  if args.sps_ladder else "every width 1..W"),
+                                  if args.sps_ladder else
+                                  f"decimated ladder, {args.sps_dec} base widths (approximate)"
+                                  if args.sps_dec else "every width 1..W"),
                        "dedispersion": [_strategy_name(abi.aa_plan_range(plan.handle, nsamp, r))
                                         for r in range(len(w.ranges))],
                        "l2": (f"inputs larger than L2 ({alg['in_bytes'] / 1e9:.2f} GB filterbank, "
@@ -906,6 +910,8 @@ def main():
                     help="batched workloads: graph forms to time (0 = persistent work-queue kernels, "
                          "k = each beam's kernels on k concurrent branches); the first is reported "
                          "(8 = the library's default), the others are listed beside it")
+    ap.add_argument("--sps-dec", type=int, default=0,
+                    help="W0: decimated boxcar width ladder with W0 base widths (approximate), e.g. 32")
     ap.add_argument("--sps-ladder", type=int, default=0,
                     help="G16: sparse boxcar width ladder of growth G16/16 (approximate), e.g. 24")
     ap.add_argument("--fused", action="store_true",

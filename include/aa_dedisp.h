@@ -326,8 +326,28 @@ aa_status aa_plan_set_strategy(aa_plan* plan, int32_t r, int32_t strategy);
  * the widths taking part and a candidate's width the smallest of them
  * reaching it.  growth_x16 = 0 restores every width 1..W (the default);
  * otherwise it must lie in [17, 64].  Applies to the searches started (and
- * batches created) after the call.  AA_ERR_ARG for other values. */
+ * batches created) after the call.  AA_ERR_ARG for other values,
+ * AA_ERR_CONFIG while the decimated ladder (aa_plan_set_sps_decimated) is on. */
 aa_status aa_plan_set_sps_ladder(aa_plan* plan, int32_t growth_x16);
+
+/* Decimated width ladder for the single-pulse search: an approximation for
+ * wide boxcars (the cited search method evaluates them on the dedispersed
+ * series decimated by pairs; Sec. 1 names boxcar filters with peak finding).
+ * With base_widths = W0: every width 1..min(W0, W) at every start t
+ * (level 0), and for each level k >= 1 with W0 * 2^(k-1) < W the widths
+ * m * 2^k, W0/2 < m <= W0, m * 2^k <= W, of the window that starts at the
+ * level-k grid point floor(t / 2^k) * 2^k <= t (m samples of the series
+ * decimated k times by pairs), each window inside [0, L).  B(t) is the
+ * largest SNR over those windows (SNR as in the exhaustive search, with the
+ * row's mean and standard deviation), a candidate's width the smallest width
+ * reaching it; a wide window's value holds over its level's grid cell, and
+ * a candidate sits at the first sample of the cell (peaks as usual: B >= thr,
+ * B(t) > B(t-1), B(t) >= B(t+1)).  Evaluates about W0 + W0/2 widths per start
+ * instead of W.  base_widths = 0 restores every width (the default);
+ * otherwise a power of two in [16, 256].  AA_ERR_ARG for other values,
+ * AA_ERR_CONFIG while the sparse ladder (aa_plan_set_sps_ladder) is on.
+ * Applies to searches started (and batches created) after the call. */
+aa_status aa_plan_set_sps_decimated(aa_plan* plan, int32_t base_widths);
 
 /* Robust statistics for the single-pulse search (outlier rejection).  The
  * mean and standard deviation that normalise each dedispersed series' SNR

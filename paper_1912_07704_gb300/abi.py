@@ -137,6 +137,7 @@ _SIG = {
     "aa_plan_set_fdmt": (ctypes.c_int, [_P, _I32]),
     "aa_plan_effective_shifts": (ctypes.c_int, [_P, _I32, _P, _I64]),
     "aa_plan_set_sps_ladder": (ctypes.c_int, [_P, _I32]),
+    "aa_plan_set_sps_decimated": (ctypes.c_int, [_P, _I32]),
     "aa_postprocess_ws_bytes": (ctypes.c_int, [_P, _I64, _I32, _I64,
                                                ctypes.POINTER(ctypes.c_size_t)]),
     "aa_sps_order_device": (ctypes.c_int, [_P, _I64, _I32, _P, _P, _P, _I64, _P, _P,
@@ -374,6 +375,10 @@ def aa_corner_turn_device(d_tm: int, nsamp: int, nchans: int, tm_stride: int, d_
 
 def aa_plan_set_sps_ladder(plan, growth_x16: int) -> None:
     check(lib().aa_plan_set_sps_ladder(plan, int(growth_x16)), "aa_plan_set_sps_ladder")
+
+
+def aa_plan_set_sps_decimated(plan, base_widths: int) -> None:
+    check(lib().aa_plan_set_sps_decimated(plan, base_widths), "aa_plan_set_sps_decimated")
 
 
 def aa_plan_effective_shifts(plan, r: int, ndm: int, nchans: int):

@@ -104,6 +104,10 @@ class Plan:
         """Sparse boxcar width ladder for later searches (0: every width)."""
         abi.aa_plan_set_sps_ladder(self.handle, growth_x16)
 
+    def set_sps_decimated(self, base_widths: int) -> None:
+        """Decimated boxcar width ladder for later searches (0: every width)."""
+        abi.aa_plan_set_sps_decimated(self.handle, base_widths)
+
     def set_subband(self, r: int, band_channels: int, coarse_trials: int) -> None:
         """Sub-band dedispersion (an approximation) for range r."""
         abi.aa_plan_set_subband(self.handle, r, band_channels, coarse_trials)

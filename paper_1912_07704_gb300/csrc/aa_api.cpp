@@ -458,6 +458,11 @@ aa_status aa_sps_search_device(const aa_plan* p, int64_t nsamp, const float* d_d
         set_error("workspace %zu bytes < required %lld", ws_bytes, (long long)L.sps_ws);
         return AA_ERR_ARG;
     }
+    if (sps_boxcar_smem_for(max_width, L.wpad, p->dec_w0) > kMaxBoxcarSmem) {
+        set_error("max_width %d needs %zu bytes of shared memory per boxcar tile (at most %zu)", max_width,
+                  sps_boxcar_smem_for(max_width, L.wpad, p->dec_w0), kMaxBoxcarSmem);
+        return AA_ERR_CONFIG;
+    }
     if (p->clip_iters > 0)
         for (int64_t len : L.length)
             if (len >= (int64_t(1) << 31)) {  // keeps the clipping test inside 128-bit integers
@@ -508,6 +513,7 @@ aa_status aa_sps_search_device(const aa_plan* p, int64_t nsamp, const float* d_d
         a.clip_c16 = p->clip_c16;
         a.clip_iters = p->clip_iters;
         a.ladder_g16 = p->ladder_g16;
+        a.dec_w0 = p->dec_w0;
         a.err = err;
         a.chunks = chunks;
         a.nchunks = nchunks;

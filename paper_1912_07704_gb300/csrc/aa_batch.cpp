@@ -58,6 +58,7 @@ struct WaveTables {
     int* d_bx_ntiles = nullptr;
     unsigned long long* d_queues = nullptr;  // 6 counters: 4 dedispersion variants, stats, boxcar
     size_t dd_smem[4] = {0, 0, 0, 0};
+    size_t bx_smem = 0;  // the largest boxcar shared memory of the wave's descriptors
 };
 
 }  // namespace
@@ -171,7 +172,7 @@ cudaError_t capture_graph(aa_batch* b) {
                                                 T.dd_smem[sg], &T.d_queues[sg], b->grid_dd, sg >= 2, (sg & 1) + 1, cs));
                 chk(launch_sps_stats_batch(T.d_sps, T.d_st_first, (int)T.sps.size(), &T.d_queues[4],
                                            b->grid_st, cs));
-                chk(launch_sps_boxcar_batch(T.d_sps, T.d_bx_first, T.d_bx_ntiles, (int)T.sps.size(), b->wpad,
+                chk(launch_sps_boxcar_batch(T.d_sps, T.d_bx_first, T.d_bx_ntiles, (int)T.sps.size(), T.bx_smem,
                                             &T.d_queues[5], b->grid_bx, cs));
                 continue;
             }
@@ -439,6 +440,8 @@ aa_status aa_batch_create(aa_plan* const* plans, const int64_t* nsamps, int32_t 
                 s.clip_c16 = pl.clip_c16;
                 s.clip_iters = pl.clip_iters;
                 s.ladder_g16 = pl.ladder_g16;
+                s.dec_w0 = pl.dec_w0;
+                T.bx_smem = std::max(T.bx_smem, sps_boxcar_smem_for(s.max_width, s.wpad, s.dec_w0));
                 s.beam = bi;
                 s.chunks = b->d_chunks;
                 s.nchunks = &b->d_counts[1];

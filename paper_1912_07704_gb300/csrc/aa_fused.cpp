@@ -211,6 +211,7 @@ aa_status aa_search_fused_device(const aa_plan* p, const uint8_t* d_in, int64_t 
             sa.clip_c16 = p->clip_c16;
             sa.clip_iters = p->clip_iters;
             sa.ladder_g16 = p->ladder_g16;
+            sa.dec_w0 = p->dec_w0;
             sa.err = err;
             sa.chunks = reinterpret_cast<CandChunk*>(sps + L.chunk_offset);
             sa.nchunks = reinterpret_cast<unsigned long long*>(sps + kChunkCounterOffset);

@@ -176,6 +176,8 @@ struct aa_plan {
     int32_t clip_c16 = 0, clip_iters = 0;
     // boxcar widths: 0 every width 1..W, else the sparse ladder of growth ladder_g16 / 16
     int32_t ladder_g16 = 0;
+    // decimated width ladder with dec_w0 base widths (0: off)
+    int32_t dec_w0 = 0;
     int device = -1;
     bool ready = false;
     void* d_tables = nullptr;
@@ -348,6 +350,7 @@ struct SpsArgs {
     int32_t clip_c16;       // k-sigma clipping of the statistics, k = clip_c16 / 16
     int32_t clip_iters;     // clipping passes (0: plain statistics)
     int32_t ladder_g16;     // sparse width ladder growth x16 (0: every width)
+    int32_t dec_w0;         // decimated width ladder base widths (0: off)
     int32_t beam;           // beam id stored in candidate records (batched mode)
     unsigned long long* evaluated;  // width-samples actually evaluated (instrumentation)
     CandChunk* chunks;      // chunk headers (all ranges)
@@ -362,10 +365,14 @@ cudaError_t launch_sps_boxcar(const SpsArgs& a, cudaStream_t s);
 cudaError_t launch_sps_stats_batch(const SpsArgs* d_descs, const int64_t* d_first, int ndesc,
                                    unsigned long long* d_queue, int grid, cudaStream_t s);
 cudaError_t launch_sps_boxcar_batch(const SpsArgs* d_descs, const int64_t* d_first,
-                                    const int* d_ntiles, int ndesc, int wpad,
+                                    const int* d_ntiles, int ndesc, size_t smem,
                                     unsigned long long* d_queue, int grid, cudaStream_t s);
 int sps_boxcar_tiles(int64_t length);
 size_t sps_boxcar_smem(int wpad);
+// dynamic shared memory of the boxcar kernel that serves (max_width, wpad,
+// dec_w0): the decimated ladder's when dec_w0 > 0
+size_t sps_boxcar_smem_for(int32_t max_width, int32_t wpad, int32_t dec_w0);
+constexpr size_t kMaxBoxcarSmem = 227 * 1024;
 cudaError_t launch_rsqrt_table(double* t, int wpad, cudaStream_t s);
 
 // Candidate runs moved into their final order: run i copies n[i] records

@@ -734,7 +734,26 @@ aa_status aa_plan_set_sps_ladder(aa_plan* p, int32_t growth_x16) {
         set_error("growth_x16 %d: 0 or within [17, 64]", growth_x16);
         return AA_ERR_ARG;
     }
+    if (growth_x16 != 0 && p->dec_w0 != 0) {
+        set_error("the decimated width ladder is on: switch it off first");
+        return AA_ERR_CONFIG;
+    }
     p->ladder_g16 = growth_x16;
+    return AA_OK;
+}
+
+aa_status aa_plan_set_sps_decimated(aa_plan* p, int32_t base_widths) {
+    clear_error();
+    if (!p) { set_error("plan is NULL"); return AA_ERR_ARG; }
+    if (base_widths != 0 && (base_widths < 16 || base_widths > 256 || (base_widths & (base_widths - 1)))) {
+        set_error("base_widths %d: 0 or a power of two within [16, 256]", base_widths);
+        return AA_ERR_ARG;
+    }
+    if (base_widths != 0 && p->ladder_g16 != 0) {
+        set_error("the sparse width ladder is on: switch it off first");
+        return AA_ERR_CONFIG;
+    }
+    p->dec_w0 = base_widths;
     return AA_OK;
 }
 

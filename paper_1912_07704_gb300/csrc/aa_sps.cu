@@ -763,6 +763,368 @@ __global__ void __launch_bounds__(NT, 2) sps_boxcar_kernel(SpsArgs a, int ntiles
     boxcar_block(a, ntiles, blockIdx.x, sm);
 }
 
+constexpr int kMaxDecLevels = 16;
+
+// ------------------------------------------------------------ decimated ladder
+// Approximate search for wide boxcars (the cited search evaluates them on the
+// series decimated by pairs, Sec. 1).  Level 0: widths 1..min(W0, W) of the
+// windows starting at t, evaluated as the exhaustive search's first chunks.
+// Level k >= 1 (while W0 2^(k-1) < W): widths w = m 2^k, W0/2 < m <= W0,
+// w <= W, of the window starting at the level-k grid point
+// s = floor(t / 2^k) 2^k <= t (m samples of the series decimated k times by
+// pairs).  Every level comes from the tile's one full-rate prefix sum P:
+// S = P[s + w] - P[s], exact.  B(t) = the largest SNR over level 0 at t and
+// each level's window at its grid point, levels in increasing width (ties to
+// the smallest width); the width of a level-k maximum is known directly, that
+// of a level-0 maximum is resolved as in the exhaustive search.
+//
+// Shared memory: the staged series with a left halo H >= 2^K (a slot's
+// level-K grid point lies up to 2^K - 1 samples before it), the compact width
+// table (level 0, then W0/2 entries per level), and a region that holds the
+// levels' strided prefix sums P_k and grid maxima B_k, then B(t), the
+// candidate list and the direct widths.
+struct DecLayout {
+    int K, H, W0, W0e, wpad0, ylen4, ntab;
+    int npk, nbk;             // entries of all levels' P_k and B_k (upper bounds for any tile)
+    int tab_off, reg_off;     // in floats
+    size_t bytes;
+};
+__host__ __device__ inline int dec_level_points(int k) { return ((kSpsTile - 1) >> k) + 2; }
+__host__ __device__ inline DecLayout dec_layout(int W, int W0) {
+    DecLayout d{};
+    d.W0 = W0;
+    d.K = 0;
+    while ((W0 << d.K) < W) ++d.K;
+    d.H = d.K > 0 ? ((1 << d.K) > 16 ? (1 << d.K) : 16) : 0;
+    d.W0e = W0 < W ? W0 : W;
+    d.wpad0 = (d.W0e + M - 1) / M * M;
+    d.ylen4 = (d.H + kSpsTile + W + M + 3) & ~3;
+    d.ntab = d.wpad0 + d.K * (W0 / 2);
+    d.npk = d.nbk = 0;
+    for (int k = 1; k <= d.K; ++k) {
+        d.nbk += dec_level_points(k);
+        d.npk += dec_level_points(k) + W0;
+    }
+    const int reg_a = d.npk * 4 + d.nbk * 4 + d.nbk;       // P_k, B_k (float), winning m (u8)
+    const int reg_b = kSpsTile * 4 + kSpsTile * 4 + kSpsTile * 2;  // B(t), candidates, direct widths
+    d.tab_off = d.ylen4;
+    d.reg_off = d.tab_off + ((d.ntab * 2 + 3) & ~3);
+    d.bytes = (size_t)d.reg_off * 4 + (size_t)(((reg_a > reg_b ? reg_a : reg_b) + 15) & ~15);
+    return d;
+}
+
+__device__ __forceinline__ void boxcar_dec_block(const SpsArgs& a, int ntiles, int64_t bid, float* sm) {
+    __shared__ long long scratch[2 * NT / 32];
+    __shared__ unsigned long long s_base;
+    __shared__ int s_lvl[2 * kMaxDecLevels + 2];  // per level: P_k offset, B_k offset
+    const DecLayout d = dec_layout(a.max_width, a.dec_w0);
+    const int W0 = d.W0, K = d.K, H = d.H, ylen = d.ylen4;
+    float* ys = sm;
+    float2* tab = reinterpret_cast<float2*>(sm + d.tab_off);
+    float* reg = sm + d.reg_off;
+    const int row = (int)(bid / ntiles);
+    const int64_t tile = bid - (int64_t)row * ntiles;
+    const int64_t t0 = tile * kSpsOwned;
+    const int64_t L = a.length;
+    const int64_t o = t0 - 1 - H;  // t of ys[0]
+    const float* y = a.dd + (int64_t)row * a.pitch;
+    const RowStats st = a.stats[row];
+    const float m0 = st.m0;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+
+    // stage the series (minus m0, sentinel outside [0, L)) and the table
+    constexpr int kBatch = 8;
+    for (int i0b = threadIdx.x; i0b < ylen; i0b += NT * kBatch) {
+        float v[kBatch];
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+            const int i = i0b + u * NT;
+            const int64_t t = o + i;
+            v[u] = (i < ylen && t >= 0 && t < L) ? __ldg(y + t) - m0 : kSentinel;
+        }
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u)
+            if (i0b + u * NT < ylen) ys[i0b + u * NT] = v[u];
+    }
+    const float2* gtab = a.table + (int64_t)row * a.wpad;
+    for (int e = threadIdx.x; e < d.ntab; e += NT) {
+        int w;
+        if (e < d.wpad0) {
+            w = e + 1;
+        } else {
+            const int k = 1 + (e - d.wpad0) / (W0 / 2);
+            w = (W0 / 2 + 1 + (e - d.wpad0) % (W0 / 2)) << k;
+        }
+        tab[e] = w <= a.max_width ? __ldg(gtab + w - 1) : make_float2(0.0f, -FLT_MAX);
+    }
+    if (threadIdx.x == 0) {
+        int pk = 0, bk = d.npk;
+        for (int k = 1; k <= K; ++k) {
+            s_lvl[2 * k] = pk;
+            s_lvl[2 * k + 1] = bk;
+            pk += dec_level_points(k) + W0;
+            bk += dec_level_points(k);
+        }
+    }
+    __syncthreads();
+
+    // exact FP32 prefix sums when the tile's partial sums stay within 2^24
+    const int seg = (ylen + NT - 1) / NT;
+    const int i0 = min(ylen, threadIdx.x * seg), i1 = min(ylen, i0 + seg);
+    long long run = 0, mn = 0, mx = 0;
+    for (int i = i0; i < i1; ++i) {
+        const float v = ys[i];
+        if (v > kSentinelTest) {
+            run += (long long)(int)v;
+            mn = min(mn, run);
+            mx = max(mx, run);
+        }
+    }
+    const long long before = block_exclusive_scan<NT>(run, scratch);
+    long long gmn = mn + before, gmx = mx + before;
+    block_minmax<NT>(gmn, gmx, scratch);
+    const bool fast = (gmx - gmn) <= (1ll << 24);
+    const int va = (int)max((int64_t)0, -o);                 // ys index of t = 0
+    const int vb = (int)min((int64_t)ylen - 1, L - 1 - o);   // ys index of t = L - 1
+
+    float B[M];
+    int C[M];  // level 0: w0 of the first width chunk reaching B
+    if (fast) {
+        __syncthreads();
+        float runf = (float)before;
+        for (int i = i0; i < i1; ++i) {
+            const float v = ys[i];
+            ys[i] = i > vb + 1 ? -kBig : runf;
+            if (v > kSentinelTest) runf += v;
+        }
+        __syncthreads();
+        const float* P = ys;
+        float base[M];
+#pragma unroll
+        for (int i = 0; i < M; ++i) {
+            const int q = H + M * threadIdx.x + i;
+            base[i] = (q >= va && q <= vb) ? P[q] : kBig;
+        }
+        ThreadBound bnd{};
+        bnd.active = false;
+        boxcar_prefix(P + H, tab, d.wpad0, base, bnd, nullptr, B, C);
+        // the levels' strided prefix sums: P_k[i] = P at t = (jk0 + i) 2^k
+        for (int k = 1; k <= K; ++k) {
+            const int64_t jk0 = (t0 - 1) >> k;
+            float* Pk = reg + s_lvl[2 * k];
+            const int n = dec_level_points(k) + W0;
+            for (int i = threadIdx.x; i < n; i += NT) {
+                const int64_t q = (jk0 + i) * ((int64_t)1 << k) - o;  // jk0 may be -1
+                Pk[i] = q < ylen ? P[q] : -kBig;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < M; ++i) {
+            B[i] = boxcar_exact_slot(ys + H, tab, d.wpad0, i, nullptr);
+            C[i] = 0;
+        }
+    }
+    __syncthreads();
+
+    // B_k at every grid point of the tile: the best of the level's widths
+    int nitems = 0;
+    for (int k = 1; k <= K; ++k) nitems += (int)((((t0 + kSpsTile - 2) >> k) - ((t0 - 1) >> k)) + 1);
+    for (int it = threadIdx.x; it < nitems; it += NT) {
+        int k = 1, jj = it;
+        for (;;) {
+            const int nk = (int)((((t0 + kSpsTile - 2) >> k) - ((t0 - 1) >> k)) + 1);
+            if (jj < nk) break;
+            jj -= nk;
+            ++k;
+        }
+        const int64_t j = ((t0 - 1) >> k) + jj;
+        const float2* tk = tab + d.wpad0 + (k - 1) * (W0 / 2);
+        float best = -FLT_MAX;
+        int bm = 0;
+        if (j >= 0) {
+            if (fast) {
+                const float* Pk = reg + s_lvl[2 * k] + jj;
+                const float p0 = Pk[0];
+                for (int u = 0; u < W0 / 2; ++u) {
+                    const float2 rc = tk[u];
+                    const float snr = fmaf(Pk[W0 / 2 + 1 + u] - p0, rc.x, rc.y);
+                    if (snr > best) { best = snr; bm = u; }
+                }
+            } else {
+                // exact int64 running sums over the window's samples
+                const int64_t q0 = (j << k) - o;
+                const int step = 1 << k;
+                long long S = 0;
+                bool ok = true;
+                for (int m = 1; m <= W0 && ok; ++m) {
+                    for (int r = 0; r < step; ++r) {
+                        const int64_t q = q0 + (int64_t)(m - 1) * step + r;
+                        const float v = q < ylen ? ys[q] : kSentinel;
+                        if (v < kSentinelTest) { ok = false; break; }  // past the series end
+                        S += (long long)v;
+                    }
+                    if (ok && m > W0 / 2) {
+                        const float2 rc = tk[m - W0 / 2 - 1];
+                        const float snr = fmaf(__ll2float_rn(S), rc.x, rc.y);
+                        if (snr > best) { best = snr; bm = m - W0 / 2 - 1; }
+                    }
+                }
+            }
+        }
+        reg[s_lvl[2 * k + 1] + jj] = best;
+        reinterpret_cast<uint8_t*>(reg + d.npk + d.nbk)[s_lvl[2 * k + 1] - d.npk + jj] = (uint8_t)bm;
+    }
+    __syncthreads();
+
+    // B(t) = max over level 0 and every level's grid point at or before t
+    int wdir[M];  // width of a level maximum (0: level 0)
+#pragma unroll
+    for (int i = 0; i < M; ++i) wdir[i] = 0;
+    const int64_t tf = t0 - 1 + M * (int64_t)threadIdx.x;
+    unsigned valid = 0;  // slots with t in [0, L): B is defined there only
+#pragma unroll
+    for (int i = 0; i < M; ++i)
+        if (tf + i >= 0 && tf + i < L) valid |= 1u << i;
+    for (int k = 1; k <= K; ++k) {
+        const int64_t jk0 = (t0 - 1) >> k;
+        const float* Bk = reg + s_lvl[2 * k + 1];
+        const uint8_t* Mk = reinterpret_cast<const uint8_t*>(reg + d.npk + d.nbk) + (s_lvl[2 * k + 1] - d.npk);
+        int64_t jc = -(1ll << 62);
+        float bv = -FLT_MAX;
+        int wv = 0;
+#pragma unroll
+        for (int i = 0; i < M; ++i) {
+            const int64_t j = (tf + i) >> k;
+            if (j != jc) {
+                jc = j;
+                bv = Bk[j - jk0];
+                wv = (W0 / 2 + 1 + Mk[j - jk0]) << k;
+            }
+            if (((valid >> i) & 1u) && bv > B[i]) {
+                B[i] = bv;
+                wdir[i] = wv;
+            }
+        }
+    }
+    if (a.evaluated && threadIdx.x == 0)
+        atomicAdd(a.evaluated, (unsigned long long)NT * M * d.wpad0 + (unsigned long long)nitems * (W0 / 2));
+    __syncthreads();  // everyone done with the level arrays
+
+    float* Bs = reg;                                          // B(t) of every slot
+    uint32_t* plist = reinterpret_cast<uint32_t*>(Bs + kSpsTile);  // slot | level-0 chunk << 16
+    uint16_t* WS = reinterpret_cast<uint16_t*>(plist + kSpsTile);  // direct widths per slot
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+        Bs[M * threadIdx.x + i] = B[i];
+        WS[M * threadIdx.x + i] = (uint16_t)wdir[i];
+    }
+    __syncthreads();
+
+    const bool zero_sigma = st.zero_sigma != 0;
+    unsigned cmask = 0;
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+        const int p = M * threadIdx.x + i;
+        const int64_t t = t0 - 1 + p;
+        if (p >= 1 && p <= kSpsTile - 2 && t < L) {
+            const float v = Bs[p];
+            if (a.snr_out) a.snr_out[(int64_t)row * a.pitch + t] = zero_sigma ? 0.0f : v;
+            if (!zero_sigma && v >= a.threshold && v > Bs[p - 1] && v >= Bs[p + 1]) cmask |= 1u << i;
+        }
+    }
+    long long total = 0;
+    const long long my_off = block_exclusive_scan_total<NT>(__popc(cmask), scratch, total);
+    if (total == 0) return;
+    const uint32_t dm_index = (uint32_t)(a.dm_offset + row);
+    if (threadIdx.x == 0) {
+        s_base = atomicAdd(a.count, (unsigned long long)total);
+        const unsigned long long ci = atomicAdd(a.nchunks, 1ull);
+        if (ci < (unsigned long long)a.chunk_cap)
+            a.chunks[ci] = CandChunk{s_base, (uint32_t)total, dm_index, (uint32_t)t0, (uint32_t)a.beam};
+    }
+    {
+        int j = (int)my_off;
+#pragma unroll
+        for (int i = 0; i < M; ++i)
+            if ((cmask >> i) & 1u)
+                plist[j++] = (uint32_t)(M * threadIdx.x + i) | ((uint32_t)(C[i] / M) << 16);
+    }
+    __syncthreads();
+
+    // widths: direct for a level maximum; for level 0 the smallest w reaching
+    // B(t) within its first chunk, as in the exhaustive search
+    for (int q = warp; q < (int)total; q += NT / 32) {
+        const int p = (int)(plist[q] & 0xffffu);
+        const int cw0 = (int)(plist[q] >> 16) * M;
+        const int64_t t = t0 - 1 + p;
+        const float target = Bs[p];
+        float best = -FLT_MAX;
+        int bw = 0x7fffffff;
+        if (WS[p] != 0) {
+            best = target;
+            bw = WS[p];
+        } else {
+            const int wmax = (int)min((int64_t)d.W0e, L - t);
+            if (fast) {
+                const float* P = ys + H;
+                const float b0 = P[p];
+                for (int w0 = cw0; w0 < wmax; w0 += 32) {
+                    const int w = w0 + lane + 1;
+                    if (w <= wmax) {
+                        const float2 rc = __ldg(gtab + w - 1);
+                        const float snr = fmaf(P[p + w] - b0, rc.x, rc.y);
+                        if (snr > best) { best = snr; bw = w; }
+                    }
+                    if (__any_sync(0xffffffffu, best == target)) break;
+                }
+            } else {
+                const float* yq = ys + H + p;
+                long long base = 0;
+                for (int w0 = 0; w0 < wmax; w0 += 32) {
+                    const int w = w0 + lane + 1;
+                    long long v = (w <= wmax) ? (long long)yq[w - 1] : 0;
+#pragma unroll
+                    for (int s = 1; s < 32; s <<= 1) {
+                        const long long u = __shfl_up_sync(0xffffffffu, v, s);
+                        if (lane >= s) v += u;
+                    }
+                    const long long S = base + v;
+                    base += __shfl_sync(0xffffffffu, v, 31);
+                    if (w <= wmax) {
+                        const float2 rc = __ldg(gtab + w - 1);
+                        const float snr = fmaf(__ll2float_rn(S), rc.x, rc.y);
+                        if (snr > best) { best = snr; bw = w; }
+                    }
+                    if (__any_sync(0xffffffffu, best == target)) break;
+                }
+            }
+#pragma unroll
+            for (int s = 16; s > 0; s >>= 1) {
+                const float ob = __shfl_xor_sync(0xffffffffu, best, s);
+                const int ow = __shfl_xor_sync(0xffffffffu, bw, s);
+                if (ob > best || (ob == best && ow < bw)) { best = ob; bw = ow; }
+            }
+        }
+        const unsigned long long idx = s_base + (unsigned long long)q;
+        if (lane == 0 && idx < (unsigned long long)a.capacity) {
+            aa_candidate c;
+            c.dm_index = dm_index;
+            c.t = (uint32_t)t;
+            c.width = (uint16_t)bw;
+            c.range = (uint8_t)a.range;
+            c.reserved = (uint8_t)a.beam;
+            c.snr = best;
+            a.cands[idx] = c;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(NT, 2) sps_boxcar_dec_kernel(SpsArgs a, int ntiles) {
+    extern __shared__ __align__(16) float sm[];
+    boxcar_dec_block(a, ntiles, blockIdx.x, sm);
+}
+
 __device__ __forceinline__ int find_desc(const int64_t* first, int n, int64_t item) {
     int lo = 0, hi = n - 1;
     while (lo < hi) {
@@ -803,7 +1165,10 @@ __global__ void __launch_bounds__(NT, 2) sps_boxcar_batch_kernel(
         const int64_t item = s_item;
         if (item >= total) break;
         const int k = find_desc(first, ndesc, item);
-        boxcar_block(descs[k], ntiles[k], item - first[k], sm);
+        if (descs[k].dec_w0 > 0)
+            boxcar_dec_block(descs[k], ntiles[k], item - first[k], sm);
+        else
+            boxcar_block(descs[k], ntiles[k], item - first[k], sm);
     }
 }
 
@@ -855,15 +1220,21 @@ size_t sps_boxcar_smem(int wpad) {
            (size_t)((sps_q_count(wpad) + 3) & ~3) * 4 + (size_t)ladder_words(wpad) * 4;
 }
 
+size_t sps_boxcar_smem_for(int32_t max_width, int32_t wpad, int32_t dec_w0) {
+    return dec_w0 > 0 ? dec_layout(max_width, dec_w0).bytes : sps_boxcar_smem(wpad);
+}
+
 cudaError_t launch_sps_boxcar(const SpsArgs& a, cudaStream_t s) {
     if (a.nrows <= 0 || a.length <= 0) return cudaSuccess;
     const int64_t ntiles = (a.length + kSpsOwned - 1) / kSpsOwned;
     const int64_t nblocks = ntiles * a.nrows;
     if (nblocks >= (1ll << 31)) return cudaErrorInvalidConfiguration;
-    const size_t smem = sps_boxcar_smem(a.wpad);
-    cudaError_t e = cudaFuncSetAttribute(sps_boxcar_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem = sps_boxcar_smem_for(a.max_width, a.wpad, a.dec_w0);
+    if (smem > kMaxBoxcarSmem) return cudaErrorInvalidConfiguration;
+    auto kern = a.dec_w0 > 0 ? sps_boxcar_dec_kernel : sps_boxcar_kernel;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    sps_boxcar_kernel<<<(unsigned)nblocks, NT, smem, s>>>(a, (int)ntiles);
+    kern<<<(unsigned)nblocks, NT, smem, s>>>(a, (int)ntiles);
     return cudaGetLastError();
 }
 
@@ -880,10 +1251,10 @@ cudaError_t launch_sps_stats_batch(const SpsArgs* d_descs, const int64_t* d_firs
 }
 
 cudaError_t launch_sps_boxcar_batch(const SpsArgs* d_descs, const int64_t* d_first,
-                                    const int* d_ntiles, int ndesc, int wpad,
+                                    const int* d_ntiles, int ndesc, size_t smem,
                                     unsigned long long* d_queue, int grid, cudaStream_t s) {
     if (ndesc <= 0) return cudaSuccess;
-    const size_t smem = sps_boxcar_smem(wpad);
+    if (smem > kMaxBoxcarSmem) return cudaErrorInvalidConfiguration;
     cudaError_t e = cudaFuncSetAttribute(sps_boxcar_batch_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

@@ -140,3 +140,24 @@ def test_search_row_uses_the_ladder(oracle):
     assert np.array_equal(B, Bd) and np.array_equal(wb, wbd)
     solid = [c for c in cands if not c.fragile]
     assert any(abs(c.t - 1024) <= 16 and c.width >= 128 for c in solid)
+
+
+def test_set_sps_decimated_arguments():
+    from paper_1912_07704_gb300 import abi
+    from paper_1912_07704_gb300.api import Plan
+    p = Plan(64, 1400.0, -4.0, 64e-6, [(0.0, 4.0, 20, 1)])
+    for w0 in (0, 16, 32, 64, 128, 256):
+        p.set_sps_decimated(w0)
+    for w0 in (-16, 8, 24, 48, 512):
+        with pytest.raises(abi.AAError, match="AA_ERR_ARG"):
+            p.set_sps_decimated(w0)
+    # the two width ladders exclude each other
+    p.set_sps_decimated(32)
+    with pytest.raises(abi.AAError, match="AA_ERR_CONFIG"):
+        p.set_sps_ladder(24)
+    p.set_sps_decimated(0)
+    p.set_sps_ladder(24)
+    with pytest.raises(abi.AAError, match="AA_ERR_CONFIG"):
+        p.set_sps_decimated(32)
+    p.set_sps_ladder(0)
+    p.set_sps_decimated(32)
