@@ -806,8 +806,11 @@ aa_status aa_corner_turn_device(const uint8_t* d_tm, int64_t nsamp, int32_t ncha
  * channel chunk `value` (that stage's barrier never completes, so every CTA
  * gives up after the wait limit, sets the workspace error word and exits
  * without writing output; the grouped strategy has no staging waits); what =
- * 2: set the wait limit to `value` nanoseconds (default 2 s).
- * Returns AA_ERR_ARG for an unknown `what` or a non-positive limit. */
+ * 2: set the wait limit to `value` nanoseconds (default 2 s); what = 3: the
+ * boxcar kernel processes `value` consecutive tiles of a series per CTA
+ * (0: its own choice; the results do not depend on it).
+ * Returns AA_ERR_ARG for an unknown `what`, a non-positive limit or a tile
+ * count outside [0, 4096]. */
 aa_status aa_debug_inject(int32_t what, int64_t value);
 
 #ifdef __cplusplus

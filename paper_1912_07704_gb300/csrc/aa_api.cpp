@@ -712,6 +712,7 @@ aa_status aa_debug_inject(int32_t what, int64_t value) {
         case 0:  // reset
             g_fault_skip_chunk = -1;
             g_wait_limit_ns = 2000000000ull;
+            g_boxcar_seg_tiles = 0;
             return AA_OK;
         case 1:  // never issue the staging copy of this channel chunk
             g_fault_skip_chunk = (int)value;
@@ -719,6 +720,10 @@ aa_status aa_debug_inject(int32_t what, int64_t value) {
         case 2:  // bounded-wait limit in nanoseconds
             if (value <= 0) { set_error("limit must be > 0"); return AA_ERR_ARG; }
             g_wait_limit_ns = (uint64_t)value;
+            return AA_OK;
+        case 3:  // boxcar tiles per CTA (0: the launcher's choice)
+            if (value < 0 || value > 4096) { set_error("tiles per CTA must be in [0, 4096]"); return AA_ERR_ARG; }
+            g_boxcar_seg_tiles = (int)value;
             return AA_OK;
     }
     set_error("unknown injection %d", what);

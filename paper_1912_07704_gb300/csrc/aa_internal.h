@@ -373,6 +373,8 @@ size_t sps_boxcar_smem(int wpad);
 // dec_w0): the decimated ladder's when dec_w0 > 0
 size_t sps_boxcar_smem_for(int32_t max_width, int32_t wpad, int32_t dec_w0);
 constexpr size_t kMaxBoxcarSmem = 227 * 1024;
+// test hook: boxcar tiles per CTA (0: the launcher's choice)
+extern int g_boxcar_seg_tiles;
 cudaError_t launch_rsqrt_table(double* t, int wpad, cudaStream_t s);
 
 // Candidate runs moved into their final order: run i copies n[i] records

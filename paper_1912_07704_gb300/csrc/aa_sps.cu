@@ -511,12 +511,22 @@ __host__ __device__ constexpr int sps_region_bytes(int wpad) {
     return (wpad * 8 > kSpsTile * 8) ? wpad * 8 : kSpsTile * 8;
 }
 
-// One CTA's work item: series bid / ntiles, start-time tile bid % ntiles.
-// `sm` is the dynamic shared memory; the caller guarantees that every thread
-// has finished any previous item.
-__device__ __forceinline__ void boxcar_block(const SpsArgs& a, int ntiles, int64_t bid, float* sm) {
+// One CTA's work: tiles [tile_lo, tile_hi) of series `row`, in order.  `sm`
+// is the dynamic shared memory; the caller guarantees that every thread has
+// finished any previous work.
+//
+// Consecutive tiles of a series overlap by ylen - kSpsOwned staged samples
+// (the W-sample halo), so after the first tile the staged prefix sums are
+// slid down by kSpsOwned and only the kSpsOwned new samples are staged and
+// summed, continuing from the exact sum at the old end.  Prefix sums are then
+// relative to the first fully staged tile; sliding is allowed while every
+// staged prefix sum lies within +-2^23 (so every window sum, a difference of
+// two, is an exact FP32 integer); otherwise the tile is staged afresh.
+__device__ __forceinline__ void boxcar_block(const SpsArgs& a, int row, int64_t tile_lo, int64_t tile_hi,
+                                             float* sm) {
     __shared__ long long scratch[2 * NT / 32];
     __shared__ unsigned long long s_base;
+    __shared__ long long s_pend;  // exact prefix sum just past the staged series
     const int wpad = a.wpad;
     const int ylen = kSpsTile + wpad + M;
     float* ys = sm;
@@ -526,31 +536,25 @@ __device__ __forceinline__ void boxcar_block(const SpsArgs& a, int ntiles, int64
     uint32_t* s_ladder = reinterpret_cast<uint32_t*>(Qs + ((nq + 3) & ~3));
     const uint32_t* lmask = a.ladder_g16 > 0 ? s_ladder : nullptr;
     if (lmask) fill_ladder(s_ladder, wpad / M, a.ladder_g16);  // visible after the staging barrier
-    const int row = (int)(bid / ntiles);
-    const int64_t tile = bid - (int64_t)row * ntiles;
-    const int64_t t0 = tile * kSpsOwned;
     const int64_t L = a.length;
     const float* y = a.dd + (int64_t)row * a.pitch;
     const RowStats st = a.stats[row];
     const float m0 = st.m0;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-
-    // Stage the series (minus m0, sentinel outside [0, L)) and the width
-    // table; loads are issued in batches so that their latencies overlap.
-    constexpr int kBatch = 8;
-    for (int i0b = threadIdx.x; i0b < ylen; i0b += NT * kBatch) {
-        float v[kBatch];
-#pragma unroll
-        for (int u = 0; u < kBatch; ++u) {
-            const int i = i0b + u * NT;
-            const int64_t t = t0 - 1 + i;
-            v[u] = (i < ylen && t >= 0 && t < L) ? __ldg(y + t) - m0 : kSentinel;
-        }
-#pragma unroll
-        for (int u = 0; u < kBatch; ++u)
-            if (i0b + u * NT < ylen) ys[i0b + u * NT] = v[u];
-    }
     const float2* gtab = a.table + (int64_t)row * wpad;
+    constexpr int kBatch = 8;
+    constexpr long long kSlideMax = 1ll << 23;
+    bool slide = false;  // ys holds the previous tile's prefix sums, all within +-2^23
+
+    for (int64_t tile = tile_lo; tile < tile_hi; ++tile) {
+    const int64_t t0 = tile * kSpsOwned;
+    // valid start/sample positions: i in [va, vb]  (t = t0-1+i in [0, L))
+    const int va = t0 == 0 ? 1 : 0;
+    const int vb = (int)min((int64_t)ylen - 1, L - t0);
+    const int nkeep = ylen - kSpsOwned;  // staged samples shared with the previous tile
+
+    // The width table, then the series: after a slide only the new samples
+    // (minus m0, sentinel outside [0, L)), else all of them.
     {
         const float4* g4 = reinterpret_cast<const float4*>(gtab);  // wpad is even
         float4* t4 = reinterpret_cast<float4*>(tab);
@@ -567,41 +571,123 @@ __device__ __forceinline__ void boxcar_block(const SpsArgs& a, int ntiles, int64
                 if (i0b + u * NT < n4) t4[i0b + u * NT] = v[u];
         }
     }
-    __syncthreads();
+    bool fast = false;
+    if (slide) {
+        // slide P down by kSpsOwned: rounds of NT x 16 values, all loads of a
+        // round before its stores (a round's source and destination overlap;
+        // a later round's source never meets an earlier round's destination)
+        constexpr int kR = 16;
+        for (int r0 = 0; r0 < nkeep; r0 += NT * kR) {
+            float v[kR];
+#pragma unroll
+            for (int u = 0; u < kR; ++u) {
+                const int i = r0 + u * NT + threadIdx.x;
+                v[u] = i < nkeep ? ys[i + kSpsOwned] : 0.0f;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int u = 0; u < kR; ++u) {
+                const int i = r0 + u * NT + threadIdx.x;
+                if (i < nkeep) ys[i] = v[u];
+            }
+        }
+        __syncthreads();  // the last round's loads are done before the new samples land
+        for (int i0b = nkeep + threadIdx.x; i0b < ylen; i0b += NT * kBatch) {
+            float v[kBatch];
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u) {
+                const int i = i0b + u * NT;
+                const int64_t t = t0 - 1 + i;
+                v[u] = (i < ylen && t >= 0 && t < L) ? __ldg(y + t) - m0 : kSentinel;
+            }
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u)
+                if (i0b + u * NT < ylen) ys[i0b + u * NT] = v[u];
+        }
+        __syncthreads();
+        // exact sums of the new samples, continuing from the old end
+        const int segn = ((kSpsOwned + NT - 1) / NT) | 1;  // odd: distinct banks
+        const int j0 = min(ylen, nkeep + threadIdx.x * segn), j1 = min(ylen, j0 + segn);
+        long long run = 0, mn = 0, mx = 0;
+        for (int i = j0; i < j1; ++i) {
+            const float v = ys[i];
+            if (v > kSentinelTest) {
+                run += (long long)(int)v;
+                mn = min(mn, run);
+                mx = max(mx, run);
+            }
+        }
+        long long tot = 0;
+        const long long pend = s_pend;
+        const long long before = pend + block_exclusive_scan_total<NT>(run, scratch, tot);
+        long long gmn = mn + before, gmx = mx + before;
+        block_minmax<NT>(gmn, gmx, scratch);
+        fast = gmn >= -kSlideMax && gmx <= kSlideMax;
+        if (fast) {
+            float runf = (float)before;
+            for (int i = j0; i < j1; ++i) {
+                const float v = ys[i];
+                ys[i] = i > vb + 1 ? -kBig : runf;
+                if (v > kSentinelTest) runf += v;
+            }
+            if (threadIdx.x == 0) s_pend = pend + tot;
+        }
+        // (the reads of s_pend above precede this barrier, its write follows it)
+        __syncthreads();
+    }
+    if (!fast) {
+        // stage every sample afresh; loads in batches so that latencies overlap
+        for (int i0b = threadIdx.x; i0b < ylen; i0b += NT * kBatch) {
+            float v[kBatch];
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u) {
+                const int i = i0b + u * NT;
+                const int64_t t = t0 - 1 + i;
+                v[u] = (i < ylen && t >= 0 && t < L) ? __ldg(y + t) - m0 : kSentinel;
+            }
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u)
+                if (i0b + u * NT < ylen) ys[i0b + u * NT] = v[u];
+        }
+        __syncthreads();
 
-    // Largest |partial sum| of the tile = range of the prefix sums of ys over
-    // its valid samples: FP32 sums are exact when it is <= 2^24.
-    const int seg = (ylen + NT - 1) / NT;
-    const int i0 = min(ylen, threadIdx.x * seg), i1 = min(ylen, i0 + seg);
-    long long run = 0, mn = 0, mx = 0;
-    for (int i = i0; i < i1; ++i) {
-        const float v = ys[i];
-        if (v > kSentinelTest) {
-            run += (long long)(int)v;
-            mn = min(mn, run);
-            mx = max(mx, run);
+        // Largest |partial sum| of the tile = range of the prefix sums of ys over
+        // its valid samples: FP32 sums are exact when it is <= 2^24.
+        const int seg = ((ylen + NT - 1) / NT) | 1;  // odd: the threads' segments fall on distinct banks
+        const int i0 = min(ylen, threadIdx.x * seg), i1 = min(ylen, i0 + seg);
+        long long run = 0, mn = 0, mx = 0;
+        for (int i = i0; i < i1; ++i) {
+            const float v = ys[i];
+            if (v > kSentinelTest) {
+                run += (long long)(int)v;
+                mn = min(mn, run);
+                mx = max(mx, run);
+            }
+        }
+        long long tot = 0;
+        const long long before = block_exclusive_scan_total<NT>(run, scratch, tot);
+        long long gmn = mn + before, gmx = mx + before;
+        block_minmax<NT>(gmn, gmx, scratch);
+        fast = (gmx - gmn) <= (1ll << 24);
+        slide = gmn >= -kSlideMax && gmx <= kSlideMax;  // the next tile may slide
+        if (fast) {
+            // ys -> prefix sums P, in place (exact FP32 integers)
+            __syncthreads();
+            float runf = (float)before;
+            for (int i = i0; i < i1; ++i) {
+                const float v = ys[i];
+                ys[i] = i > vb + 1 ? -kBig : runf;
+                if (v > kSentinelTest) runf += v;
+            }
+            if (threadIdx.x == 0) s_pend = tot;
+            __syncthreads();
         }
     }
-    const long long before = block_exclusive_scan<NT>(run, scratch);
-    long long gmn = mn + before, gmx = mx + before;
-    block_minmax<NT>(gmn, gmx, scratch);
-    const bool fast = (gmx - gmn) <= (1ll << 24);
-    // valid start/sample positions: i in [va, vb]  (t = t0-1+i in [0, L))
-    const int va = t0 == 0 ? 1 : 0;
-    const int vb = (int)min((int64_t)ylen - 1, L - t0);
+    slide = slide && fast && (tile + 1 < tile_hi);
 
     float B[M];
     int C[M];  // per slot: w0 of the first width chunk reaching B (0 on the exact path)
     if (fast) {
-        // ys -> prefix sums P, in place (exact FP32 integers)
-        __syncthreads();
-        float runf = (float)before;
-        for (int i = i0; i < i1; ++i) {
-            const float v = ys[i];
-            ys[i] = i > vb + 1 ? -kBig : runf;
-            if (v > kSentinelTest) runf += v;
-        }
-        __syncthreads();
         const float* P = ys;
         if (a.prune) {  // block maxima Q, one warp per block
             for (int j = warp; j < nq; j += NT / 32) {
@@ -670,10 +756,10 @@ __device__ __forceinline__ void boxcar_block(const SpsArgs& a, int ntiles, int64
             if (!zero_sigma && v >= a.threshold && v > Bs[p - 1] && v >= Bs[p + 1]) cmask |= 1u << i;
         }
     }
-    // One atomic per CTA: the CTA's candidates form one contiguous run in t order.
+    // One atomic per tile: the tile's candidates form one contiguous run in t order.
     long long total = 0;
     const long long my_off = block_exclusive_scan_total<NT>(__popc(cmask), scratch, total);
-    if (total == 0) return;
+    if (total > 0) {
     const uint32_t dm_index = (uint32_t)(a.dm_offset + row);
     if (threadIdx.x == 0) {
         s_base = atomicAdd(a.count, (unsigned long long)total);
@@ -756,11 +842,19 @@ __device__ __forceinline__ void boxcar_block(const SpsArgs& a, int ntiles, int64
             a.cands[idx] = c;
         }
     }
+    }  // total > 0
+    __syncthreads();  // the next tile overwrites the series, table and lists
+    }  // tiles
 }
 
-__global__ void __launch_bounds__(NT, 2) sps_boxcar_kernel(SpsArgs a, int ntiles) {
+// CTA = seg_tiles consecutive tiles of one series (the last segment of a
+// series may be shorter).
+__global__ void __launch_bounds__(NT, 2) sps_boxcar_kernel(SpsArgs a, int ntiles, int seg_tiles) {
     extern __shared__ __align__(16) float sm[];
-    boxcar_block(a, ntiles, blockIdx.x, sm);
+    const int nseg = (ntiles + seg_tiles - 1) / seg_tiles;
+    const int row = (int)(blockIdx.x / (unsigned)nseg);
+    const int64_t lo = (int64_t)(blockIdx.x - (unsigned)row * (unsigned)nseg) * seg_tiles;
+    boxcar_block(a, row, lo, min((int64_t)ntiles, lo + seg_tiles), sm);
 }
 
 constexpr int kMaxDecLevels = 16;
@@ -869,7 +963,7 @@ __device__ __forceinline__ void boxcar_dec_block(const SpsArgs& a, int ntiles, i
     __syncthreads();
 
     // exact FP32 prefix sums when the tile's partial sums stay within 2^24
-    const int seg = (ylen + NT - 1) / NT;
+    const int seg = ((ylen + NT - 1) / NT) | 1;  // odd: the threads' segments fall on distinct banks
     const int i0 = min(ylen, threadIdx.x * seg), i1 = min(ylen, i0 + seg);
     long long run = 0, mn = 0, mx = 0;
     for (int i = i0; i < i1; ++i) {
@@ -1165,10 +1259,14 @@ __global__ void __launch_bounds__(NT, 2) sps_boxcar_batch_kernel(
         const int64_t item = s_item;
         if (item >= total) break;
         const int k = find_desc(first, ndesc, item);
-        if (descs[k].dec_w0 > 0)
-            boxcar_dec_block(descs[k], ntiles[k], item - first[k], sm);
-        else
-            boxcar_block(descs[k], ntiles[k], item - first[k], sm);
+        const int64_t bid = item - first[k];
+        if (descs[k].dec_w0 > 0) {
+            boxcar_dec_block(descs[k], ntiles[k], bid, sm);
+        } else {
+            const int row = (int)(bid / ntiles[k]);
+            const int64_t tile = bid - (int64_t)row * ntiles[k];
+            boxcar_block(descs[k], row, tile, tile + 1, sm);
+        }
     }
 }
 
@@ -1220,6 +1318,8 @@ size_t sps_boxcar_smem(int wpad) {
            (size_t)((sps_q_count(wpad) + 3) & ~3) * 4 + (size_t)ladder_words(wpad) * 4;
 }
 
+int g_boxcar_seg_tiles = 0;
+
 size_t sps_boxcar_smem_for(int32_t max_width, int32_t wpad, int32_t dec_w0) {
     return dec_w0 > 0 ? dec_layout(max_width, dec_w0).bytes : sps_boxcar_smem(wpad);
 }
@@ -1231,10 +1331,25 @@ cudaError_t launch_sps_boxcar(const SpsArgs& a, cudaStream_t s) {
     if (nblocks >= (1ll << 31)) return cudaErrorInvalidConfiguration;
     const size_t smem = sps_boxcar_smem_for(a.max_width, a.wpad, a.dec_w0);
     if (smem > kMaxBoxcarSmem) return cudaErrorInvalidConfiguration;
-    auto kern = a.dec_w0 > 0 ? sps_boxcar_dec_kernel : sps_boxcar_kernel;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (a.dec_w0 > 0) {
+        cudaError_t e = cudaFuncSetAttribute(sps_boxcar_dec_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        sps_boxcar_dec_kernel<<<(unsigned)nblocks, NT, smem, s>>>(a, (int)ntiles);
+        return cudaGetLastError();
+    }
+    // tiles per CTA: up to 16 (sharing the staged halo), keeping at least
+    // 16 CTAs per resident CTA slot (2 per SM)
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 1;
+    const int seg = g_boxcar_seg_tiles > 0
+                        ? (int)std::min<int64_t>(g_boxcar_seg_tiles, ntiles)
+                        : (int)std::max<int64_t>(1, std::min<int64_t>({16, ntiles, nblocks / (sms * 2 * 16)}));
+    const int64_t ncta = (int64_t)a.nrows * ((ntiles + seg - 1) / seg);
+    cudaError_t e = cudaFuncSetAttribute(sps_boxcar_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<(unsigned)nblocks, NT, smem, s>>>(a, (int)ntiles);
+    sps_boxcar_kernel<<<(unsigned)ncta, NT, smem, s>>>(a, (int)ntiles, seg);
     return cudaGetLastError();
 }
 
