@@ -16,6 +16,7 @@
 //             arithmetic bit for bit.
 #include <algorithm>
 #include <cfloat>
+#include <climits>
 #include <cstdint>
 
 #include "aa_internal.h"
@@ -302,6 +303,49 @@ __device__ long long block_exclusive_scan_total(long long v, long long* scratch,
     return ex;
 }
 
+// Block-wide exclusive scan of one int64 `run` per thread, together with the
+// block total and the smallest and largest prefix value min(before + mn) /
+// max(before + mx) (mn <= 0 <= mx relative to the thread's own start), in two
+// barriers.  scratch: 3 * NT / 32 entries.
+template <int NT>
+__device__ void block_scan_minmax(long long run, long long mn, long long mx, long long* scratch,
+                                  long long& before, long long& total, long long& gmn, long long& gmx) {
+    constexpr int NW = NT / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    long long inc = run;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long u = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += u;
+    }
+    const long long ex = inc - run;
+    long long lmn = ex + mn, lmx = ex + mx;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        lmn = min(lmn, __shfl_xor_sync(0xffffffffu, lmn, o));
+        lmx = max(lmx, __shfl_xor_sync(0xffffffffu, lmx, o));
+    }
+    if (lane == 31) scratch[warp] = inc;
+    if (lane == 0) {
+        scratch[NW + warp] = lmn;
+        scratch[2 * NW + warp] = lmx;
+    }
+    __syncthreads();
+    long long t = 0, wbase = 0, bmn = LLONG_MAX, bmx = LLONG_MIN;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+        bmn = min(bmn, t + scratch[NW + w]);
+        bmx = max(bmx, t + scratch[2 * NW + w]);
+        if (w == warp) wbase = t;
+        t += scratch[w];
+    }
+    before = wbase + ex;
+    total = t;
+    gmn = bmn;
+    gmx = bmx;
+    __syncthreads();  // scratch may be reused after this
+}
+
 template <int NT>
 __device__ void block_minmax(long long& mn, long long& mx, long long* scratch) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -524,7 +568,7 @@ __host__ __device__ constexpr int sps_region_bytes(int wpad) {
 // two, is an exact FP32 integer); otherwise the tile is staged afresh.
 __device__ __forceinline__ void boxcar_block(const SpsArgs& a, int row, int64_t tile_lo, int64_t tile_hi,
                                              float* sm) {
-    __shared__ long long scratch[2 * NT / 32];
+    __shared__ long long scratch[3 * NT / 32];
     __shared__ unsigned long long s_base;
     __shared__ long long s_pend;  // exact prefix sum just past the staged series
     const int wpad = a.wpad;
@@ -554,11 +598,13 @@ __device__ __forceinline__ void boxcar_block(const SpsArgs& a, int row, int64_t 
     const int nkeep = ylen - kSpsOwned;  // staged samples shared with the previous tile
 
     // The width table, then the series: after a slide only the new samples
-    // (minus m0, sentinel outside [0, L)), else all of them.
+    // (minus m0, sentinel outside [0, L)), else all of them.  The previous
+    // tile's B(t) and candidate list overwrote only the table's first
+    // kSpsTile * 8 bytes, so after a slide only those are staged again.
     {
         const float4* g4 = reinterpret_cast<const float4*>(gtab);  // wpad is even
         float4* t4 = reinterpret_cast<float4*>(tab);
-        const int n4 = wpad / 2;
+        const int n4 = slide ? min(wpad / 2, kSpsTile * 8 / 16) : wpad / 2;
         for (int i0b = threadIdx.x; i0b < n4; i0b += NT * kBatch) {
             float4 v[kBatch];
 #pragma unroll
@@ -617,11 +663,12 @@ __device__ __forceinline__ void boxcar_block(const SpsArgs& a, int row, int64_t 
                 mx = max(mx, run);
             }
         }
-        long long tot = 0;
+        long long tot = 0, ex = 0, gmn = 0, gmx = 0;
         const long long pend = s_pend;
-        const long long before = pend + block_exclusive_scan_total<NT>(run, scratch, tot);
-        long long gmn = mn + before, gmx = mx + before;
-        block_minmax<NT>(gmn, gmx, scratch);
+        block_scan_minmax<NT>(run, mn, mx, scratch, ex, tot, gmn, gmx);
+        const long long before = pend + ex;
+        gmn += pend;
+        gmx += pend;
         fast = gmn >= -kSlideMax && gmx <= kSlideMax;
         if (fast) {
             float runf = (float)before;
@@ -664,10 +711,8 @@ __device__ __forceinline__ void boxcar_block(const SpsArgs& a, int row, int64_t 
                 mx = max(mx, run);
             }
         }
-        long long tot = 0;
-        const long long before = block_exclusive_scan_total<NT>(run, scratch, tot);
-        long long gmn = mn + before, gmx = mx + before;
-        block_minmax<NT>(gmn, gmx, scratch);
+        long long tot = 0, before = 0, gmn = 0, gmx = 0;
+        block_scan_minmax<NT>(run, mn, mx, scratch, before, tot, gmn, gmx);
         fast = (gmx - gmn) <= (1ll << 24);
         slide = gmn >= -kSlideMax && gmx <= kSlideMax;  // the next tile may slide
         if (fast) {
@@ -689,17 +734,23 @@ __device__ __forceinline__ void boxcar_block(const SpsArgs& a, int row, int64_t 
     int C[M];  // per slot: w0 of the first width chunk reaching B (0 on the exact path)
     if (fast) {
         const float* P = ys;
-        if (a.prune) {  // block maxima Q, one warp per block
-            for (int j = warp; j < nq; j += NT / 32) {
-                float m = -FLT_MAX;
+        if (a.prune) {  // block maxima Q: a warp reduces 4 blocks at once
+            for (int j0 = 4 * warp; j0 < nq; j0 += 4 * (NT / 32)) {
+                float m[4];
 #pragma unroll
-                for (int u = 0; u < kQSpan / 32; ++u) {
-                    const int i = j * kQSpan + u * 32 + lane;
-                    if (i < ylen) m = fmaxf(m, P[i]);
+                for (int b = 0; b < 4; ++b) {
+                    m[b] = -FLT_MAX;
+#pragma unroll
+                    for (int u = 0; u < kQSpan / 32; ++u) {
+                        const int i = (j0 + b) * kQSpan + u * 32 + lane;
+                        if (i < ylen) m[b] = fmaxf(m[b], P[i]);
+                    }
                 }
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-                if (lane == 0) Qs[j] = m;
+                for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) m[b] = fmaxf(m[b], __shfl_xor_sync(0xffffffffu, m[b], o));
+                if (lane < 4 && j0 + lane < nq) Qs[j0 + lane] = lane == 0 ? m[0] : lane == 1 ? m[1] : lane == 2 ? m[2] : m[3];
             }
             __syncthreads();
         }
