@@ -440,10 +440,13 @@ __device__ __forceinline__ void load_words5(const unsigned char* row, int64_t bo
 //            the warps;
 //   phase 2: warp w (trial d0 + w) adds z_g[t + delta_g(w)] for its 16
 //            samples t: copy (delta & 1), word offset delta >> 1, aligned.
-// 16-bit lanes never overflow: a chunk holds at most 65535 / (255 dec)
-// channels, and trial accumulators are flushed every a.gflush chunks.
+// 16-bit lanes never overflow: a group sum has at most 65535 / (255 dec)
+// members, and a trial's accumulators are flushed into 32-bit totals every
+// a.gflush chunks when a chunk fits the lanes, else (a.gflush = 0) before each
+// group flagged by the plan (the members added since the last flush would
+// otherwise pass 65535 / (255 dec)).
 // `wait_limit_ns` and `fault_skip_chunk` are unused (no device-side waits).
-template <int EB>
+template <int EB, bool FLAGS>
 __device__ __forceinline__ void dedisperse_grouped_block(const DedispArgs& a, int ndm_blocks,
                                                          int64_t bid, unsigned char* smem) {
     constexpr int T = kGroupTau;
@@ -500,7 +503,7 @@ __device__ __forceinline__ void dedisperse_grouped_block(const DedispArgs& a, in
                 g_ms = (uint32_t)g.mstart | ((uint32_t)g.mcount << 16);
                 g_span = g.span;
                 const int dl = g.delta[warp];
-                g_p2 = (lane * 2 + (dl & 1)) * gzw + (dl >> 1);
+                g_p2 = ((lane * 2 + (dl & 1)) * gzw + (dl >> 1)) | (g.pad ? (int)0x80000000u : 0);
             }
             // ---- phase 1: group sums of this batch.  With a.gtl > 0: two full
             // units per group (samples 0..511), then tail units that cover the
@@ -634,16 +637,34 @@ __device__ __forceinline__ void dedisperse_grouped_block(const DedispArgs& a, in
                 // unrolled twice for 8-bit input; once for 16-bit (measured 2.6 ms
                 // faster per step on the decimated ranges, equal on range 0)
                 constexpr int kP2Unroll = EB == 1 ? 2 : 1;
+                if constexpr (!FLAGS) {
 #pragma unroll kP2Unroll
-                for (int g = 0; g < ge - gb; ++g) {
-                    const uint32_t* src = zl + __shfl_sync(0xffffffffu, g_p2, g);
+                    for (int g = 0; g < ge - gb; ++g) {
+                        const uint32_t* src = zl + __shfl_sync(0xffffffffu, g_p2, g);
 #pragma unroll
-                    for (int q = 0; q < QW; ++q) acc[q] += src[32 * q];
+                        for (int q = 0; q < QW; ++q) acc[q] += src[32 * q];
+                    }
+                } else {
+#pragma unroll 1
+                    for (int g = 0; g < ge - gb; ++g) {
+                        const int off = __shfl_sync(0xffffffffu, g_p2, g);
+                        if (off < 0) {  // this group would overflow the 16-bit lanes
+#pragma unroll
+                            for (int q = 0; q < QW; ++q) {
+                                tot[2 * q] += acc[q] & 0xffffu;
+                                tot[2 * q + 1] += acc[q] >> 16;
+                                acc[q] = 0;
+                            }
+                        }
+                        const uint32_t* src = zl + (off & 0x7fffffff);
+#pragma unroll
+                        for (int q = 0; q < QW; ++q) acc[q] += src[32 * q];
+                    }
                 }
             }
             __syncthreads();  // the next batch (or chunk) overwrites the group sums
         }
-        if (++since_flush >= a.gflush) {
+        if (!FLAGS && ++since_flush >= a.gflush) {
 #pragma unroll
             for (int q = 0; q < QW; ++q) {
                 tot[2 * q] += acc[q] & 0xffffu;
@@ -684,11 +705,12 @@ __device__ __forceinline__ void dedisperse_grouped_block(const DedispArgs& a, in
     }
 }
 
-template <int EB>
+// FLAGS: the plan places the 16-bit flushes group by group (a.gflush == 0)
+template <int EB, bool FLAGS>
 __global__ void __launch_bounds__(kDedispThreads, 2)
     dedisperse_grouped_kernel(DedispArgs a, int ndm_blocks) {
     extern __shared__ __align__(128) unsigned char smem[];
-    dedisperse_grouped_block<EB>(a, ndm_blocks, blockIdx.x, smem);
+    dedisperse_grouped_block<EB, FLAGS>(a, ndm_blocks, blockIdx.x, smem);
 }
 
 template <int SPW>
@@ -734,7 +756,10 @@ __global__ void __launch_bounds__(kDedispThreads, 2)
         const int k = find_desc(first, ndesc, item);
         const DedispArgs& a = descs[k];
         if constexpr (GROUPED)
-            dedisperse_grouped_block<EB>(a, ndm_blocks[k], item - first[k], smem);
+            if (a.gflush == 0)
+                dedisperse_grouped_block<EB, true>(a, ndm_blocks[k], item - first[k], smem);
+            else
+                dedisperse_grouped_block<EB, false>(a, ndm_blocks[k], item - first[k], smem);
         else
             dedisperse_block<4 / EB>(a, ndm_blocks[k], item - first[k], wait_limit_ns, -1, one, smem,
                                      bars, reinit);
@@ -833,7 +858,8 @@ cudaError_t launch_dedisperse(const DedispArgs& a, cudaStream_t s) {
     const int64_t nblocks = (int64_t)ndmb * ntiles;
     if (nblocks >= (1ll << 31)) return cudaErrorInvalidConfiguration;
     if (a.grouped) {
-        auto kern = a.elem == 1 ? dedisperse_grouped_kernel<1> : dedisperse_grouped_kernel<2>;
+        auto kern = a.elem == 1 ? (a.gflush == 0 ? dedisperse_grouped_kernel<1, true> : dedisperse_grouped_kernel<1, false>)
+                                : (a.gflush == 0 ? dedisperse_grouped_kernel<2, true> : dedisperse_grouped_kernel<2, false>);
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)a.smem);
         if (e != cudaSuccess) return e;
         kern<<<(unsigned)nblocks, kDedispThreads, a.smem, s>>>(a, ndmb);

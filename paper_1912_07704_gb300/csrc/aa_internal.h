@@ -46,7 +46,7 @@ struct GroupDesc {
     uint16_t mstart;    // first member in the record's member list
     uint16_t mcount;
     uint16_t span;      // largest relative delay (delta at the block's last trial)
-    uint16_t pad;
+    uint16_t pad;       // 1: flush the trials' 16-bit sums before adding this group
     uint16_t delta[kDmPerBlock];  // relative delay at each trial of the block
 };
 struct GroupMember {   // member m of a (DM block, channel chunk), in group order
@@ -147,7 +147,7 @@ struct RangePlan {
     int gcc = 0;           // channels per chunk
     int gz = 0;            // group sums held in shared memory at once
     int gzw = 0;           // 32-bit words per group-sum copy
-    int gflush = 1;        // chunks between SWAR flushes
+    int gflush = 1;        // chunks between SWAR flushes (0: flushes placed by the groups' flags)
     int gnj = 3;           // 256-sample blocks covering kGroupTau + span_max
     int gtl = 0;           // lanes per group tail (power of two <= 32), 0: none
     size_t gsmem = 0;      // dynamic shared memory per CTA

@@ -108,9 +108,15 @@ static void build_groups(RangePlan& r, int C) {
     // overflow): larger chunks put more channels with one delay pattern into
     // one group; as many group sums per batch as two CTAs per SM leave room
     // for (<= 32, one per lane of the warps' group-field registers)
+    // The 16-bit lanes bound each group sum (at most kGroupSplit members,
+    // fewer when lane_max is smaller) and each trial's running sum between
+    // two flushes (at most lane_max members' worth of group sums: the
+    // flushes are placed group by group, see the flush flags below), not the
+    // chunk.
     constexpr int kGroupChunkMax = 256;
-    constexpr int kGroupSplit = 16;  // members per group sum at most
-    const int gcc = std::min(kGroupChunkMax, lane_max) / 8 * 8;
+    if (lane_max < 1) return;
+    const int kGroupSplit = std::min(16, lane_max);  // members per group sum at most
+    const int gcc = kGroupChunkMax;
     int gz = 0;
     while (grouped_smem(gz + 1, gzw) <= kPairSmem && gz < std::min(gcc, 32)) ++gz;
     if (gcc < 8 || gz < 1) return;
@@ -132,6 +138,7 @@ static void build_groups(RangePlan& r, int C) {
     double direct = 0, grouped = 0;
     std::vector<GroupDesc> local;
     std::vector<std::vector<uint8_t>> members;
+    int run = 0;  // members summed into the trials' 16-bit lanes since the last flush
     for (int b = 0; b < nblk; ++b) {
         const int d0 = b * B, nb = std::min(B, ndm - d0);
         for (int k = 0; k < nchk; ++k) {
@@ -192,6 +199,7 @@ static void build_groups(RangePlan& r, int C) {
                 }
             }
             GroupRec& rec = r.grec[(size_t)b * nchk + k];
+            if (k == 0) run = 0;
             rec.first = (uint32_t)r.gdesc.size();
             rec.ngroups = (uint16_t)laid.size();
             rec.nch = (uint16_t)nch;
@@ -201,6 +209,17 @@ static void build_groups(RangePlan& r, int C) {
                 GroupDesc g = local[(size_t)pt.gi];
                 g.mstart = (uint16_t)m;
                 g.mcount = (uint16_t)(pt.e - pt.b);
+                // flush flag: the trials' 16-bit sums are emptied into their
+                // 32-bit totals before this group when its members would take
+                // the members summed since the last flush past lane_max
+                // (groups are added in this order: chunk by chunk, batch by
+                // batch, in list order)
+                g.pad = 0;
+                if (gcc > lane_max && run + g.mcount > lane_max) {
+                    g.pad = 1;
+                    run = 0;
+                }
+                run += g.mcount;
                 for (int j = pt.b; j < pt.e; ++j) {
                     const uint8_t cl = members[(size_t)pt.gi][(size_t)j];
                     const int32_t s0 = r.shifts[(size_t)d0 * C + c0 + cl];
@@ -216,7 +235,9 @@ static void build_groups(RangePlan& r, int C) {
     r.gcc = gcc;
     r.gz = gz;
     r.gzw = gzw;
-    r.gflush = std::max(1, lane_max / gcc);
+    // a chunk that fits the 16-bit lanes is flushed whole (every lane_max /
+    // gcc chunks); otherwise gflush = 0 and the groups' flags place the flushes
+    r.gflush = gcc <= lane_max ? lane_max / gcc : 0;
     r.gnj = (kGroupTau + r.span_max + 255) / 256;
     r.gsmem = grouped_smem(gz, gzw);
     r.gwork = direct > 0 ? grouped / direct : 1.0;
