@@ -113,7 +113,11 @@ static void build_groups(RangePlan& r, int C) {
     // two flushes (at most lane_max members' worth of group sums: the
     // flushes are placed group by group, see the flush flags below), not the
     // chunk.
-    constexpr int kGroupChunkMax = 256;
+    // Chunks of up to 1024 channels for 8-bit input, 4096 for 16-bit
+    // (measured on the 4096-channel plan: larger chunks give fewer, larger
+    // groups, but past 1024 channels the 8-bit kernel's member rows no longer
+    // stay in L2 across the DM blocks' CTAs).
+    const int kGroupChunkMax = r.elem == 1 ? 1024 : 4096;
     if (lane_max < 1) return;
     const int kGroupSplit = std::min(16, lane_max);  // members per group sum at most
     const int gcc = kGroupChunkMax;
@@ -137,7 +141,7 @@ static void build_groups(RangePlan& r, int C) {
     r.gdesc.clear();
     double direct = 0, grouped = 0;
     std::vector<GroupDesc> local;
-    std::vector<std::vector<uint8_t>> members;
+    std::vector<std::vector<uint16_t>> members;
     int run = 0;  // members summed into the trials' 16-bit lanes since the last flush
     for (int b = 0; b < nblk; ++b) {
         const int d0 = b * B, nb = std::min(B, ndm - d0);
@@ -160,7 +164,7 @@ static void build_groups(RangePlan& r, int C) {
                     local.push_back(g);
                     members.emplace_back();
                 }
-                members[gi].push_back((uint8_t)cl);
+                members[gi].push_back((uint16_t)cl);
             }
             // Phase 1 of the kernel gives the unit(s) of the group at batch
             // position j to slot j % kSlots (a warp or a warp pair), and a unit
@@ -221,7 +225,7 @@ static void build_groups(RangePlan& r, int C) {
                 }
                 run += g.mcount;
                 for (int j = pt.b; j < pt.e; ++j) {
-                    const uint8_t cl = members[(size_t)pt.gi][(size_t)j];
+                    const uint16_t cl = members[(size_t)pt.gi][(size_t)j];
                     const int32_t s0 = r.shifts[(size_t)d0 * C + c0 + cl];
                     const int32_t s1 = r.shifts[(size_t)(d0 + nb - 1) * C + c0 + cl];
                     mem[m++] = GroupMember{s0, (uint16_t)cl, (uint16_t)(s1 - s0)};

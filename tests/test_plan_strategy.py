@@ -53,9 +53,9 @@ def test_grouped_work_counts_delay_patterns(ranges, C):
         split = min(16, 65535 // (255 * rg[3]))
         want = _pattern_work(p.shifts(r), rg[2], C, info.stage_channels, split=split)
         assert info.grouped_work == pytest.approx(want, rel=1e-12)
-        # chunks of 256 channels at every decimation (the 16-bit lanes are
-        # flushed group by group, not chunk by chunk)
-        assert info.stage_channels == 256
+        # chunks of 1024 channels for 8-bit input, 4096 for decimated 16-bit
+        # input (the 16-bit lanes are flushed group by group, not per chunk)
+        assert info.stage_channels == (1024 if rg[3] == 1 else 4096)
 
 
 def test_coarse_plan_keeps_direct():
@@ -77,7 +77,7 @@ def test_grouped_wide_spans_then_unavailable():
     p = Plan(203, 1400.0, -1.5, 64e-6, [(0.0, 3.0, 35, 1)])  # span ~940 samples
     p.set_strategy(0, abi.AA_DEDISP_GROUPED)
     info = abi.aa_plan_range(p.handle, 9001, 0)
-    assert info.grouped_available == 1 and info.stage_channels == 256
+    assert info.grouped_available == 1 and info.stage_channels == 1024
     assert info.smem_bytes <= 113 * 1024
     p = Plan(203, 1400.0, -1.5, 64e-6, [(0.0, 15.0, 35, 1)])  # span ~4700 samples
     info = abi.aa_plan_range(p.handle, 9001, 0)
