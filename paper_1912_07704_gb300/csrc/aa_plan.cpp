@@ -119,7 +119,10 @@ static void build_groups(RangePlan& r, int C) {
     // stay in L2 across the DM blocks' CTAs).
     const int kGroupChunkMax = r.elem == 1 ? 1024 : 4096;
     if (lane_max < 1) return;
-    const int kGroupSplit = std::min(16, lane_max);  // members per group sum at most
+    // members per group sum at most (larger parts mean fewer group sums but a
+    // longer phase 1 for the warp that builds one: measured best at 16 for
+    // 8-bit input, 32 for 16-bit)
+    const int kGroupSplit = std::min(r.elem == 1 ? 16 : 32, lane_max);
     const int gcc = kGroupChunkMax;
     int gz = 0;
     while (grouped_smem(gz + 1, gzw) <= kPairSmem && gz < std::min(gcc, 32)) ++gz;

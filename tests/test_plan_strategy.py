@@ -49,8 +49,9 @@ def test_grouped_work_counts_delay_patterns(ranges, C):
     for r, rg in enumerate(ranges):
         p.set_strategy(r, abi.AA_DEDISP_GROUPED)  # stage_channels of the grouped tiles
         info = abi.aa_plan_range(p.handle, 1 << 17, r)
-        # a group sum holds at most 16 members, fewer when 16-bit lanes need it
-        split = min(16, 65535 // (255 * rg[3]))
+        # a group sum holds at most 16 members (32 for decimated input), fewer
+        # when 16-bit lanes need it
+        split = min(16 if rg[3] == 1 else 32, 65535 // (255 * rg[3]))
         want = _pattern_work(p.shifts(r), rg[2], C, info.stage_channels, split=split)
         assert info.grouped_work == pytest.approx(want, rel=1e-12)
         # chunks of 1024 channels for 8-bit input, 4096 for decimated 16-bit
