@@ -151,11 +151,11 @@ def build_input(plan, w, device):
 # when the kernel changes until it is captured again.
 NCU_TRAFFIC = {
     ("dedisperse_u8", "grouped"): {
-        "small_read_bytes": 543_437_824, "small_write_bytes": 740_257_536,
+        "small_read_bytes": 542_687_232, "small_write_bytes": 740_074_496,
         "small_output_samples": 1500 * 128687,
         "capture": "profiles/dedisperse_grouped_u8_ska-4096ch-2^17.md"},
     ("sps_boxcar", "pruned"): {
-        "small_read_bytes": 875_240_960, "small_write_bytes": 44_166_400,
+        "small_read_bytes": 947_282_688, "small_write_bytes": 42_682_624,
         "small_output_samples": 1500 * 128687,
         "capture": "profiles/sps_boxcar_ska-4096ch-2^17.md"},
 }
