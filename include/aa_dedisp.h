@@ -135,7 +135,9 @@ typedef struct aa_range_info {
     /* strategy (fixed at aa_plan_create) */
     int32_t tile_dms;        /* DM trials per dedispersion CTA */
     int32_t tile_samples;    /* output samples per dedispersion CTA */
-    int32_t stage_channels;  /* channel rows per shared-memory stage */
+    int32_t stage_channels;  /* direct strategy: channel rows per shared-memory stage;
+                                grouped: channels per chunk whose delay patterns are
+                                grouped (1024 for 8-bit, 4096 for decimated input) */
     int32_t stages;          /* pipeline depth of the staging copies */
     int32_t span_max;        /* largest delay spread across one CTA's trials */
     int32_t smem_bytes;      /* dynamic shared memory per dedispersion CTA */
