@@ -14,6 +14,8 @@
 // 32-bit add), flushing into 32-bit totals before a lane can overflow.
 #include <cstdint>
 
+#include <algorithm>
+
 #include "aa_internal.h"
 
 namespace aa {
@@ -793,6 +795,49 @@ __global__ void __launch_bounds__(256) decimate_kernel(const Tin* __restrict__ i
     }
 }
 
+// Pair sums (factor 2) with 16-byte loads and stores: a thread makes 8
+// outputs of a row from 16 input samples; the last nout % 8 outputs of each
+// row one by one.  Rows, pitches and bases are 16-byte aligned (the launcher
+// checks).  For 8-bit input a word (b0, b1, b2, b3) gives the 16-bit lanes
+// (b0 + b1, b2 + b3) as (x & 0x00ff00ff) + ((x >> 8) & 0x00ff00ff); for
+// 16-bit input a word (a, b) gives a + b.
+template <typename Tin>
+__global__ void __launch_bounds__(256) decimate2_vec_kernel(const Tin* __restrict__ in, int64_t in_pitch,
+                                                            int32_t nchans, int64_t nout,
+                                                            uint16_t* __restrict__ out, int64_t out_pitch) {
+    const int64_t octs = nout / 8;
+    const int64_t total = octs * nchans;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += stride) {
+        const int64_t c = q / octs;
+        const int64_t j0 = (q - c * octs) * 8;
+        const Tin* src = in + c * in_pitch + 2 * j0;
+        uint4 r;
+        if constexpr (sizeof(Tin) == 1) {
+            const uint4 v = __ldg(reinterpret_cast<const uint4*>(src));
+            r.x = (v.x & 0x00ff00ffu) + ((v.x >> 8) & 0x00ff00ffu);
+            r.y = (v.y & 0x00ff00ffu) + ((v.y >> 8) & 0x00ff00ffu);
+            r.z = (v.z & 0x00ff00ffu) + ((v.z >> 8) & 0x00ff00ffu);
+            r.w = (v.w & 0x00ff00ffu) + ((v.w >> 8) & 0x00ff00ffu);
+        } else {
+            const uint4 v0 = __ldg(reinterpret_cast<const uint4*>(src));
+            const uint4 v1 = __ldg(reinterpret_cast<const uint4*>(src) + 1);
+            auto pair = [](uint32_t a, uint32_t b) {
+                return ((a & 0xffffu) + (a >> 16)) | (((b & 0xffffu) + (b >> 16)) << 16);
+            };
+            r = make_uint4(pair(v0.x, v0.y), pair(v0.z, v0.w), pair(v1.x, v1.y), pair(v1.z, v1.w));
+        }
+        *reinterpret_cast<uint4*>(out + c * out_pitch + j0) = r;
+    }
+    const int64_t rem = nout - octs * 8;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < rem * nchans; q += stride) {
+        const int64_t c = q / rem;
+        const int64_t j = octs * 8 + (q - c * rem);
+        const Tin* src = in + c * in_pitch + 2 * j;
+        out[c * out_pitch + j] = (uint16_t)((uint32_t)src[0] + (uint32_t)src[1]);
+    }
+}
+
 // Several decimation jobs in one grid-stride launch (jobs of one cascade
 // level only: no job reads another's output).
 __global__ void __launch_bounds__(256) decimate_batch_kernel(const DecimateJob* __restrict__ jobs,
@@ -877,6 +922,18 @@ cudaError_t launch_decimate(const void* in, int in_elem, int64_t in_pitch, int32
                             int64_t nout, int factor, uint16_t* out, int64_t out_pitch,
                             cudaStream_t s) {
     if (nout <= 0) return cudaSuccess;
+    const auto al16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
+    if (factor == 2 && al16(in) && al16(out) && (in_pitch * in_elem) % 16 == 0 && (out_pitch * 2) % 16 == 0) {
+        int64_t blocks = (nout / 8 * nchans + 255) / 256;
+        blocks = std::max<int64_t>(1, std::min<int64_t>(blocks, 152 * 64));
+        if (in_elem == 1)
+            decimate2_vec_kernel<uint8_t><<<(unsigned)blocks, 256, 0, s>>>(
+                static_cast<const uint8_t*>(in), in_pitch, nchans, nout, out, out_pitch);
+        else
+            decimate2_vec_kernel<uint16_t><<<(unsigned)blocks, 256, 0, s>>>(
+                static_cast<const uint16_t*>(in), in_pitch, nchans, nout, out, out_pitch);
+        return cudaGetLastError();
+    }
     const int64_t total = (nout + 3) / 4 * nchans;
     int64_t blocks = (total + 255) / 256;
     if (blocks > 152 * 64) blocks = 152 * 64;
