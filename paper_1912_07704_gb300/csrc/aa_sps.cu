@@ -591,310 +591,310 @@ __device__ __forceinline__ void boxcar_block(const SpsArgs& a, int row, int64_t 
     bool slide = false;  // ys holds the previous tile's prefix sums, all within +-2^23
 
     for (int64_t tile = tile_lo; tile < tile_hi; ++tile) {
-    const int64_t t0 = tile * kSpsOwned;
-    // valid start/sample positions: i in [va, vb]  (t = t0-1+i in [0, L))
-    const int va = t0 == 0 ? 1 : 0;
-    const int vb = (int)min((int64_t)ylen - 1, L - t0);
-    const int nkeep = ylen - kSpsOwned;  // staged samples shared with the previous tile
+        const int64_t t0 = tile * kSpsOwned;
+        // valid start/sample positions: i in [va, vb]  (t = t0-1+i in [0, L))
+        const int va = t0 == 0 ? 1 : 0;
+        const int vb = (int)min((int64_t)ylen - 1, L - t0);
+        const int nkeep = ylen - kSpsOwned;  // staged samples shared with the previous tile
 
-    // The width table, then the series: after a slide only the new samples
-    // (minus m0, sentinel outside [0, L)), else all of them.  The previous
-    // tile's B(t) and candidate list overwrote only the table's first
-    // kSpsTile * 8 bytes, so after a slide only those are staged again.
-    {
-        const float4* g4 = reinterpret_cast<const float4*>(gtab);  // wpad is even
-        float4* t4 = reinterpret_cast<float4*>(tab);
-        const int n4 = slide ? min(wpad / 2, kSpsTile * 8 / 16) : wpad / 2;
-        for (int i0b = threadIdx.x; i0b < n4; i0b += NT * kBatch) {
-            float4 v[kBatch];
+        // The width table, then the series: after a slide only the new samples
+        // (minus m0, sentinel outside [0, L)), else all of them.  The previous
+        // tile's B(t) and candidate list overwrote only the table's first
+        // kSpsTile * 8 bytes, so after a slide only those are staged again.
+        {
+            const float4* g4 = reinterpret_cast<const float4*>(gtab);  // wpad is even
+            float4* t4 = reinterpret_cast<float4*>(tab);
+            const int n4 = slide ? min(wpad / 2, kSpsTile * 8 / 16) : wpad / 2;
+            for (int i0b = threadIdx.x; i0b < n4; i0b += NT * kBatch) {
+                float4 v[kBatch];
 #pragma unroll
-            for (int u = 0; u < kBatch; ++u) {
-                const int i = i0b + u * NT;
-                if (i < n4) v[u] = __ldg(g4 + i);
-            }
-#pragma unroll
-            for (int u = 0; u < kBatch; ++u)
-                if (i0b + u * NT < n4) t4[i0b + u * NT] = v[u];
-        }
-    }
-    bool fast = false;
-    if (slide) {
-        // slide P down by kSpsOwned: rounds of NT x 16 values, all loads of a
-        // round before its stores (a round's source and destination overlap;
-        // a later round's source never meets an earlier round's destination)
-        constexpr int kR = 16;
-        for (int r0 = 0; r0 < nkeep; r0 += NT * kR) {
-            float v[kR];
-#pragma unroll
-            for (int u = 0; u < kR; ++u) {
-                const int i = r0 + u * NT + threadIdx.x;
-                v[u] = i < nkeep ? ys[i + kSpsOwned] : 0.0f;
-            }
-            __syncthreads();
-#pragma unroll
-            for (int u = 0; u < kR; ++u) {
-                const int i = r0 + u * NT + threadIdx.x;
-                if (i < nkeep) ys[i] = v[u];
-            }
-        }
-        __syncthreads();  // the last round's loads are done before the new samples land
-        for (int i0b = nkeep + threadIdx.x; i0b < ylen; i0b += NT * kBatch) {
-            float v[kBatch];
-#pragma unroll
-            for (int u = 0; u < kBatch; ++u) {
-                const int i = i0b + u * NT;
-                const int64_t t = t0 - 1 + i;
-                v[u] = (i < ylen && t >= 0 && t < L) ? __ldg(y + t) - m0 : kSentinel;
-            }
-#pragma unroll
-            for (int u = 0; u < kBatch; ++u)
-                if (i0b + u * NT < ylen) ys[i0b + u * NT] = v[u];
-        }
-        __syncthreads();
-        // exact sums of the new samples, continuing from the old end
-        const int segn = ((kSpsOwned + NT - 1) / NT) | 1;  // odd: distinct banks
-        const int j0 = min(ylen, nkeep + threadIdx.x * segn), j1 = min(ylen, j0 + segn);
-        long long run = 0, mn = 0, mx = 0;
-        for (int i = j0; i < j1; ++i) {
-            const float v = ys[i];
-            if (v > kSentinelTest) {
-                run += (long long)(int)v;
-                mn = min(mn, run);
-                mx = max(mx, run);
-            }
-        }
-        long long tot = 0, ex = 0, gmn = 0, gmx = 0;
-        const long long pend = s_pend;
-        block_scan_minmax<NT>(run, mn, mx, scratch, ex, tot, gmn, gmx);
-        const long long before = pend + ex;
-        gmn += pend;
-        gmx += pend;
-        fast = gmn >= -kSlideMax && gmx <= kSlideMax;
-        if (fast) {
-            float runf = (float)before;
-            for (int i = j0; i < j1; ++i) {
-                const float v = ys[i];
-                ys[i] = i > vb + 1 ? -kBig : runf;
-                if (v > kSentinelTest) runf += v;
-            }
-            if (threadIdx.x == 0) s_pend = pend + tot;
-        }
-        // (the reads of s_pend above precede this barrier, its write follows it)
-        __syncthreads();
-    }
-    if (!fast) {
-        // stage every sample afresh; loads in batches so that latencies overlap
-        for (int i0b = threadIdx.x; i0b < ylen; i0b += NT * kBatch) {
-            float v[kBatch];
-#pragma unroll
-            for (int u = 0; u < kBatch; ++u) {
-                const int i = i0b + u * NT;
-                const int64_t t = t0 - 1 + i;
-                v[u] = (i < ylen && t >= 0 && t < L) ? __ldg(y + t) - m0 : kSentinel;
-            }
-#pragma unroll
-            for (int u = 0; u < kBatch; ++u)
-                if (i0b + u * NT < ylen) ys[i0b + u * NT] = v[u];
-        }
-        __syncthreads();
-
-        // Largest |partial sum| of the tile = range of the prefix sums of ys over
-        // its valid samples: FP32 sums are exact when it is <= 2^24.
-        const int seg = ((ylen + NT - 1) / NT) | 1;  // odd: the threads' segments fall on distinct banks
-        const int i0 = min(ylen, threadIdx.x * seg), i1 = min(ylen, i0 + seg);
-        long long run = 0, mn = 0, mx = 0;
-        for (int i = i0; i < i1; ++i) {
-            const float v = ys[i];
-            if (v > kSentinelTest) {
-                run += (long long)(int)v;
-                mn = min(mn, run);
-                mx = max(mx, run);
-            }
-        }
-        long long tot = 0, before = 0, gmn = 0, gmx = 0;
-        block_scan_minmax<NT>(run, mn, mx, scratch, before, tot, gmn, gmx);
-        fast = (gmx - gmn) <= (1ll << 24);
-        slide = gmn >= -kSlideMax && gmx <= kSlideMax;  // the next tile may slide
-        if (fast) {
-            // ys -> prefix sums P, in place (exact FP32 integers)
-            __syncthreads();
-            float runf = (float)before;
-            for (int i = i0; i < i1; ++i) {
-                const float v = ys[i];
-                ys[i] = i > vb + 1 ? -kBig : runf;
-                if (v > kSentinelTest) runf += v;
-            }
-            if (threadIdx.x == 0) s_pend = tot;
-            __syncthreads();
-        }
-    }
-    slide = slide && fast && (tile + 1 < tile_hi);
-
-    float B[M];
-    int C[M];  // per slot: w0 of the first width chunk reaching B (0 on the exact path)
-    if (fast) {
-        const float* P = ys;
-        if (a.prune) {  // block maxima Q: a warp reduces 4 blocks at once
-            for (int j0 = 4 * warp; j0 < nq; j0 += 4 * (NT / 32)) {
-                float m[4];
-#pragma unroll
-                for (int b = 0; b < 4; ++b) {
-                    m[b] = -FLT_MAX;
-#pragma unroll
-                    for (int u = 0; u < kQSpan / 32; ++u) {
-                        const int i = (j0 + b) * kQSpan + u * 32 + lane;
-                        if (i < ylen) m[b] = fmaxf(m[b], P[i]);
-                    }
+                for (int u = 0; u < kBatch; ++u) {
+                    const int i = i0b + u * NT;
+                    if (i < n4) v[u] = __ldg(g4 + i);
                 }
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1)
+                for (int u = 0; u < kBatch; ++u)
+                    if (i0b + u * NT < n4) t4[i0b + u * NT] = v[u];
+            }
+        }
+        bool fast = false;
+        if (slide) {
+            // slide P down by kSpsOwned: rounds of NT x 16 values, all loads of a
+            // round before its stores (a round's source and destination overlap;
+            // a later round's source never meets an earlier round's destination)
+            constexpr int kR = 16;
+            for (int r0 = 0; r0 < nkeep; r0 += NT * kR) {
+                float v[kR];
 #pragma unroll
-                    for (int b = 0; b < 4; ++b) m[b] = fmaxf(m[b], __shfl_xor_sync(0xffffffffu, m[b], o));
-                if (lane < 4 && j0 + lane < nq) Qs[j0 + lane] = lane == 0 ? m[0] : lane == 1 ? m[1] : lane == 2 ? m[2] : m[3];
+                for (int u = 0; u < kR; ++u) {
+                    const int i = r0 + u * NT + threadIdx.x;
+                    v[u] = i < nkeep ? ys[i + kSpsOwned] : 0.0f;
+                }
+                __syncthreads();
+#pragma unroll
+                for (int u = 0; u < kR; ++u) {
+                    const int i = r0 + u * NT + threadIdx.x;
+                    if (i < nkeep) ys[i] = v[u];
+                }
+            }
+            __syncthreads();  // the last round's loads are done before the new samples land
+            for (int i0b = nkeep + threadIdx.x; i0b < ylen; i0b += NT * kBatch) {
+                float v[kBatch];
+#pragma unroll
+                for (int u = 0; u < kBatch; ++u) {
+                    const int i = i0b + u * NT;
+                    const int64_t t = t0 - 1 + i;
+                    v[u] = (i < ylen && t >= 0 && t < L) ? __ldg(y + t) - m0 : kSentinel;
+                }
+#pragma unroll
+                for (int u = 0; u < kBatch; ++u)
+                    if (i0b + u * NT < ylen) ys[i0b + u * NT] = v[u];
             }
             __syncthreads();
+            // exact sums of the new samples, continuing from the old end
+            const int segn = ((kSpsOwned + NT - 1) / NT) | 1;  // odd: distinct banks
+            const int j0 = min(ylen, nkeep + threadIdx.x * segn), j1 = min(ylen, j0 + segn);
+            long long run = 0, mn = 0, mx = 0;
+            for (int i = j0; i < j1; ++i) {
+                const float v = ys[i];
+                if (v > kSentinelTest) {
+                    run += (long long)(int)v;
+                    mn = min(mn, run);
+                    mx = max(mx, run);
+                }
+            }
+            long long tot = 0, ex = 0, gmn = 0, gmx = 0;
+            const long long pend = s_pend;
+            block_scan_minmax<NT>(run, mn, mx, scratch, ex, tot, gmn, gmx);
+            const long long before = pend + ex;
+            gmn += pend;
+            gmx += pend;
+            fast = gmn >= -kSlideMax && gmx <= kSlideMax;
+            if (fast) {
+                float runf = (float)before;
+                for (int i = j0; i < j1; ++i) {
+                    const float v = ys[i];
+                    ys[i] = i > vb + 1 ? -kBig : runf;
+                    if (v > kSentinelTest) runf += v;
+                }
+                if (threadIdx.x == 0) s_pend = pend + tot;
+            }
+            // (the reads of s_pend above precede this barrier, its write follows it)
+            __syncthreads();
         }
-        float base[M];
-        float pmin = FLT_MAX;
+        if (!fast) {
+            // stage every sample afresh; loads in batches so that latencies overlap
+            for (int i0b = threadIdx.x; i0b < ylen; i0b += NT * kBatch) {
+                float v[kBatch];
+#pragma unroll
+                for (int u = 0; u < kBatch; ++u) {
+                    const int i = i0b + u * NT;
+                    const int64_t t = t0 - 1 + i;
+                    v[u] = (i < ylen && t >= 0 && t < L) ? __ldg(y + t) - m0 : kSentinel;
+                }
+#pragma unroll
+                for (int u = 0; u < kBatch; ++u)
+                    if (i0b + u * NT < ylen) ys[i0b + u * NT] = v[u];
+            }
+            __syncthreads();
+
+            // Largest |partial sum| of the tile = range of the prefix sums of ys over
+            // its valid samples: FP32 sums are exact when it is <= 2^24.
+            const int seg = ((ylen + NT - 1) / NT) | 1;  // odd: the threads' segments fall on distinct banks
+            const int i0 = min(ylen, threadIdx.x * seg), i1 = min(ylen, i0 + seg);
+            long long run = 0, mn = 0, mx = 0;
+            for (int i = i0; i < i1; ++i) {
+                const float v = ys[i];
+                if (v > kSentinelTest) {
+                    run += (long long)(int)v;
+                    mn = min(mn, run);
+                    mx = max(mx, run);
+                }
+            }
+            long long tot = 0, before = 0, gmn = 0, gmx = 0;
+            block_scan_minmax<NT>(run, mn, mx, scratch, before, tot, gmn, gmx);
+            fast = (gmx - gmn) <= (1ll << 24);
+            slide = gmn >= -kSlideMax && gmx <= kSlideMax;  // the next tile may slide
+            if (fast) {
+                // ys -> prefix sums P, in place (exact FP32 integers)
+                __syncthreads();
+                float runf = (float)before;
+                for (int i = i0; i < i1; ++i) {
+                    const float v = ys[i];
+                    ys[i] = i > vb + 1 ? -kBig : runf;
+                    if (v > kSentinelTest) runf += v;
+                }
+                if (threadIdx.x == 0) s_pend = tot;
+                __syncthreads();
+            }
+        }
+        slide = slide && fast && (tile + 1 < tile_hi);
+
+        float B[M];
+        int C[M];  // per slot: w0 of the first width chunk reaching B (0 on the exact path)
+        if (fast) {
+            const float* P = ys;
+            if (a.prune) {  // block maxima Q: a warp reduces 4 blocks at once
+                for (int j0 = 4 * warp; j0 < nq; j0 += 4 * (NT / 32)) {
+                    float m[4];
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) {
+                        m[b] = -FLT_MAX;
+#pragma unroll
+                        for (int u = 0; u < kQSpan / 32; ++u) {
+                            const int i = (j0 + b) * kQSpan + u * 32 + lane;
+                            if (i < ylen) m[b] = fmaxf(m[b], P[i]);
+                        }
+                    }
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+                        for (int b = 0; b < 4; ++b) m[b] = fmaxf(m[b], __shfl_xor_sync(0xffffffffu, m[b], o));
+                    if (lane < 4 && j0 + lane < nq) Qs[j0 + lane] = lane == 0 ? m[0] : lane == 1 ? m[1] : lane == 2 ? m[2] : m[3];
+                }
+                __syncthreads();
+            }
+            float base[M];
+            float pmin = FLT_MAX;
+#pragma unroll
+            for (int i = 0; i < M; ++i) {
+                const int p = M * threadIdx.x + i;
+                const bool valid = p >= va && p <= vb;
+                base[i] = valid ? P[p] : kBig;
+                if (valid) pmin = fminf(pmin, base[i]);
+            }
+            ThreadBound bnd;
+            bnd.Q = Qs;
+            bnd.pmin = pmin;
+            bnd.f = (float)(st.mu - (double)m0);
+            bnd.inv_sigma = (float)st.inv_sigma;
+            bnd.cut = a.threshold > 0.0f ? a.threshold - 1e-3f : -FLT_MAX;
+            bnd.max_width = a.max_width;
+            bnd.ylen = ylen;
+            bnd.nq = nq;
+            bnd.ps = M * threadIdx.x;
+            bnd.active = a.prune != 0;
+            const int chunks = boxcar_prefix(P, tab, wpad, base, bnd, lmask, B, C);
+            if (a.evaluated && (threadIdx.x & 31) == 0)
+                atomicAdd(a.evaluated, (unsigned long long)chunks * 32ull * M * M);
+        } else {
+#pragma unroll
+            for (int i = 0; i < M; ++i) {
+                B[i] = boxcar_exact_slot(ys, tab, wpad, i, lmask);
+                C[i] = 0;
+            }
+            if (a.evaluated && threadIdx.x == 0)
+                atomicAdd(a.evaluated, (unsigned long long)wpad * NT * M);
+        }
+
+        __syncthreads();  // everyone done with the table
+        float* Bs = reinterpret_cast<float*>(tab);  // B(t) of every slot
+        // candidate entries: slot p (bits 0-15) | first chunk w0 / M (bits 16-31)
+        uint32_t* plist = reinterpret_cast<uint32_t*>(Bs + kSpsTile);
+#pragma unroll
+        for (int i = 0; i < M; ++i) Bs[M * threadIdx.x + i] = B[i];
+        __syncthreads();
+
+        const bool zero_sigma = st.zero_sigma != 0;
+        unsigned cmask = 0;
 #pragma unroll
         for (int i = 0; i < M; ++i) {
             const int p = M * threadIdx.x + i;
-            const bool valid = p >= va && p <= vb;
-            base[i] = valid ? P[p] : kBig;
-            if (valid) pmin = fminf(pmin, base[i]);
-        }
-        ThreadBound bnd;
-        bnd.Q = Qs;
-        bnd.pmin = pmin;
-        bnd.f = (float)(st.mu - (double)m0);
-        bnd.inv_sigma = (float)st.inv_sigma;
-        bnd.cut = a.threshold > 0.0f ? a.threshold - 1e-3f : -FLT_MAX;
-        bnd.max_width = a.max_width;
-        bnd.ylen = ylen;
-        bnd.nq = nq;
-        bnd.ps = M * threadIdx.x;
-        bnd.active = a.prune != 0;
-        const int chunks = boxcar_prefix(P, tab, wpad, base, bnd, lmask, B, C);
-        if (a.evaluated && (threadIdx.x & 31) == 0)
-            atomicAdd(a.evaluated, (unsigned long long)chunks * 32ull * M * M);
-    } else {
-#pragma unroll
-        for (int i = 0; i < M; ++i) {
-            B[i] = boxcar_exact_slot(ys, tab, wpad, i, lmask);
-            C[i] = 0;
-        }
-        if (a.evaluated && threadIdx.x == 0)
-            atomicAdd(a.evaluated, (unsigned long long)wpad * NT * M);
-    }
-
-    __syncthreads();  // everyone done with the table
-    float* Bs = reinterpret_cast<float*>(tab);  // B(t) of every slot
-    // candidate entries: slot p (bits 0-15) | first chunk w0 / M (bits 16-31)
-    uint32_t* plist = reinterpret_cast<uint32_t*>(Bs + kSpsTile);
-#pragma unroll
-    for (int i = 0; i < M; ++i) Bs[M * threadIdx.x + i] = B[i];
-    __syncthreads();
-
-    const bool zero_sigma = st.zero_sigma != 0;
-    unsigned cmask = 0;
-#pragma unroll
-    for (int i = 0; i < M; ++i) {
-        const int p = M * threadIdx.x + i;
-        const int64_t t = t0 - 1 + p;
-        if (p >= 1 && p <= kSpsTile - 2 && t < L) {
-            const float v = Bs[p];
-            if (a.snr_out) a.snr_out[(int64_t)row * a.pitch + t] = zero_sigma ? 0.0f : v;
-            if (!zero_sigma && v >= a.threshold && v > Bs[p - 1] && v >= Bs[p + 1]) cmask |= 1u << i;
-        }
-    }
-    // One atomic per tile: the tile's candidates form one contiguous run in t order.
-    long long total = 0;
-    const long long my_off = block_exclusive_scan_total<NT>(__popc(cmask), scratch, total);
-    if (total > 0) {
-    const uint32_t dm_index = (uint32_t)(a.dm_offset + row);
-    if (threadIdx.x == 0) {
-        s_base = atomicAdd(a.count, (unsigned long long)total);
-        const unsigned long long ci = atomicAdd(a.nchunks, 1ull);
-        if (ci < (unsigned long long)a.chunk_cap)
-            a.chunks[ci] = CandChunk{s_base, (uint32_t)total, dm_index, (uint32_t)t0, (uint32_t)a.beam};
-    }
-    {
-        int j = (int)my_off;
-#pragma unroll
-        for (int i = 0; i < M; ++i)
-            if ((cmask >> i) & 1u)
-                plist[j++] = (uint32_t)(M * threadIdx.x + i) | ((uint32_t)(C[i] / M) << 16);
-    }
-    __syncthreads();
-
-    // Width of each candidate: the smallest w reaching B(t), recomputed from
-    // the staged series with the main loop's arithmetic (exact running sums,
-    // fmaf of the correctly rounded sum), one warp per candidate, widths
-    // interleaved over lanes with a warp prefix sum.
-    for (int q = warp; q < (int)total; q += NT / 32) {
-        const int p = (int)(plist[q] & 0xffffu);
-        const int cw0 = (int)(plist[q] >> 16) * M;
-        const int64_t t = t0 - 1 + p;
-        const int wmax = (int)min((int64_t)a.max_width, L - t);
-        const float* yq = ys + p;  // exact path: yq[w-1] = y[t+w-1] - m0
-        const float target = Bs[p];
-        float best = -FLT_MAX;
-        int bw = 0x7fffffff;
-        if (fast) {
-            // prefix form: S_w = P[p+w] - P[p], exact
-            const float* P = ys;
-            const float b0 = P[p];
-            for (int w0 = cw0; w0 < wmax; w0 += 32) {
-                const int w = w0 + lane + 1;
-                if (w <= wmax && (!lmask || ladder_has(lmask, w))) {
-                    const float2 rc = __ldg(gtab + w - 1);
-                    const float snr = fmaf(P[p + w] - b0, rc.x, rc.y);
-                    if (snr > best) { best = snr; bw = w; }
-                }
-                // widths are visited in increasing order: stop at the chunk
-                // where B(t) is first reached
-                if (__any_sync(0xffffffffu, best == target)) break;
-            }
-        } else {
-            long long base = 0;
-            for (int w0 = 0; w0 < wmax; w0 += 32) {
-                const int w = w0 + lane + 1;
-                long long v = (w <= wmax) ? (long long)yq[w - 1] : 0;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const long long u = __shfl_up_sync(0xffffffffu, v, o);
-                    if (lane >= o) v += u;
-                }
-                const long long S = base + v;
-                base += __shfl_sync(0xffffffffu, v, 31);
-                if (w <= wmax && (!lmask || ladder_has(lmask, w))) {
-                    const float2 rc = __ldg(gtab + w - 1);
-                    const float snr = fmaf(__ll2float_rn(S), rc.x, rc.y);
-                    if (snr > best) { best = snr; bw = w; }
-                }
-                if (__any_sync(0xffffffffu, best == target)) break;
+            const int64_t t = t0 - 1 + p;
+            if (p >= 1 && p <= kSpsTile - 2 && t < L) {
+                const float v = Bs[p];
+                if (a.snr_out) a.snr_out[(int64_t)row * a.pitch + t] = zero_sigma ? 0.0f : v;
+                if (!zero_sigma && v >= a.threshold && v > Bs[p - 1] && v >= Bs[p + 1]) cmask |= 1u << i;
             }
         }
+        // One atomic per tile: the tile's candidates form one contiguous run in t order.
+        long long total = 0;
+        const long long my_off = block_exclusive_scan_total<NT>(__popc(cmask), scratch, total);
+        if (total > 0) {
+            const uint32_t dm_index = (uint32_t)(a.dm_offset + row);
+            if (threadIdx.x == 0) {
+                s_base = atomicAdd(a.count, (unsigned long long)total);
+                const unsigned long long ci = atomicAdd(a.nchunks, 1ull);
+                if (ci < (unsigned long long)a.chunk_cap)
+                    a.chunks[ci] = CandChunk{s_base, (uint32_t)total, dm_index, (uint32_t)t0, (uint32_t)a.beam};
+            }
+            {
+                int j = (int)my_off;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const float ob = __shfl_xor_sync(0xffffffffu, best, o);
-            const int ow = __shfl_xor_sync(0xffffffffu, bw, o);
-            if (ob > best || (ob == best && ow < bw)) { best = ob; bw = ow; }
-        }
-        const unsigned long long idx = s_base + (unsigned long long)q;
-        if (lane == 0 && idx < (unsigned long long)a.capacity) {
-            aa_candidate c;
-            c.dm_index = dm_index;
-            c.t = (uint32_t)t;
-            c.width = (uint16_t)bw;
-            c.range = (uint8_t)a.range;
-            c.reserved = (uint8_t)a.beam;
-            c.snr = best;
-            a.cands[idx] = c;
-        }
-    }
-    }  // total > 0
-    __syncthreads();  // the next tile overwrites the series, table and lists
+                for (int i = 0; i < M; ++i)
+                    if ((cmask >> i) & 1u)
+                        plist[j++] = (uint32_t)(M * threadIdx.x + i) | ((uint32_t)(C[i] / M) << 16);
+            }
+            __syncthreads();
+
+            // Width of each candidate: the smallest w reaching B(t), recomputed from
+            // the staged series with the main loop's arithmetic (exact running sums,
+            // fmaf of the correctly rounded sum), one warp per candidate, widths
+            // interleaved over lanes with a warp prefix sum.
+            for (int q = warp; q < (int)total; q += NT / 32) {
+                const int p = (int)(plist[q] & 0xffffu);
+                const int cw0 = (int)(plist[q] >> 16) * M;
+                const int64_t t = t0 - 1 + p;
+                const int wmax = (int)min((int64_t)a.max_width, L - t);
+                const float* yq = ys + p;  // exact path: yq[w-1] = y[t+w-1] - m0
+                const float target = Bs[p];
+                float best = -FLT_MAX;
+                int bw = 0x7fffffff;
+                if (fast) {
+                    // prefix form: S_w = P[p+w] - P[p], exact
+                    const float* P = ys;
+                    const float b0 = P[p];
+                    for (int w0 = cw0; w0 < wmax; w0 += 32) {
+                        const int w = w0 + lane + 1;
+                        if (w <= wmax && (!lmask || ladder_has(lmask, w))) {
+                            const float2 rc = __ldg(gtab + w - 1);
+                            const float snr = fmaf(P[p + w] - b0, rc.x, rc.y);
+                            if (snr > best) { best = snr; bw = w; }
+                        }
+                        // widths are visited in increasing order: stop at the chunk
+                        // where B(t) is first reached
+                        if (__any_sync(0xffffffffu, best == target)) break;
+                    }
+                } else {
+                    long long base = 0;
+                    for (int w0 = 0; w0 < wmax; w0 += 32) {
+                        const int w = w0 + lane + 1;
+                        long long v = (w <= wmax) ? (long long)yq[w - 1] : 0;
+#pragma unroll
+                        for (int o = 1; o < 32; o <<= 1) {
+                            const long long u = __shfl_up_sync(0xffffffffu, v, o);
+                            if (lane >= o) v += u;
+                        }
+                        const long long S = base + v;
+                        base += __shfl_sync(0xffffffffu, v, 31);
+                        if (w <= wmax && (!lmask || ladder_has(lmask, w))) {
+                            const float2 rc = __ldg(gtab + w - 1);
+                            const float snr = fmaf(__ll2float_rn(S), rc.x, rc.y);
+                            if (snr > best) { best = snr; bw = w; }
+                        }
+                        if (__any_sync(0xffffffffu, best == target)) break;
+                    }
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+                    const int ow = __shfl_xor_sync(0xffffffffu, bw, o);
+                    if (ob > best || (ob == best && ow < bw)) { best = ob; bw = ow; }
+                }
+                const unsigned long long idx = s_base + (unsigned long long)q;
+                if (lane == 0 && idx < (unsigned long long)a.capacity) {
+                    aa_candidate c;
+                    c.dm_index = dm_index;
+                    c.t = (uint32_t)t;
+                    c.width = (uint16_t)bw;
+                    c.range = (uint8_t)a.range;
+                    c.reserved = (uint8_t)a.beam;
+                    c.snr = best;
+                    a.cands[idx] = c;
+                }
+            }
+        }  // total > 0
+        __syncthreads();  // the next tile overwrites the series, table and lists
     }  // tiles
 }
 
