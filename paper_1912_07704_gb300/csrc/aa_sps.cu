@@ -777,6 +777,15 @@ __device__ __forceinline__ void boxcar_block(const SpsArgs& a, int row, int64_t 
             const int chunks = boxcar_prefix(P, tab, wpad, base, bnd, lmask, B, C);
             if (a.evaluated && (threadIdx.x & 31) == 0)
                 atomicAdd(a.evaluated, (unsigned long long)chunks * 32ull * M * M);
+            if (slide) {
+                // A warp that finishes its widths early waits for the tile's
+                // slowest one: meanwhile it asks L2 for the next tile's new
+                // samples (every warp covers them all; later requests hit L2).
+                const int64_t t_new = t0 + kSpsOwned - 1 + nkeep;  // first new sample of the next tile
+                const int64_t t_end = min(L, t_new + kSpsOwned);
+                for (int64_t t = t_new + 32 * lane; t < t_end; t += 32 * 32)
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(y + t));
+            }
         } else {
 #pragma unroll
             for (int i = 0; i < M; ++i) {
