@@ -549,8 +549,8 @@ __device__ __noinline__ float boxcar_exact_slot(const float* __restrict__ ys,
     return best;
 }
 
-// Shared memory after the main loop: the table region is reused for B(t)
-// (kSpsTile floats) followed by the candidate entries (kSpsTile u32).
+// Shared memory after the main loop: the end of the table region is reused
+// for B(t) (kSpsTile floats) followed by the candidate entries (kSpsTile u32).
 __host__ __device__ constexpr int sps_region_bytes(int wpad) {
     return (wpad * 8 > kSpsTile * 8) ? wpad * 8 : kSpsTile * 8;
 }
@@ -586,6 +586,10 @@ __device__ __forceinline__ void boxcar_block(const SpsArgs& a, int row, int64_t 
     const float m0 = st.m0;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const float2* gtab = a.table + (int64_t)row * wpad;
+    // B(t) and the candidate list take the last kSpsTile * 8 bytes of the
+    // table region after the width loop: the entries of widths up to
+    // 2 * lists4 stay in shared memory for the candidates' widths
+    const int lists4 = (sps_region_bytes(wpad) - kSpsTile * 8) / 16;
     constexpr int kBatch = 8;
     constexpr long long kSlideMax = 1ll << 23;
     bool slide = false;  // ys holds the previous tile's prefix sums, all within +-2^23
@@ -599,13 +603,14 @@ __device__ __forceinline__ void boxcar_block(const SpsArgs& a, int row, int64_t 
 
         // The width table, then the series: after a slide only the new samples
         // (minus m0, sentinel outside [0, L)), else all of them.  The previous
-        // tile's B(t) and candidate list overwrote only the table's first
-        // kSpsTile * 8 bytes, so after a slide only those are staged again.
+        // tile's B(t) and candidate list overwrote only the table's last
+        // kSpsTile * 8 bytes (from float4 lists4 on), so after a slide only
+        // those are staged again.
         {
             const float4* g4 = reinterpret_cast<const float4*>(gtab);  // wpad is even
             float4* t4 = reinterpret_cast<float4*>(tab);
-            const int n4 = slide ? min(wpad / 2, kSpsTile * 8 / 16) : wpad / 2;
-            for (int i0b = threadIdx.x; i0b < n4; i0b += NT * kBatch) {
+            const int n4 = wpad / 2;
+            for (int i0b = (slide ? lists4 : 0) + threadIdx.x; i0b < n4; i0b += NT * kBatch) {
                 float4 v[kBatch];
 #pragma unroll
                 for (int u = 0; u < kBatch; ++u) {
@@ -797,7 +802,7 @@ __device__ __forceinline__ void boxcar_block(const SpsArgs& a, int row, int64_t 
         }
 
         __syncthreads();  // everyone done with the table
-        float* Bs = reinterpret_cast<float*>(tab);  // B(t) of every slot
+        float* Bs = reinterpret_cast<float*>(tab) + 4 * lists4;  // B(t) of every slot
         // candidate entries: slot p (bits 0-15) | first chunk w0 / M (bits 16-31)
         uint32_t* plist = reinterpret_cast<uint32_t*>(Bs + kSpsTile);
 #pragma unroll
@@ -856,7 +861,7 @@ __device__ __forceinline__ void boxcar_block(const SpsArgs& a, int row, int64_t 
                     for (int w0 = cw0; w0 < wmax; w0 += 32) {
                         const int w = w0 + lane + 1;
                         if (w <= wmax && (!lmask || ladder_has(lmask, w))) {
-                            const float2 rc = __ldg(gtab + w - 1);
+                            const float2 rc = w <= 2 * lists4 ? tab[w - 1] : __ldg(gtab + w - 1);
                             const float snr = fmaf(P[p + w] - b0, rc.x, rc.y);
                             if (snr > best) { best = snr; bw = w; }
                         }
@@ -877,7 +882,7 @@ __device__ __forceinline__ void boxcar_block(const SpsArgs& a, int row, int64_t 
                         const long long S = base + v;
                         base += __shfl_sync(0xffffffffu, v, 31);
                         if (w <= wmax && (!lmask || ladder_has(lmask, w))) {
-                            const float2 rc = __ldg(gtab + w - 1);
+                            const float2 rc = w <= 2 * lists4 ? tab[w - 1] : __ldg(gtab + w - 1);
                             const float snr = fmaf(__ll2float_rn(S), rc.x, rc.y);
                             if (snr > best) { best = snr; bw = w; }
                         }
