@@ -795,46 +795,62 @@ __global__ void __launch_bounds__(256) decimate_kernel(const Tin* __restrict__ i
     }
 }
 
-// Pair sums (factor 2) with 16-byte loads and stores: a thread makes 8
-// outputs of a row from 16 input samples; the last nout % 8 outputs of each
-// row one by one.  Rows, pitches and bases are 16-byte aligned (the launcher
-// checks).  For 8-bit input a word (b0, b1, b2, b3) gives the 16-bit lanes
-// (b0 + b1, b2 + b3) as (x & 0x00ff00ff) + ((x >> 8) & 0x00ff00ff); for
-// 16-bit input a word (a, b) gives a + b.
-template <typename Tin>
-__global__ void __launch_bounds__(256) decimate2_vec_kernel(const Tin* __restrict__ in, int64_t in_pitch,
-                                                            int32_t nchans, int64_t nout,
-                                                            uint16_t* __restrict__ out, int64_t out_pitch) {
-    const int64_t octs = nout / 8;
-    const int64_t total = octs * nchans;
+// Sums of F consecutive samples with 16-byte loads: a thread reads 16 input
+// samples (8-bit: one 16-byte load, F = 2, 4 or 8; 16-bit: two, F = 2) and
+// writes their 16 / F sums with one store; the last nout % (16 / F) outputs
+// of each row one by one.  Rows, pitches and bases are 16-byte aligned (the
+// launcher checks).  An 8-bit word (b0, b1, b2, b3) gives the 16-bit lanes
+// (b0 + b1, b2 + b3) as (x & 0x00ff00ff) + ((x >> 8) & 0x00ff00ff), and the
+// two lanes added give b0 + b1 + b2 + b3; a 16-bit word (a, b) gives a + b.
+template <typename Tin, int F>
+__global__ void __launch_bounds__(256) decimate_vec_kernel(const Tin* __restrict__ in, int64_t in_pitch,
+                                                           int32_t nchans, int64_t nout,
+                                                           uint16_t* __restrict__ out, int64_t out_pitch) {
+    constexpr int OPT = 16 / F;  // outputs per thread
+    static_assert(sizeof(Tin) == 1 || F == 2, "16-bit input: pair sums only");
+    const int64_t units = nout / OPT;
+    const int64_t total = units * nchans;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += stride) {
-        const int64_t c = q / octs;
-        const int64_t j0 = (q - c * octs) * 8;
-        const Tin* src = in + c * in_pitch + 2 * j0;
-        uint4 r;
+        const int64_t c = q / units;
+        const int64_t j0 = (q - c * units) * OPT;
+        const Tin* src = in + c * in_pitch + F * j0;
+        uint16_t* dst = out + c * out_pitch + j0;
         if constexpr (sizeof(Tin) == 1) {
             const uint4 v = __ldg(reinterpret_cast<const uint4*>(src));
-            r.x = (v.x & 0x00ff00ffu) + ((v.x >> 8) & 0x00ff00ffu);
-            r.y = (v.y & 0x00ff00ffu) + ((v.y >> 8) & 0x00ff00ffu);
-            r.z = (v.z & 0x00ff00ffu) + ((v.z >> 8) & 0x00ff00ffu);
-            r.w = (v.w & 0x00ff00ffu) + ((v.w >> 8) & 0x00ff00ffu);
+            const uint32_t p0 = (v.x & 0x00ff00ffu) + ((v.x >> 8) & 0x00ff00ffu);
+            const uint32_t p1 = (v.y & 0x00ff00ffu) + ((v.y >> 8) & 0x00ff00ffu);
+            const uint32_t p2 = (v.z & 0x00ff00ffu) + ((v.z >> 8) & 0x00ff00ffu);
+            const uint32_t p3 = (v.w & 0x00ff00ffu) + ((v.w >> 8) & 0x00ff00ffu);
+            if constexpr (F == 2) {
+                *reinterpret_cast<uint4*>(dst) = make_uint4(p0, p1, p2, p3);
+            } else {
+                const uint32_t s0 = (p0 & 0xffffu) + (p0 >> 16), s1 = (p1 & 0xffffu) + (p1 >> 16);
+                const uint32_t s2 = (p2 & 0xffffu) + (p2 >> 16), s3 = (p3 & 0xffffu) + (p3 >> 16);
+                if constexpr (F == 4)
+                    *reinterpret_cast<uint2*>(dst) = make_uint2(s0 | (s1 << 16), s2 | (s3 << 16));
+                else
+                    *reinterpret_cast<uint32_t*>(dst) = (s0 + s1) | ((s2 + s3) << 16);
+            }
         } else {
             const uint4 v0 = __ldg(reinterpret_cast<const uint4*>(src));
             const uint4 v1 = __ldg(reinterpret_cast<const uint4*>(src) + 1);
-            auto pair = [](uint32_t a, uint32_t b) {
-                return ((a & 0xffffu) + (a >> 16)) | (((b & 0xffffu) + (b >> 16)) << 16);
+            auto pair = [](uint32_t x, uint32_t y) {
+                return ((x & 0xffffu) + (x >> 16)) | (((y & 0xffffu) + (y >> 16)) << 16);
             };
-            r = make_uint4(pair(v0.x, v0.y), pair(v0.z, v0.w), pair(v1.x, v1.y), pair(v1.z, v1.w));
+            *reinterpret_cast<uint4*>(dst) = make_uint4(pair(v0.x, v0.y), pair(v0.z, v0.w), pair(v1.x, v1.y),
+                                                         pair(v1.z, v1.w));
         }
-        *reinterpret_cast<uint4*>(out + c * out_pitch + j0) = r;
     }
-    const int64_t rem = nout - octs * 8;
+    const int64_t rem = nout - units * OPT;
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < rem * nchans; q += stride) {
         const int64_t c = q / rem;
-        const int64_t j = octs * 8 + (q - c * rem);
-        const Tin* src = in + c * in_pitch + 2 * j;
-        out[c * out_pitch + j] = (uint16_t)((uint32_t)src[0] + (uint32_t)src[1]);
+        const int64_t j = units * OPT + (q - c * rem);
+        const Tin* src = in + c * in_pitch + F * j;
+        uint32_t sum = 0;
+#pragma unroll
+        for (int k = 0; k < F; ++k) sum += src[k];
+        out[c * out_pitch + j] = (uint16_t)sum;
     }
 }
 
@@ -923,15 +939,21 @@ cudaError_t launch_decimate(const void* in, int in_elem, int64_t in_pitch, int32
                             cudaStream_t s) {
     if (nout <= 0) return cudaSuccess;
     const auto al16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
-    if (factor == 2 && al16(in) && al16(out) && (in_pitch * in_elem) % 16 == 0 && (out_pitch * 2) % 16 == 0) {
-        int64_t blocks = (nout / 8 * nchans + 255) / 256;
+    const bool vec_ok = al16(in) && al16(out) && (in_pitch * in_elem) % 16 == 0 && (out_pitch * 2) % 16 == 0 &&
+                        (in_elem == 1 ? (factor == 2 || factor == 4 || factor == 8) : factor == 2);
+    if (vec_ok) {
+        int64_t blocks = (nout / (16 / factor) * nchans + 255) / 256;
         blocks = std::max<int64_t>(1, std::min<int64_t>(blocks, 152 * 64));
-        if (in_elem == 1)
-            decimate2_vec_kernel<uint8_t><<<(unsigned)blocks, 256, 0, s>>>(
-                static_cast<const uint8_t*>(in), in_pitch, nchans, nout, out, out_pitch);
-        else
-            decimate2_vec_kernel<uint16_t><<<(unsigned)blocks, 256, 0, s>>>(
+        const uint8_t* in8 = static_cast<const uint8_t*>(in);
+        if (in_elem == 2)
+            decimate_vec_kernel<uint16_t, 2><<<(unsigned)blocks, 256, 0, s>>>(
                 static_cast<const uint16_t*>(in), in_pitch, nchans, nout, out, out_pitch);
+        else if (factor == 2)
+            decimate_vec_kernel<uint8_t, 2><<<(unsigned)blocks, 256, 0, s>>>(in8, in_pitch, nchans, nout, out, out_pitch);
+        else if (factor == 4)
+            decimate_vec_kernel<uint8_t, 4><<<(unsigned)blocks, 256, 0, s>>>(in8, in_pitch, nchans, nout, out, out_pitch);
+        else
+            decimate_vec_kernel<uint8_t, 8><<<(unsigned)blocks, 256, 0, s>>>(in8, in_pitch, nchans, nout, out, out_pitch);
         return cudaGetLastError();
     }
     const int64_t total = (nout + 3) / 4 * nchans;
