@@ -505,7 +505,7 @@ __device__ __forceinline__ void dedisperse_grouped_block(const DedispArgs& a, in
                 g_ms = (uint32_t)g.mstart | ((uint32_t)g.mcount << 16);
                 g_span = g.span;
                 const int dl = g.delta[warp];
-                g_p2 = ((lane * 2 + (dl & 1)) * gzw + (dl >> 1)) | (g.pad ? (int)0x80000000u : 0);
+                g_p2 = ((lane * 2 + (dl & 1)) * gzw + (dl >> 1)) | (g.flush ? (int)0x80000000u : 0);
             }
             // ---- phase 1: group sums of this batch.  With a.gtl > 0: two full
             // units per group (samples 0..511), then tail units that cover the

@@ -46,7 +46,7 @@ struct GroupDesc {
     uint16_t mstart;    // first member in the record's member list
     uint16_t mcount;
     uint16_t span;      // largest relative delay (delta at the block's last trial)
-    uint16_t pad;       // 1: flush the trials' 16-bit sums before adding this group
+    uint16_t flush;     // 1: flush the trials' 16-bit sums before adding this group
     uint16_t delta[kDmPerBlock];  // relative delay at each trial of the block
 };
 struct GroupMember {   // member m of a (DM block, channel chunk), in group order

@@ -221,9 +221,9 @@ static void build_groups(RangePlan& r, int C) {
                 // the members summed since the last flush past lane_max
                 // (groups are added in this order: chunk by chunk, batch by
                 // batch, in list order)
-                g.pad = 0;
+                g.flush = 0;
                 if (gcc > lane_max && run + g.mcount > lane_max) {
-                    g.pad = 1;
+                    g.flush = 1;
                     run = 0;
                 }
                 run += g.mcount;
